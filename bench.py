@@ -1,0 +1,350 @@
+"""AS-TAX throughput benchmark (frames/s) on the 128-element workload.
+
+Workload: 128-element linear array, 0.3 mm pitch, 4096 samples at 40 MHz,
+c = 1540 m/s, 1-6 seeded sources, 128 lateral x 512 depth pixels over
+5-60 mm, 300 bins over 0.5-8 MHz, 3 Pattern-16 apodizations.
+One step = one frame through the whole path: time FFT, apodized lateral
+FFTs, propagate + inverse lateral FFT + correlate, NCC/TAX epilogue.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU. Frames are independent, so
+every rank processes its own frames (weak scaling) and the only
+collectives are a barrier and the max over ranks of the timed region.
+Rank 0 prints one JSON line.
+
+`--impl reference` times the FP64 CPU oracle on the host cores, on a bounded
+sample of the same workload (bins x depth rows), scaled to frames/s.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "AS-TAX frames/s (128 el, 128×512 grid), plain vs chosen form at stated err"
+SMS = 152
+FP32_LANES_PER_SM = 128
+POOL_FRAMES = 96        # 96 distinct frames x 2 MiB = 201 MB > 129 MB L2
+
+
+def fused_flops_per_frame(n_bins, nz, nx, n_apod=3):
+    """Algorithmic FP32 flops of the fused propagate-and-correlate kernel per
+    frame: per (bin, row) and aperture, one phasor multiply (6 nx) and one
+    nx-point inverse FFT (5 nx log2 nx); per pixel 6 accumulations of 4 flops."""
+    import math
+    n_acc = {1: 1, 2: 3, 3: 6}[n_apod]
+    per_row = n_apod * (6 * nx + 5 * nx * math.log2(nx)) + 4 * n_acc * nx
+    return float(n_bins * nz * per_row)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 CUDA-core peak from unit counts: SMs x FP32 lanes x 2 flops (FMA) x clock."""
+    return SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def prop_source_hash():
+    h = hashlib.sha256()
+    for f in ("pam_prop.cu", "pam_internal.h"):
+        with open(os.path.join(ROOT, "paper_2412_02413_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    or None when the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "prop_corr_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("source_sha256") != prop_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"pam_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu_index)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.remove(self.path)
+        if not rows:
+            return None
+        import statistics
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_index_for(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+# ------------------------------------------------------------------- pool --
+def _make_frame(args):
+    wid, f = args
+    from paper_2412_02413_gb300 import synth
+    return synth.make_frame(synth.workload(wid), f)[0]
+
+
+def make_pool(wid, first, n):
+    """Seeded synthetic frames, generated in spawned worker processes (before any CUDA call)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes=max(1, min(16, os.cpu_count() or 1))) as pool:
+        frames = pool.map(_make_frame, [(wid, first + i) for i in range(n)])
+    return np.stack(frames)
+
+
+# --------------------------------------------------------- oracle timing --
+def oracle_sample_rate(w, rf, budget_s, threads=None):
+    """Times the oracle on a bounded sample of the workload (the first n_b bins
+    of Omega x the first nz' depth rows) and scales it to frames/s. Returns
+    (frames/s, seconds measured, sample description, threads)."""
+    import numpy as np
+
+    import oracle
+    threads = threads or (os.cpu_count() or 1)
+    bins = w.bins()
+    A = oracle.pattern(w.n_elem, 3, w.pattern_m)
+
+    def run(nb, nzs):
+        g = oracle.Geometry(w.n_elem, w.nt, w.fs, w.c, w.pitch, nzs, w.z0, w.dz, bins[:nb])
+        t0 = time.perf_counter()
+        oracle.as_tax(g, rf, A, threads=threads)
+        return time.perf_counter() - t0
+
+    # calibrate on one bin per thread and 8 rows, then size the sample to the budget
+    nb0 = min(len(bins), threads)
+    t0 = run(nb0, 8)
+    per_unit = t0 / (nb0 * 8)                               # s per (bin x row), all threads busy
+    units = max(1, int(budget_s / max(per_unit, 1e-9)))
+    nzs = int(min(w.nz, max(1, units // nb0)))
+    nb = int(min(len(bins), max(nb0, units // max(nzs, 1))))
+    t = run(nb, nzs)
+    full_units = len(bins) * w.nz
+    fps = 1.0 / (t * full_units / (nb * nzs))
+    sample = f"{nb} of {len(bins)} bins x {nzs} of {w.nz} depth rows of one frame, {threads} threads"
+    return fps, t, sample, threads
+
+
+def run_reference(args):
+    from paper_2412_02413_gb300 import dist, synth
+    rank, _, world = dist.env_rank()
+    if rank != 0:
+        return 0
+    w = synth.workload(args.workload)
+    rf, _ = synth.make_frame(w, 0)
+    budget = max(0.05, min(2.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample_rate(w, rf, budget)
+    rates = []
+    t_total = 0.0
+    sample, threads = "", 0
+    for _ in range(args.steps):
+        fps, t, sample, threads = oracle_sample_rate(w, rf, budget)
+        rates.append(fps)
+        t_total += t
+    value = len(rates) / sum(1.0 / r for r in rates)   # frames per second of extrapolated time
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "frames_per_step": 1},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads, "kind": "oracle",
+                             "sample": sample + " per step"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------- our arm --
+def run_ours(args):
+    import numpy as np
+
+    from paper_2412_02413_gb300 import dist, synth
+    rank, local, world = dist.env_rank()
+    w = synth.workload(args.workload)
+    F = args.frames_per_step
+    pool_np = make_pool(args.workload, 1000 * rank, args.pool)   # before any CUDA call
+
+    import torch
+    from paper_2412_02413_gb300 import pam
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist.init("nccl")
+    plan = pam.Plan.from_workload(w, max_frames=F)
+    pool = torch.from_numpy(pool_np).to(dev)
+    P = pool.shape[0]
+    outs = {"image": torch.empty(F, w.nz, w.nx, device=dev), "rho_n": torch.empty(F, w.nz, w.nx, device=dev)}
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        s = (i * F) % (P - F + 1)
+        plan.as_tax(pool[s:s + F], outs=outs, stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(gpu_index_for(local))
+    clocks.start()
+    time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize()
+    plan.profile_enable(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prop_ms, prop_launches, launches = plan.profile_read()
+    plan.profile_enable(False)
+    ms_max = dist.max_over_ranks(ms, device=dev)
+    frames_total = dist.sum_over_ranks(args.steps * F, device=dev)
+    value = frames_total / (ms_max / 1000.0)
+
+    # end to end through the host-buffer entry point: pinned rf in, image + rho_n out
+    n_host = min(8, P)
+    rf_host = torch.from_numpy(pool_np[: n_host * F].reshape(n_host, F, w.n_elem, w.nt).copy()).pin_memory()
+    img_host = torch.empty(F, w.nz, w.nx).pin_memory()
+    rho_host = torch.empty(F, w.nz, w.nx).pin_memory()
+    img_np, rho_np = img_host.numpy(), rho_host.numpy()
+    e2e_steps = max(1, min(args.steps, 500))
+    for i in range(min(3, e2e_steps)):
+        plan.as_xcorr_host(rf_host[i % n_host].numpy(), img_np, rho_np, stream=stream)
+    dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        plan.as_xcorr_host(rf_host[i % n_host].numpy(), img_np, rho_np, stream=stream)
+    t_e2e = time.perf_counter() - t0
+    t_e2e = dist.max_over_ranks(t_e2e, device=dev)
+    e2e_value = dist.sum_over_ranks(e2e_steps * F, device=dev) / t_e2e
+
+    peaks, peak_kind = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tf = fp32_peak_tflops(sm_max)
+    flops = fused_flops_per_frame(plan.n_bins, w.nz, w.nx, 3) * F
+    avg_launch_s = prop_ms / max(prop_launches, 1) / 1000.0
+    achieved_tf = flops / avg_launch_s / 1e12
+    traffic = committed_traffic()
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            fps, t, sample, threads = oracle_sample_rate(w, pool_np[0], budget_s=args.cpu_budget)
+            cpu = {"value": fps, "unit": "frames/s", "cores": threads, "kind": "oracle", "sample": sample}
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Green's-function point sources, 20 dB channel SNR)",
+            "config": {"workload": w.name, "frames_per_step": F, "n_elem": w.n_elem, "n_samples": w.nt,
+                       "nx": w.nx, "nz": w.nz, "n_bins": int(plan.n_bins), "n_apod": 3,
+                       "l2": f"rotating pool of {P} distinct input frames ({P * w.n_elem * w.nt * 4 / 1e6:.0f} MB)"
+                             " > 129 MB L2", "parallelism": f"frames sharded over {world} GPU(s)"},
+            "e2e": {"value": e2e_value, "unit": "frames/s",
+                    "h2d_bytes_per_step": F * w.n_elem * w.nt * 4, "d2h_bytes_per_step": 2 * F * w.nz * w.nx * 4},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "kernel": "prop_corr_kernel<3,128>", "achieved": achieved_tf,
+                         "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": traffic,
+                         "peak_basis": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                       f"(sm_max_mhz, {peak_kind})",
+                         "flops_per_launch": flops, "avg_launch_us": avg_launch_s * 1e6,
+                         "share_of_step": (prop_ms / ms) if ms > 0 else None},
+            "clocks": ck,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    dist.finalize()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--frames-per-step", type=int, default=1)
+    ap.add_argument("--pool", type=int, default=POOL_FRAMES)
+    ap.add_argument("--cpu-budget", type=float, default=8.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

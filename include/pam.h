@@ -1,0 +1,176 @@
+/*
+ * pam.h -- C ABI of libpam, GB300 (sm_103a) angular-spectrum passive acoustic
+ * mapping with cross-correlated apodizations: AS, AS-DAX and AS-TAX
+ * (arXiv 2412.02413).
+ *
+ * Every computational step runs in this library's CUDA kernels. The
+ * signatures carry only plain pointers, sizes and an opaque stream handle.
+ *
+ * Problem statement (paper notation)
+ *   rf p(x_e, z0=0, t): float32 [n_frames][n_elem][n_samples], channel-major.
+ *       Element e sits at x_e = (e - (n_elem-1)/2) * pitch_m. The array face is
+ *       the plane z = 0 and its centre is the origin (Fig. 1(a)).
+ *   Omega: the selected DFT bins k, with w_k = 2 pi k fs / n_samples (Eq. 3).
+ *   Eq. 1: P(kx, 0, w) = F_x{F_t{p}}. The forward transforms use exp(-i w t)
+ *       and exp(-i kx x) and are unnormalised. kx_u = 2 pi u' / (nx * pitch)
+ *       with u' = u for u < nx/2, else u - nx.
+ *   Eq. 2: P(kx, z, w) = P(kx, 0, w) exp(i z sqrt(w^2/c^2 - kx^2)), principal
+ *       branch. Evanescent components decay as exp(-kappa z), unless
+ *       PAM_EVANESCENT_ZERO drops them.
+ *   Fields: p~_q(x_i, z_j, w_k) = (1/nx) sum_u P_q exp(+2 pi i u i / nx).
+ *       Pixel column i is element position x_i (nx == n_elem). Row j is at
+ *       depth z_j = z0_m + j * dz_m.
+ *   Eq. 3: I_AS(r) = sum_k |p~(r, w_k)|^2.
+ *   Eq. 4 + Appendix A: rho_qr = Re sum_k conj(p~_q) p~_r /
+ *       sqrt(sum_k |p~_q|^2 * sum_k |p~_r|^2), clamped below at eps (Sec. II-A).
+ *       A zero denominator gives eps.
+ *   Eq. 10: rho_TAX = cbrt(rho_12 * rho_23 * rho_31).
+ *       rho_n = rho / max over the frame's pixels.
+ *   Eq. 5 / Eq. 11: I = rho_n^2 * sum_k |sum_q p~_q|^2.
+ *
+ * Conventions of every entry point
+ *   - Device buffers belong to the caller. They must be device memory that the
+ *     current device can access, and 16-byte aligned; otherwise the call
+ *     returns PAM_ERR_INVALID_ARG.
+ *   - Output maps are float32 [n_frames][nz][nx], row-major (row = depth).
+ *   - Work is queued asynchronously on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream). A returned status reports validation and launch
+ *     errors. Errors raised later on the device, such as a bounded wait that
+ *     timed out, are reported by pam_sync() or by the next call.
+ *   - A plan is not thread-safe: calls on one plan must not overlap. No call
+ *     aborts the process. pam_last_error() gives the message of the calling
+ *     thread's last failure.
+ */
+#ifndef PAM_H
+#define PAM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pam_plan_s *pam_plan_t;
+
+typedef enum {
+    PAM_OK = 0,
+    PAM_ERR_INVALID_ARG = 1, /* a pointer, size or descriptor field is out of range */
+    PAM_ERR_UNSUPPORTED = 2, /* valid for the method, not built here (e.g. nt not a power of 2) */
+    PAM_ERR_OOM = 3,         /* a device or host allocation failed */
+    PAM_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    PAM_ERR_TIMEOUT = 5,     /* a kernel's bounded wait expired (device status word) */
+    PAM_ERR_NUMERIC = 6      /* non-finite input detected */
+} pam_status;
+
+/* descriptor flags */
+#define PAM_EVANESCENT_ZERO 0x1u /* drop components with kx^2 > (w/c)^2 instead of decaying them */
+
+/* Acquisition and imaging geometry (Sec. II-A, Fig. 1; band selection Sec. II-D). */
+typedef struct {
+    int n_elem;           /* elements / channels, 8..256 */
+    double pitch_m;       /* element pitch (m), > 0 */
+    double fs_hz;         /* sampling rate (Hz), > 0 */
+    double c_mps;         /* sound speed (m/s), > 0 */
+    int n_samples;        /* samples per channel nt: a power of two, 64..8192 */
+    int nx;               /* lateral pixels = lateral DFT length; 0 or n_elem. Built: 16, 32, 64, 128 */
+    int nz;               /* depth rows, 1..65535 */
+    double z0_m;          /* depth of row 0 from the array face (m), >= 0 */
+    double dz_m;          /* row spacing (m), > 0 */
+    double f_lo_hz;       /* band used when bins == NULL: all k with f_lo <= k*fs/nt <= f_hi */
+    double f_hi_hz;
+    const int *bins;      /* host, explicit Omega: strictly increasing, 0 < k < nt/2; or NULL */
+    int n_bins;           /* entries in bins (ignored when bins == NULL); 1..8192 */
+    int n_apod;           /* 1 (AS), 2 (AS-DAX) or 3 (AS-TAX) */
+    const float *apod;    /* host [n_apod][n_elem] real weights, or NULL for Pattern-m */
+    int pattern_m;        /* Pattern-m (Sec. II-A): element e in aperture q iff floor(e/m) mod n_apod == q */
+    float eps;            /* NCC floor (Sec. II-A, usually 0.001), 0 < eps <= 1 */
+    unsigned flags;       /* PAM_EVANESCENT_ZERO */
+    int max_frames;       /* frames per kernel batch; larger calls run in batches of this size */
+} pam_plan_desc;
+
+/* Fills `d` with defaults: nx = 0, n_apod = 3, pattern_m = 16, eps = 1e-3,
+ * flags = 0, max_frames = 1, bins = apod = NULL. Geometry fields are zeroed. */
+void pam_plan_desc_init(pam_plan_desc *d);
+
+/* Builds a plan on the current CUDA device (the paper's "pre-run", Sec. II-E,
+ * Table III). It validates `d` and copies it, together with the bins and the
+ * apodizations. It then runs the FP64 table kernel, which computes kz
+ * (Eq. 2) and the fixed-point phase words, and allocates the workspace for
+ * max_frames frames. The call blocks until the tables are built. On failure
+ * *out is set to NULL and nothing is left allocated. */
+pam_status pam_plan_create(const pam_plan_desc *d, pam_plan_t *out);
+
+/* Releases everything the plan owns. NULL-safe. It synchronises with the
+ * plan's outstanding work first. */
+void pam_destroy(pam_plan_t p);
+
+/* Number of bins in Omega. When bins_out != NULL, also copies them there
+ * (host, n_bins ints). */
+int pam_plan_bins(pam_plan_t p, int *bins_out);
+
+/* Copies the plan's apodizations to host memory [n_apod][n_elem]. Returns n_apod. */
+int pam_plan_apod(pam_plan_t p, float *apod_out);
+
+/* AS back-propagation energy map, Eq. 3, for one apodization.
+ *   rf          device float32 [n_frames][n_elem][n_samples]
+ *   apod_index  -1 = full aperture (all ones); 0..n_apod-1 = plan aperture q
+ *   energy      device float32 [n_frames][nz][nx]
+ *   fields      device complex64 as interleaved float pairs
+ *               [n_frames][n_bins][nz][nx][2], or NULL. This is a debug and test
+ *               output: it writes every monochromatic field p~(x_i, z_j, w_k)
+ *               to memory.
+ *   stream      cudaStream_t or NULL */
+pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod_index,
+                           float *energy, float *fields, void *stream);
+
+/* AS-TAX (Eq. 4, 10, 11). The plan must have n_apod == 3.
+ *   image_tax   device [n_frames][nz][nx]  I = rho_n^2 * sum_k |p~_1 + p~_2 + p~_3|^2
+ *   rho_n       device [n_frames][nz][nx] or NULL (normalised rho_TAX)
+ *   rho_pairs   device [n_frames][3][nz][nx] or NULL (rho_12, rho_23, rho_31 after the clamp)
+ *   image_as    device [n_frames][nz][nx] or NULL (sum_k |p~_1 + p~_2 + p~_3|^2; the AS
+ *               image of Eq. 3 when the apodizations sum to one) */
+pam_status pam_as_tax(pam_plan_t p, const float *rf, int n_frames, float *image_tax,
+                      float *rho_n, float *rho_pairs, float *image_as, void *stream);
+
+/* AS-DAX (Eq. 4-5). The plan must have n_apod == 2. rho_pair is
+ * [n_frames][nz][nx] or NULL. */
+pam_status pam_as_dax(pam_plan_t p, const float *rf, int n_frames, float *image_dax,
+                      float *rho_n, float *rho_pair, float *image_as, void *stream);
+
+/* AS-TAX (n_apod == 3) or AS-DAX (n_apod == 2) from HOST memory. rf_host
+ * [n_frames][n_elem][n_samples], image_host and rho_n_host (or NULL)
+ * [n_frames][nz][nx]. The copies run on `stream` through plan-owned device
+ * staging buffers, which the first call allocates. The call returns after the
+ * results are in host memory. Pinned host buffers make the copies faster. */
+pam_status pam_as_xcorr_host(pam_plan_t p, const float *rf_host, int n_frames,
+                             float *image_host, float *rho_n_host, void *stream);
+
+/* Waits for the plan's work on `stream` and reads the device status word.
+ * Returns PAM_ERR_TIMEOUT if a kernel reported an expired wait (then clears
+ * it), PAM_ERR_CUDA on a runtime error, PAM_OK otherwise. */
+pam_status pam_sync(pam_plan_t p, void *stream);
+
+/* Kernel timing for measurement. While enabled, the plan records a CUDA event
+ * pair on the launching stream around every launch of the fused
+ * propagate-and-correlate kernel (the dominant kernel). Enabling or disabling
+ * clears the counters. */
+pam_status pam_profile_enable(pam_plan_t p, int on);
+
+/* Reads and clears the counters: *prop_ms gets the summed device time of the
+ * recorded propagate-and-correlate launches, *prop_launches their count, and
+ * *kernel_launches the number of libpam kernels launched since the last read
+ * or enable (counted whether or not timing is on). Waits for the recorded
+ * events. Any output pointer may be NULL. */
+pam_status pam_profile_read(pam_plan_t p, double *prop_ms, long long *prop_launches,
+                            long long *kernel_launches);
+
+/* Static description of a status code. */
+const char *pam_status_string(pam_status s);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *pam_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAM_H */

@@ -1,0 +1,493 @@
+// pam_api.cu -- host side of libpam: descriptor validation, the plan
+// ("pre-run", Sec. II-E), workspace, and the C entry points of include/pam.h.
+// The arithmetic of every step runs in the kernels of pam_fft.cu and pam_prop.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pam_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+pam_status fail(pam_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+pam_status cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(PAM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+void free_plan_memory(pam_plan_s *p)
+{
+    auto fr = [](void *q) { if (q) cudaFree(q); };
+    fr(p->t.bins); fr(p->t.apod); fr(p->t.ones); fr(p->t.tw_t); fr(p->t.tw_x);
+    fr(p->t.dds); fr(p->t.ecoef); fr(p->t.live); fr(p->t.bin_evan);
+    fr(p->w.S); fr(p->w.Q); fr(p->w.part); fr(p->w.rho_tmp); fr(p->w.e_tmp);
+    fr(p->w.fmax); fr(p->w.status); fr(p->w.rf_stage); fr(p->w.img_stage); fr(p->w.rho_stage);
+    p->t = pam::Tables{};
+    p->w = pam::Workspace{};
+}
+
+// A device pointer argument: non-null, 16-byte aligned, and device or managed memory.
+pam_status check_dev_ptr(const void *ptr, const char *name, bool required)
+{
+    if (!ptr) {
+        if (required) return fail(PAM_ERR_INVALID_ARG, std::string(name) + " is NULL");
+        return PAM_OK;
+    }
+    if (reinterpret_cast<uintptr_t>(ptr) & 15u)
+        return fail(PAM_ERR_INVALID_ARG, std::string(name) + " is not 16-byte aligned");
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PAM_ERR_INVALID_ARG, std::string(name) + " is not a CUDA pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(PAM_ERR_INVALID_ARG, std::string(name) + " is not device memory");
+    return PAM_OK;
+}
+
+pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
+{
+    if (d->n_elem < 8 || d->n_elem > 256) return fail(PAM_ERR_INVALID_ARG, "n_elem must be in [8, 256]");
+    if (!finite_pos(d->pitch_m)) return fail(PAM_ERR_INVALID_ARG, "pitch_m must be finite and > 0");
+    if (!finite_pos(d->fs_hz)) return fail(PAM_ERR_INVALID_ARG, "fs_hz must be finite and > 0");
+    if (!finite_pos(d->c_mps)) return fail(PAM_ERR_INVALID_ARG, "c_mps must be finite and > 0");
+    if (d->n_samples < 64 || d->n_samples > 8192)
+        return fail(d->n_samples > 8192 && d->n_samples > 0 ? PAM_ERR_UNSUPPORTED : PAM_ERR_INVALID_ARG,
+                    "n_samples must be in [64, 8192]");
+    if (!is_pow2(d->n_samples))
+        return fail(PAM_ERR_UNSUPPORTED, "n_samples must be a power of two for the radix-4/2 time FFT");
+    int nx = d->nx == 0 ? d->n_elem : d->nx;
+    if (nx != d->n_elem) return fail(PAM_ERR_UNSUPPORTED, "nx must equal n_elem (lateral padding is not built)");
+    if (nx != 16 && nx != 32 && nx != 64 && nx != 128)
+        return fail(PAM_ERR_UNSUPPORTED, "lateral length nx must be 16, 32, 64 or 128");
+    if (d->nz < 1 || d->nz > 65535) return fail(PAM_ERR_INVALID_ARG, "nz must be in [1, 65535]");
+    if (!std::isfinite(d->z0_m) || d->z0_m < 0.0) return fail(PAM_ERR_INVALID_ARG, "z0_m must be finite and >= 0");
+    if (!finite_pos(d->dz_m)) return fail(PAM_ERR_INVALID_ARG, "dz_m must be finite and > 0");
+    if (d->n_apod < 1 || d->n_apod > 3) return fail(PAM_ERR_INVALID_ARG, "n_apod must be 1, 2 or 3");
+    if (!(d->eps > 0.0f) || !(d->eps <= 1.0f)) return fail(PAM_ERR_INVALID_ARG, "eps must be in (0, 1]");
+    if (d->max_frames < 1 || d->max_frames > 65535) return fail(PAM_ERR_INVALID_ARG, "max_frames must be in [1, 65535]");
+    if (d->flags & ~PAM_EVANESCENT_ZERO) return fail(PAM_ERR_INVALID_ARG, "unknown flag bits");
+
+    const int nt = d->n_samples;
+    p->bins.clear();
+    if (d->bins) {
+        if (d->n_bins < 1 || d->n_bins > 8192) return fail(PAM_ERR_INVALID_ARG, "n_bins must be in [1, 8192]");
+        for (int b = 0; b < d->n_bins; ++b) {
+            int k = d->bins[b];
+            if (k <= 0 || 2 * k >= nt) return fail(PAM_ERR_INVALID_ARG, "every bin must satisfy 0 < k < n_samples/2");
+            if (b > 0 && k <= d->bins[b - 1]) return fail(PAM_ERR_INVALID_ARG, "bins must be strictly increasing");
+            p->bins.push_back(k);
+        }
+    } else {
+        if (!std::isfinite(d->f_lo_hz) || !std::isfinite(d->f_hi_hz) || d->f_hi_hz < d->f_lo_hz)
+            return fail(PAM_ERR_INVALID_ARG, "band must satisfy f_lo_hz <= f_hi_hz (finite)");
+        for (int k = 1; 2 * k < nt; ++k) {
+            double f = (double)k * d->fs_hz / (double)nt;
+            if (f >= d->f_lo_hz && f <= d->f_hi_hz) p->bins.push_back(k);
+        }
+        if (p->bins.empty()) return fail(PAM_ERR_INVALID_ARG, "the band holds no DFT bin");
+        if (p->bins.size() > 8192) return fail(PAM_ERR_INVALID_ARG, "the band holds more than 8192 bins");
+    }
+
+    const int ne = d->n_elem, na = d->n_apod;
+    p->apod.assign((size_t)na * ne, 0.0f);
+    if (d->apod) {
+        for (int x = 0; x < na * ne; ++x) {
+            if (!std::isfinite(d->apod[x])) return fail(PAM_ERR_INVALID_ARG, "apodization weights must be finite");
+            p->apod[x] = d->apod[x];
+        }
+    } else {
+        if (d->pattern_m < 1 || d->pattern_m > ne) return fail(PAM_ERR_INVALID_ARG, "pattern_m must be in [1, n_elem]");
+        for (int q = 0; q < na; ++q)
+            for (int e = 0; e < ne; ++e)
+                p->apod[(size_t)q * ne + e] = ((e / d->pattern_m) % na == q) ? 1.0f : 0.0f;
+    }
+
+    p->d = *d;
+    p->d.bins = nullptr;
+    p->d.apod = nullptr;
+    p->d.nx = nx;
+    p->d.n_bins = (int)p->bins.size();
+    p->ne = ne;
+    p->nt = nt;
+    p->log2nt = ilog2(nt);
+    p->nx = nx;
+    p->nz = d->nz;
+    p->n_bins = (int)p->bins.size();
+    p->n_apod = na;
+    p->max_frames = d->max_frames;
+    return PAM_OK;
+}
+
+pam_status alloc_plan(pam_plan_s *p)
+{
+    const size_t ne = p->ne, nx = p->nx, nb = p->n_bins, F = p->max_frames;
+    const size_t npix = (size_t)p->nz * nx;
+    cudaError_t e = cudaSuccess;
+#define PAM_TRY(x)                                           \
+    do {                                                     \
+        e = (x);                                             \
+        if (e != cudaSuccess) {                              \
+            cudaGetLastError();                              \
+            return e == cudaErrorMemoryAllocation            \
+                       ? fail(PAM_ERR_OOM, #x)               \
+                       : cuda_fail(e, #x);                   \
+        }                                                    \
+    } while (0)
+    PAM_TRY(dalloc(&p->t.bins, nb));
+    PAM_TRY(dalloc(&p->t.apod, (size_t)p->n_apod * ne));
+    PAM_TRY(dalloc(&p->t.ones, ne));
+    PAM_TRY(dalloc(&p->t.tw_t, (size_t)p->nt));
+    PAM_TRY(dalloc(&p->t.tw_x, nx));
+    PAM_TRY(dalloc(&p->t.dds, nb * nx));
+    PAM_TRY(dalloc(&p->t.ecoef, nb * nx));
+    PAM_TRY(dalloc(&p->t.live, nb * nx));
+    PAM_TRY(dalloc(&p->t.bin_evan, nb));
+    PAM_TRY(dalloc(&p->w.S, F * nb * ne));
+    PAM_TRY(dalloc(&p->w.Q, F * nb * (size_t)p->n_apod * nx));
+    int rows = pam::prop_rows_per_cta(p->nx);
+    int row_tiles = (p->nz + rows - 1) / rows;
+    size_t target = 2 * (size_t)p->num_sms;
+    size_t split_units = (target + row_tiles - 1) / row_tiles;
+    p->w.part_units = std::max(F, split_units);
+    PAM_TRY(dalloc(&p->w.part, p->w.part_units * (size_t)pam::n_acc(p->n_apod) * npix));
+    PAM_TRY(dalloc(&p->w.rho_tmp, F * npix));
+    PAM_TRY(dalloc(&p->w.e_tmp, F * npix));
+    PAM_TRY(dalloc(&p->w.fmax, F));
+    PAM_TRY(dalloc(&p->w.status, 1));
+    PAM_TRY(cudaMemset(p->w.status, 0, sizeof(int)));
+    PAM_TRY(cudaMemcpy(p->t.bins, p->bins.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+    PAM_TRY(cudaMemcpy(p->t.apod, p->apod.data(), p->apod.size() * sizeof(float), cudaMemcpyHostToDevice));
+    std::vector<float> ones(ne, 1.0f);
+    PAM_TRY(cudaMemcpy(p->t.ones, ones.data(), ne * sizeof(float), cudaMemcpyHostToDevice));
+#undef PAM_TRY
+    return PAM_OK;
+}
+
+bool oom(cudaError_t e) { return e == cudaErrorMemoryAllocation; }
+
+void prof_release(pam_plan_s *p)
+{
+    for (cudaEvent_t ev : p->prof_ev) cudaEventDestroy(ev);
+    p->prof_ev.clear();
+    p->prof_used = 0;
+}
+
+cudaError_t prof_record(pam_plan_s *p, cudaStream_t st)
+{
+    if (!p->prof_on) return cudaSuccess;
+    if (p->prof_used == p->prof_ev.size()) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        p->prof_ev.push_back(ev);
+    }
+    return cudaEventRecord(p->prof_ev[p->prof_used++], st);
+}
+
+cudaError_t prof_begin(pam_plan_s *p, cudaStream_t st) { return prof_record(p, st); }
+cudaError_t prof_end(pam_plan_s *p, cudaStream_t st) { return prof_record(p, st); }
+
+pam_status run_xcorr(pam_plan_t p, const float *rf, int n_frames, float *image, float *rho_n,
+                     float *rho_pairs, float *image_as, cudaStream_t st)
+{
+    const size_t npix = (size_t)p->nz * p->nx;
+    const size_t fr_in = (size_t)p->ne * p->nt;
+    const int npairs = p->n_apod == 3 ? 3 : 1;
+    for (int f0 = 0; f0 < n_frames; f0 += p->max_frames) {
+        int Fc = std::min(p->max_frames, n_frames - f0);
+        cudaError_t e = pam::launch_time_fft(*p, rf + (size_t)f0 * fr_in, Fc, st);
+        if (e != cudaSuccess) return cuda_fail(e, "time FFT launch");
+        e = pam::launch_lateral(*p, Fc, p->n_apod, p->t.apod, st);
+        if (e != cudaSuccess) return cuda_fail(e, "lateral DFT launch");
+        int ns = pam::choose_split(*p, Fc);
+        if ((e = prof_begin(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
+        e = pam::launch_prop(*p, Fc, p->n_apod, ns, nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "propagate/correlate launch");
+        if ((e = prof_end(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
+        p->kernels += 5;
+        e = pam::launch_epilogue(*p, Fc, p->n_apod, ns, image + (size_t)f0 * npix,
+                                 rho_n ? rho_n + (size_t)f0 * npix : nullptr,
+                                 rho_pairs ? rho_pairs + (size_t)f0 * npairs * npix : nullptr,
+                                 image_as ? image_as + (size_t)f0 * npix : nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "epilogue launch");
+    }
+    return PAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pam_plan_desc_init(pam_plan_desc *d)
+{
+    if (!d) return;
+    std::memset(d, 0, sizeof(*d));
+    d->n_apod = 3;
+    d->pattern_m = 16;
+    d->eps = 1e-3f;
+    d->max_frames = 1;
+}
+
+pam_status pam_plan_create(const pam_plan_desc *d, pam_plan_t *out)
+{
+    if (!out) return fail(PAM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(PAM_ERR_INVALID_ARG, "descriptor is NULL");
+    pam_plan_s *p = new (std::nothrow) pam_plan_s();
+    if (!p) return fail(PAM_ERR_OOM, "host allocation of the plan failed");
+    pam_status s = validate_and_fill(d, p);
+    if (s != PAM_OK) { delete p; return s; }
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "device query"); }
+    s = alloc_plan(p);
+    if (s != PAM_OK) {
+        free_plan_memory(p);
+        delete p;
+        return s;
+    }
+    e = pam::prepare_kernels(*p);
+    if (e == cudaSuccess) e = pam::launch_tables(*p, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        free_plan_memory(p);
+        delete p;
+        return cuda_fail(e, "plan tables");
+    }
+    *out = p;
+    return PAM_OK;
+}
+
+void pam_destroy(pam_plan_t p)
+{
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    prof_release(p);
+    free_plan_memory(p);
+    cudaSetDevice(cur);
+    delete p;
+}
+
+int pam_plan_bins(pam_plan_t p, int *bins_out)
+{
+    if (!p) return 0;
+    if (bins_out) std::memcpy(bins_out, p->bins.data(), p->bins.size() * sizeof(int));
+    return p->n_bins;
+}
+
+int pam_plan_apod(pam_plan_t p, float *apod_out)
+{
+    if (!p) return 0;
+    if (apod_out) std::memcpy(apod_out, p->apod.data(), p->apod.size() * sizeof(float));
+    return p->n_apod;
+}
+
+pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod_index,
+                           float *energy, float *fields, void *stream)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (n_frames < 0) return fail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
+    if (apod_index < -1 || apod_index >= p->n_apod) return fail(PAM_ERR_INVALID_ARG, "apod_index out of range");
+    if (n_frames == 0) return PAM_OK;
+    pam_status s;
+    if ((s = check_dev_ptr(rf, "rf", true)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(energy, "energy", true)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(fields, "fields", false)) != PAM_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const float *apod = apod_index < 0 ? p->t.ones : p->t.apod + (size_t)apod_index * p->ne;
+    const size_t npix = (size_t)p->nz * p->nx;
+    const size_t fr_in = (size_t)p->ne * p->nt;
+    for (int f0 = 0; f0 < n_frames; f0 += p->max_frames) {
+        int Fc = std::min(p->max_frames, n_frames - f0);
+        cudaError_t e = pam::launch_time_fft(*p, rf + (size_t)f0 * fr_in, Fc, st);
+        if (e != cudaSuccess) return cuda_fail(e, "time FFT launch");
+        e = pam::launch_lateral(*p, Fc, 1, apod, st);
+        if (e != cudaSuccess) return cuda_fail(e, "lateral DFT launch");
+        int ns = pam::choose_split(*p, Fc);
+        float *fl = fields ? fields + (size_t)f0 * p->n_bins * npix * 2 : nullptr;
+        if ((e = prof_begin(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
+        e = pam::launch_prop(*p, Fc, 1, ns, fl, st);
+        if (e != cudaSuccess) return cuda_fail(e, "propagate launch");
+        if ((e = prof_end(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
+        p->kernels += 4;
+        e = pam::launch_epilogue(*p, Fc, 1, ns, energy + (size_t)f0 * npix, nullptr, nullptr, nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "epilogue launch");
+    }
+    return PAM_OK;
+}
+
+pam_status pam_as_tax(pam_plan_t p, const float *rf, int n_frames, float *image_tax,
+                      float *rho_n, float *rho_pairs, float *image_as, void *stream)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (p->n_apod != 3) return fail(PAM_ERR_INVALID_ARG, "pam_as_tax needs a plan with n_apod == 3");
+    if (n_frames < 0) return fail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
+    if (n_frames == 0) return PAM_OK;
+    pam_status s;
+    if ((s = check_dev_ptr(rf, "rf", true)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(image_tax, "image_tax", true)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(rho_n, "rho_n", false)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(rho_pairs, "rho_pairs", false)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(image_as, "image_as", false)) != PAM_OK) return s;
+    return run_xcorr(p, rf, n_frames, image_tax, rho_n, rho_pairs, image_as, static_cast<cudaStream_t>(stream));
+}
+
+pam_status pam_as_dax(pam_plan_t p, const float *rf, int n_frames, float *image_dax,
+                      float *rho_n, float *rho_pair, float *image_as, void *stream)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (p->n_apod != 2) return fail(PAM_ERR_INVALID_ARG, "pam_as_dax needs a plan with n_apod == 2");
+    if (n_frames < 0) return fail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
+    if (n_frames == 0) return PAM_OK;
+    pam_status s;
+    if ((s = check_dev_ptr(rf, "rf", true)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(image_dax, "image_dax", true)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(rho_n, "rho_n", false)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(rho_pair, "rho_pair", false)) != PAM_OK) return s;
+    if ((s = check_dev_ptr(image_as, "image_as", false)) != PAM_OK) return s;
+    return run_xcorr(p, rf, n_frames, image_dax, rho_n, rho_pair, image_as, static_cast<cudaStream_t>(stream));
+}
+
+pam_status pam_as_xcorr_host(pam_plan_t p, const float *rf_host, int n_frames, float *image_host,
+                             float *rho_n_host, void *stream)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (p->n_apod < 2) return fail(PAM_ERR_INVALID_ARG, "pam_as_xcorr_host needs n_apod of 2 or 3");
+    if (n_frames < 0) return fail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
+    if (n_frames == 0) return PAM_OK;
+    if (!rf_host || !image_host) return fail(PAM_ERR_INVALID_ARG, "rf_host and image_host are required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t npix = (size_t)p->nz * p->nx;
+    const size_t fr_in = (size_t)p->ne * p->nt;
+    const size_t F = p->max_frames;
+    cudaError_t e;
+    if (!p->w.rf_stage) {
+        if ((e = dalloc(&p->w.rf_stage, F * fr_in)) != cudaSuccess ||
+            (e = dalloc(&p->w.img_stage, F * npix)) != cudaSuccess ||
+            (e = dalloc(&p->w.rho_stage, F * npix)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(oom(e) ? PAM_ERR_OOM : PAM_ERR_CUDA, "staging allocation failed");
+        }
+    }
+    for (int f0 = 0; f0 < n_frames; f0 += p->max_frames) {
+        int Fc = std::min(p->max_frames, n_frames - f0);
+        e = cudaMemcpyAsync(p->w.rf_stage, rf_host + (size_t)f0 * fr_in, Fc * fr_in * sizeof(float),
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "rf upload");
+        pam_status s = run_xcorr(p, p->w.rf_stage, Fc, p->w.img_stage, rho_n_host ? p->w.rho_stage : nullptr,
+                                 nullptr, nullptr, st);
+        if (s != PAM_OK) return s;
+        e = cudaMemcpyAsync(image_host + (size_t)f0 * npix, p->w.img_stage, Fc * npix * sizeof(float),
+                            cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "image download");
+        if (rho_n_host) {
+            e = cudaMemcpyAsync(rho_n_host + (size_t)f0 * npix, p->w.rho_stage, Fc * npix * sizeof(float),
+                                cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return cuda_fail(e, "rho_n download");
+        }
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    return PAM_OK;
+}
+
+pam_status pam_sync(pam_plan_t p, void *stream)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    int status = 0;
+    e = cudaMemcpy(&status, p->w.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (status != 0) {
+        cudaMemset(p->w.status, 0, sizeof(int));
+        return fail(PAM_ERR_TIMEOUT, "a kernel reported an expired bounded wait");
+    }
+    return PAM_OK;
+}
+
+pam_status pam_profile_enable(pam_plan_t p, int on)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "synchronise");
+    p->prof_used = 0;
+    p->kernels = 0;
+    p->prof_on = on != 0;
+    if (!p->prof_on) prof_release(p);
+    return PAM_OK;
+}
+
+pam_status pam_profile_read(pam_plan_t p, double *prop_ms, long long *prop_launches, long long *kernel_launches)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < p->prof_used; i += 2) {
+        cudaError_t e = cudaEventSynchronize(p->prof_ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "event synchronise");
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, p->prof_ev[i], p->prof_ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "event elapsed time");
+        total += ms;
+    }
+    if (prop_ms) *prop_ms = total;
+    if (prop_launches) *prop_launches = (long long)(p->prof_used / 2);
+    if (kernel_launches) *kernel_launches = p->kernels;
+    p->prof_used = 0;
+    p->kernels = 0;
+    return PAM_OK;
+}
+
+const char *pam_status_string(pam_status s)
+{
+    switch (s) {
+    case PAM_OK: return "PAM_OK";
+    case PAM_ERR_INVALID_ARG: return "PAM_ERR_INVALID_ARG";
+    case PAM_ERR_UNSUPPORTED: return "PAM_ERR_UNSUPPORTED";
+    case PAM_ERR_OOM: return "PAM_ERR_OOM";
+    case PAM_ERR_CUDA: return "PAM_ERR_CUDA";
+    case PAM_ERR_TIMEOUT: return "PAM_ERR_TIMEOUT";
+    case PAM_ERR_NUMERIC: return "PAM_ERR_NUMERIC";
+    }
+    return "PAM_ERR_UNKNOWN";
+}
+
+const char *pam_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// pam_internal.h -- plan object and kernel launchers shared by the libpam
+// translation units. Not part of the public ABI (that is include/pam.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pam.h"
+
+namespace pam {
+
+// Rows of the depth grid handled by one CTA of the fused propagate-and-correlate
+// kernel for a lateral length nx (8 warps; 2*nx/16 lanes per row).
+int prop_rows_per_cta(int nx);
+
+// Accumulators per pixel: |p1|^2 (AS), + |p2|^2, Re p1*p2 (DAX),
+// + |p3|^2, Re p2*p3, Re p3*p1 (TAX).
+inline int n_acc(int n_apod) { return n_apod == 1 ? 1 : (n_apod == 2 ? 3 : 6); }
+
+struct Workspace {
+    float2 *S = nullptr;        // [max_frames][n_bins][n_elem]      selected time bins
+    float2 *Q = nullptr;        // [max_frames][n_bins][napq][nx]    apodized lateral spectra / nx
+    float *part = nullptr;      // [units][n_acc][nz][nx]            per-split accumulator partials
+    size_t part_units = 0;
+    float *rho_tmp = nullptr;   // [max_frames][nz][nx]              rho before normalisation
+    float *e_tmp = nullptr;     // [max_frames][nz][nx]              sum_k |sum_q p_q|^2
+    unsigned *fmax = nullptr;   // [max_frames]                      max rho bits per frame
+    int *status = nullptr;      // device status word
+    // host-buffer entry point staging (allocated on first use)
+    float *rf_stage = nullptr, *img_stage = nullptr, *rho_stage = nullptr;
+};
+
+struct Tables {
+    int *bins = nullptr;          // [n_bins]
+    float *apod = nullptr;        // [n_apod][n_elem]
+    float *ones = nullptr;        // [n_elem]
+    float2 *tw_t = nullptr;       // [nt]   exp(-2 pi i m / nt)
+    float2 *tw_x = nullptr;       // [nx]   exp(-2 pi i m / nx)
+    ulonglong2 *dds = nullptr;    // [n_bins][nx] fixed-point phase (turns * 2^64): anchor at z0, step per row
+    float *ecoef = nullptr;       // [n_bins][nx] -kappa*log2(e) for evanescent components, else 0
+    float *live = nullptr;        // [n_bins][nx] 1, or 0 for dropped evanescent components
+    int *bin_evan = nullptr;      // [n_bins] 1 if any live evanescent component in the bin
+};
+
+}  // namespace pam
+
+struct pam_plan_s {
+    pam_plan_desc d{};
+    int device = 0, num_sms = 0;
+    int ne = 0, nt = 0, log2nt = 0, nx = 0, nz = 0, n_bins = 0, n_apod = 0, max_frames = 1;
+    std::vector<int> bins;
+    std::vector<float> apod;
+    pam::Tables t;
+    pam::Workspace w;
+    // measurement hooks (pam_profile_*)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;  // pairs around propagate-and-correlate launches
+    size_t prof_used = 0;              // events recorded since the last read
+    long long kernels = 0;             // libpam kernel launches since the last read
+};
+
+namespace pam {
+
+// Launchers (all asynchronous on `st`). Each returns cudaGetLastError().
+cudaError_t launch_tables(const pam_plan_s &p, cudaStream_t st);
+cudaError_t launch_time_fft(const pam_plan_s &p, const float *rf, int n_frames, cudaStream_t st);
+cudaError_t launch_lateral(const pam_plan_s &p, int n_frames, int napq, const float *apod, cudaStream_t st);
+cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields, cudaStream_t st);
+cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, float *out_main,
+                            float *rho_n, float *rho_pairs, float *image_as, cudaStream_t st);
+cudaError_t prepare_kernels(const pam_plan_s &p);
+int choose_split(const pam_plan_s &p, int n_frames);
+
+}  // namespace pam

@@ -1,0 +1,285 @@
+"""Python binding of libpam (C ABI in ``include/pam.h``).
+
+This module only marshals arguments. It passes tensor data pointers and the
+current CUDA stream handle to the library, and every step of the
+angular-spectrum path runs in the library's CUDA kernels. PyTorch is used for
+device memory and streams only. There is no CPU fallback: when the library
+or a GPU is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+PAM_OK = 0
+PAM_EVANESCENT_ZERO = 0x1
+_STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_UNSUPPORTED", 3: "PAM_ERR_OOM",
+           4: "PAM_ERR_CUDA", 5: "PAM_ERR_TIMEOUT", 6: "PAM_ERR_NUMERIC"}
+
+
+class PamError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class PlanDesc(ctypes.Structure):
+    """Mirror of ``pam_plan_desc``."""
+    _fields_ = [
+        ("n_elem", ctypes.c_int), ("pitch_m", ctypes.c_double), ("fs_hz", ctypes.c_double),
+        ("c_mps", ctypes.c_double), ("n_samples", ctypes.c_int), ("nx", ctypes.c_int),
+        ("nz", ctypes.c_int), ("z0_m", ctypes.c_double), ("dz_m", ctypes.c_double),
+        ("f_lo_hz", ctypes.c_double), ("f_hi_hz", ctypes.c_double),
+        ("bins", ctypes.POINTER(ctypes.c_int)), ("n_bins", ctypes.c_int),
+        ("n_apod", ctypes.c_int), ("apod", ctypes.POINTER(ctypes.c_float)), ("pattern_m", ctypes.c_int),
+        ("eps", ctypes.c_float), ("flags", ctypes.c_uint), ("max_frames", ctypes.c_int),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# Every symbol include/pam.h declares, with (restype, argtypes).
+_VP = ctypes.c_void_p
+_SIGS = {
+    "pam_plan_desc_init": (None, [ctypes.POINTER(PlanDesc)]),
+    "pam_plan_create": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(_VP)]),
+    "pam_destroy": (None, [_VP]),
+    "pam_plan_bins": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "pam_plan_apod": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "pam_as_backprop": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "pam_as_tax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
+    "pam_as_dax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
+    "pam_as_xcorr_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
+    "pam_sync": (ctypes.c_int, [_VP, _VP]),
+    "pam_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pam_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                        ctypes.POINTER(ctypes.c_longlong)]),
+    "pam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pam_last_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Open libpam.so (building it first when absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libpam.so is missing at {path}; run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != PAM_OK:
+        msg = load().pam_last_error().decode(errors="replace")
+        raise PamError(status, msg)
+
+
+def _require_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libpam needs a CUDA GPU; no CPU fallback exists")
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _require_cuda()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _dptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+class Plan:
+    """An AS / AS-DAX / AS-TAX plan on the current CUDA device.
+
+    Geometry is given in SI units. Either ``bins`` (explicit DFT bin indices)
+    or the band ``(f_lo, f_hi)`` selects Omega. ``apod`` is [n_apod][n_elem]
+    or None for Pattern-``pattern_m``."""
+
+    def __init__(self, n_elem: int, pitch: float, fs: float, c: float, n_samples: int, nz: int,
+                 z0: float, dz: float, bins: Optional[Sequence[int]] = None, f_lo: float = 0.0,
+                 f_hi: float = 0.0, n_apod: int = 3, apod=None, pattern_m: int = 16, eps: float = 1e-3,
+                 evanescent_zero: bool = False, max_frames: int = 1, nx: int = 0):
+        _require_cuda()
+        L = load()
+        d = PlanDesc()
+        L.pam_plan_desc_init(ctypes.byref(d))
+        d.n_elem, d.pitch_m, d.fs_hz, d.c_mps = int(n_elem), float(pitch), float(fs), float(c)
+        d.n_samples, d.nx, d.nz = int(n_samples), int(nx), int(nz)
+        d.z0_m, d.dz_m, d.f_lo_hz, d.f_hi_hz = float(z0), float(dz), float(f_lo), float(f_hi)
+        self._bins_keep = None
+        self._apod_keep = None
+        if bins is not None:
+            self._bins_keep = np.ascontiguousarray(np.asarray(bins, dtype=np.int32))
+            d.bins = self._bins_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+            d.n_bins = int(self._bins_keep.size)
+        d.n_apod = int(n_apod)
+        if apod is not None:
+            self._apod_keep = np.ascontiguousarray(np.asarray(apod, dtype=np.float32))
+            d.apod = self._apod_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        d.pattern_m, d.eps = int(pattern_m), float(eps)
+        d.flags = PAM_EVANESCENT_ZERO if evanescent_zero else 0
+        d.max_frames = int(max_frames)
+        h = _VP()
+        _check(L.pam_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.n_elem, self.n_samples, self.nz, self.n_apod = int(n_elem), int(n_samples), int(nz), int(n_apod)
+        self.nx = self.n_elem if not nx else int(nx)
+        self.max_frames = int(max_frames)
+        self.bins = self._query_bins()
+        self.apod = self._query_apod()
+
+    @classmethod
+    def from_workload(cls, w, n_apod: Optional[int] = None, max_frames: int = 1, **kw) -> "Plan":
+        """Plan for a :class:`paper_2412_02413_gb300.synth.Workload`."""
+        return cls(n_elem=w.n_elem, pitch=w.pitch, fs=w.fs, c=w.c, n_samples=w.nt, nz=w.nz, z0=w.z0,
+                   dz=w.dz, bins=w.bins(), n_apod=w.n_apod if n_apod is None else n_apod,
+                   pattern_m=w.pattern_m, max_frames=max_frames, **kw)
+
+    def _query_bins(self) -> np.ndarray:
+        L = load()
+        n = L.pam_plan_bins(self._h, None)
+        out = np.zeros(n, dtype=np.int32)
+        L.pam_plan_bins(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return out
+
+    def _query_apod(self) -> np.ndarray:
+        L = load()
+        out = np.zeros((self.n_apod, self.n_elem), dtype=np.float32)
+        L.pam_plan_apod(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        return out
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n_bins(self) -> int:
+        return int(self.bins.size)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pam_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------- calls --
+    def _check_rf(self, rf):
+        torch = _require_cuda()
+        if not isinstance(rf, torch.Tensor) or not rf.is_cuda or rf.dtype != torch.float32:
+            raise TypeError("rf must be a float32 CUDA tensor")
+        if rf.dim() == 2:
+            rf = rf.unsqueeze(0)
+        if tuple(rf.shape[1:]) != (self.n_elem, self.n_samples):
+            raise ValueError(f"rf must be [F][{self.n_elem}][{self.n_samples}], got {tuple(rf.shape)}")
+        return rf.contiguous()
+
+    def _empty(self, *shape):
+        torch = _require_cuda()
+        return torch.empty(shape, dtype=torch.float32, device="cuda")
+
+    def as_backprop(self, rf, apod_index: int = -1, fields: bool = False, out=None, stream=None):
+        """Eq. 3 energy map [F][nz][nx] (and the fields [F][n_bins][nz][nx] complex64 if asked)."""
+        torch = _require_cuda()
+        rf = self._check_rf(rf)
+        F = rf.shape[0]
+        energy = self._empty(F, self.nz, self.nx) if out is None else out
+        fl = self._empty(F, self.n_bins, self.nz, self.nx, 2) if fields else None
+        _check(load().pam_as_backprop(self._h, _dptr(rf), F, int(apod_index), _dptr(energy), _dptr(fl),
+                                      _stream_ptr(stream)))
+        if fields:
+            return energy, torch.view_as_complex(fl)
+        return energy
+
+    def as_tax(self, rf, rho_n: bool = True, rho_pairs: bool = False, image_as: bool = False,
+               outs: Optional[dict] = None, stream=None) -> dict:
+        """AS-TAX (Eq. 10-11). Returns a dict of [F][nz][nx] maps (rho_pairs [F][3][nz][nx])."""
+        if self.n_apod != 3:
+            raise ValueError("as_tax needs a plan with three apodizations")
+        return self._xcorr(load().pam_as_tax, 3, rf, rho_n, rho_pairs, image_as, outs, stream)
+
+    def as_dax(self, rf, rho_n: bool = True, rho_pairs: bool = False, image_as: bool = False,
+               outs: Optional[dict] = None, stream=None) -> dict:
+        """AS-DAX (Eq. 4-5)."""
+        if self.n_apod != 2:
+            raise ValueError("as_dax needs a plan with two apodizations")
+        return self._xcorr(load().pam_as_dax, 1, rf, rho_n, rho_pairs, image_as, outs, stream)
+
+    def _xcorr(self, fn, npairs, rf, rho_n, rho_pairs, image_as, outs, stream):
+        rf = self._check_rf(rf)
+        F = rf.shape[0]
+        o = dict(outs or {})
+        if "image" not in o:
+            o["image"] = self._empty(F, self.nz, self.nx)
+        if rho_n and "rho_n" not in o:
+            o["rho_n"] = self._empty(F, self.nz, self.nx)
+        if rho_pairs and "rho_pairs" not in o:
+            o["rho_pairs"] = self._empty(F, npairs, self.nz, self.nx)
+        if image_as and "image_as" not in o:
+            o["image_as"] = self._empty(F, self.nz, self.nx)
+        _check(fn(self._h, _dptr(rf), F, _dptr(o["image"]), _dptr(o.get("rho_n")), _dptr(o.get("rho_pairs")),
+                  _dptr(o.get("image_as")), _stream_ptr(stream)))
+        return o
+
+    def as_xcorr_host(self, rf_host: np.ndarray, image_out: np.ndarray, rho_n_out: Optional[np.ndarray] = None,
+                      stream=None):
+        """AS-TAX / AS-DAX from host memory through ``pam_as_xcorr_host``.
+        ``rf_host`` [F][n_elem][n_samples] float32, outputs [F][nz][nx] float32
+        (pinned buffers make the copies faster). Returns after the results are
+        in the host arrays."""
+        for a in (rf_host, image_out) + ((rho_n_out,) if rho_n_out is not None else ()):
+            if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+                raise TypeError("host buffers must be C-contiguous float32")
+        F = rf_host.shape[0] if rf_host.ndim == 3 else 1
+        _check(load().pam_as_xcorr_host(self._h, rf_host.ctypes.data, F, image_out.ctypes.data,
+                                        None if rho_n_out is None else rho_n_out.ctypes.data,
+                                        _stream_ptr(stream)))
+
+    def profile_enable(self, on: bool = True):
+        """Record CUDA events around each propagate-and-correlate launch."""
+        _check(load().pam_profile_enable(self._h, int(bool(on))))
+
+    def profile_read(self):
+        """(summed prop-kernel ms, prop launches, all libpam kernel launches); clears them."""
+        ms, n, k = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load().pam_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)))
+        return ms.value, n.value, k.value
+
+    def sync(self, stream=None):
+        _check(load().pam_sync(self._h, _stream_ptr(stream)))
+
+
+def status_string(s: int) -> str:
+    return load().pam_status_string(int(s)).decode()

@@ -191,18 +191,21 @@ def make_frame(w: Workload, frame: int = 0, sources: Optional[List[Source]] = No
     rf = np.zeros((ne, nt), dtype=np.float64)
     L = 2 * nt
     fL = np.fft.rfftfreq(L, 1.0 / w.fs)
+    spec = np.zeros((ne, fL.size), dtype=np.complex128)   # summed delayed broadband spectra
     for src in sources:
         freqs, amps, phases, noise = source_signal_spectrum(src, w, rng, L)
         r = np.sqrt((xe - src.x) ** 2 + src.z ** 2)
         tau = r / w.c
         gain = 10e-3 / r
-        for e in range(ne):
-            if freqs.size:
-                ph = 2 * np.pi * np.outer(t - tau[e], freqs) + phases
-                rf[e] += gain[e] * (np.sin(ph) @ amps)
+        if freqs.size:
+            # sin(2 pi f (t - tau_e) + phi) = cos(phi_e) sin(2 pi f t) + sin(phi_e) cos(2 pi f t)
+            phi_e = phases[None, :] - 2 * np.pi * freqs[None, :] * tau[:, None]        # [ne][H]
+            wt = 2 * np.pi * np.outer(freqs, t)                                         # [H][nt]
+            rf += gain[:, None] * ((np.cos(phi_e) * amps) @ np.sin(wt) + (np.sin(phi_e) * amps) @ np.cos(wt))
         nspec = np.fft.rfft(noise)
-        delayed = np.fft.irfft(nspec[None, :] * np.exp(-2j * np.pi * fL[None, :] * tau[:, None]), L, axis=1)
-        rf += gain[:, None] * delayed[:, :nt]
+        band = np.nonzero(nspec)[0]
+        spec[:, band] += (gain[:, None] * nspec[band][None, :]) * np.exp(-2j * np.pi * fL[band][None, :] * tau[:, None])
+    rf += np.fft.irfft(spec, L, axis=1)[:, :nt]
     p = float(np.mean(rf ** 2))
     nrng = np.random.default_rng(seed + 1)
     if w.snr_db is not None and p > 0:

@@ -1,0 +1,111 @@
+"""The C ABI without a GPU: libpam builds, loads, exports every symbol that
+include/pam.h declares, and rejects bad descriptors before it touches a
+device. These tests make no compute call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2412_02413_gb300 import build as pam_build
+from paper_2412_02413_gb300 import pam
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pam.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pam_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pam_build.build()
+    return pam.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("pam_plan_create", "pam_as_backprop", "pam_as_tax", "pam_destroy"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_symbol():
+    assert set(pam._SIGS) == set(declared_functions())
+
+
+def test_status_strings(lib):
+    assert lib.pam_status_string(0) == b"PAM_OK"
+    assert lib.pam_status_string(1) == b"PAM_ERR_INVALID_ARG"
+    assert lib.pam_status_string(5) == b"PAM_ERR_TIMEOUT"
+
+
+def _desc(lib, **kw):
+    d = pam.PlanDesc()
+    lib.pam_plan_desc_init(ctypes.byref(d))
+    d.n_elem, d.pitch_m, d.fs_hz, d.c_mps = 64, 0.3e-3, 20e6, 1540.0
+    d.n_samples, d.nz, d.z0_m, d.dz_m = 1024, 128, 10e-3, 0.3e-3
+    d.f_lo_hz, d.f_hi_hz = 1e6, 7e6
+    d.pattern_m = 8
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def _create(lib, d):
+    h = ctypes.c_void_p(123)
+    s = lib.pam_plan_create(ctypes.byref(d), ctypes.byref(h))
+    return s, h
+
+
+def test_desc_defaults(lib):
+    d = pam.PlanDesc()
+    lib.pam_plan_desc_init(ctypes.byref(d))
+    assert d.n_apod == 3 and d.pattern_m == 16 and abs(d.eps - 1e-3) < 1e-9 and d.max_frames == 1
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("n_elem", 4, 1), ("n_elem", 300, 1), ("pitch_m", 0.0, 1), ("fs_hz", -1.0, 1),
+    ("c_mps", float("nan"), 1), ("n_samples", 1000, 2), ("n_samples", 32, 1), ("n_samples", 16384, 2),
+    ("nz", 0, 1), ("z0_m", -1e-3, 1), ("dz_m", 0.0, 1), ("n_apod", 4, 1), ("eps", 0.0, 1),
+    ("eps", 1.5, 1), ("max_frames", 0, 1), ("flags", 0x10, 1), ("nx", 128, 2), ("pattern_m", 0, 1),
+    ("f_lo_hz", 9e6, 1),
+])
+def test_bad_descriptor_is_rejected(lib, field, value, status):
+    d = _desc(lib, **{field: value})
+    s, h = _create(lib, d)
+    assert s == status, (field, value, s, lib.pam_last_error())
+    assert h.value is None
+    assert lib.pam_last_error()
+
+
+def test_bad_explicit_bins(lib):
+    for bins in ([0, 5], [5, 5], [9, 4], [10, 512]):
+        arr = (ctypes.c_int * len(bins))(*bins)
+        d = _desc(lib, bins=ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)), n_bins=len(bins))
+        s, h = _create(lib, d)
+        assert s == 1, bins
+
+
+def test_non_finite_apodization(lib):
+    w = (ctypes.c_float * (3 * 64))(*([1.0] * 191 + [float("inf")]))
+    d = _desc(lib, apod=ctypes.cast(w, ctypes.POINTER(ctypes.c_float)))
+    s, _ = _create(lib, d)
+    assert s == 1
+
+
+def test_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.pam_plan_create(None, ctypes.byref(h)) == 1
+    lib.pam_destroy(None)
+    assert lib.pam_as_tax(None, None, 1, None, None, None, None, None) == 1
+    assert lib.pam_as_backprop(None, None, 1, -1, None, None, None) == 1
+    assert lib.pam_sync(None, None) == 1
+    assert lib.pam_plan_bins(None, None) == 0

@@ -1,0 +1,291 @@
+"""libpam (CUDA, FP32) against the FP64 oracle on the same seeded inputs,
+called through the C ABI via the Python binding. The tests cover:
+* small grids spanning several CTA tiles with ragged tails;
+* both full workloads (64-element and 128-element);
+* multi-frame batching;
+* AS-DAX and the evanescent-zero flag;
+* edge cases: zero input, one bin, one row, the largest nt;
+* error handling.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import NCC_TOL, REL_L2_TOL, compare_xcorr, geometry_of, peak, rel_l2
+from paper_2412_02413_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C = 1540.0
+
+
+def _pam():
+    from paper_2412_02413_gb300 import pam
+    return pam
+
+
+def _tiny(ne, nt, nz, bins=None, fs=20e6, pattern_m=2, z0=4e-3, dz=0.45e-3, f_lo=1e6, f_hi=8e6):
+    w = synth.Workload(name="t", n_elem=ne, pitch=0.3e-3, fs=fs, nt=nt, c=C, nz=nz, z_first=z0,
+                       z_last=z0 + (nz - 1) * dz if nz > 1 else z0 + dz, f_lo=f_lo, f_hi=f_hi,
+                       n_bins=bins, pattern_m=pattern_m)
+    if nz == 1:
+        w.z_last = z0 + dz  # keeps dz positive; only row 0 is imaged
+    return w
+
+
+def _plan(w, n_apod=3, **kw):
+    pam = _pam()
+    dz = w.dz if w.nz > 1 else (w.z_last - w.z_first)
+    return pam.Plan(n_elem=w.n_elem, pitch=w.pitch, fs=w.fs, c=w.c, n_samples=w.nt, nz=w.nz, z0=w.z0, dz=dz,
+                    bins=w.bins(), n_apod=n_apod, pattern_m=w.pattern_m, **kw)
+
+
+def _geom(w, **kw):
+    dz = w.dz if w.nz > 1 else (w.z_last - w.z_first)
+    return oracle.Geometry(w.n_elem, w.nt, w.fs, w.c, w.pitch, w.nz, w.z0, dz, w.bins(), **kw)
+
+
+def _run_tax(plan, rf):
+    return plan.as_tax(torch.from_numpy(np.ascontiguousarray(rf)).cuda(), rho_n=True, rho_pairs=True,
+                       image_as=True)
+
+
+# ------------------------------------------------------------- small grids --
+@pytest.mark.parametrize("ne,nt,nz,nbins", [
+    (16, 128, 7, None),     # one CTA tile (128 rows) with a short tail
+    (32, 256, 70, None),    # 64 rows per CTA: two tiles, ragged
+    (64, 512, 45, None),    # 32 rows per CTA: two tiles, ragged
+    (128, 256, 37, 10),     # 16 rows per CTA: three tiles, ragged
+])
+def test_small_tax_parity(ne, nt, nz, nbins):
+    w = _tiny(ne, nt, nz, bins=nbins)
+    rf = synth.random_rf(ne, nt, seed=100 + ne)
+    plan = _plan(w)
+    assert np.array_equal(plan.apod, oracle.pattern(ne, 3, w.pattern_m).astype(np.float32))
+    assert np.array_equal(plan.bins, w.bins())
+    out = _run_tax(plan, rf)
+    torch.cuda.synchronize()
+    orc = oracle.as_tax(_geom(w), rf, oracle.pattern(ne, 3, w.pattern_m))
+    compare_xcorr(out, orc, check_peak=False)
+
+
+@pytest.mark.parametrize("apod_index", [-1, 1])
+def test_backprop_energy_and_fields(apod_index):
+    w = _tiny(16, 128, 9)
+    rf = synth.random_rf(16, 128, seed=7)
+    plan = _plan(w)
+    e, fl = plan.as_backprop(torch.from_numpy(rf).cuda(), apod_index=apod_index, fields=True)
+    torch.cuda.synchronize()
+    a = None if apod_index < 0 else oracle.pattern(16, 3, 2)[apod_index]
+    g = _geom(w)
+    want_f = oracle.fields(g, rf, a)
+    want_e = oracle.as_backprop(g, rf, a)
+    got_f = fl[0].cpu().numpy()
+    assert rel_l2(np.abs(got_f), np.abs(want_f)) < REL_L2_TOL
+    assert np.max(np.abs(got_f - want_f)) / np.max(np.abs(want_f)) < 1e-5
+    assert rel_l2(e[0].cpu().numpy(), want_e) < REL_L2_TOL
+
+
+def test_gpu_fields_obey_composition():
+    """F_x of the GPU field at row j+m equals F_x at row j times exp(i kz m dz)
+    for every propagating component (Eq. 2 composes)."""
+    w = _tiny(32, 256, 12, z0=2e-3, dz=0.6e-3)
+    rf = synth.random_rf(32, 256, seed=9)
+    plan = _plan(w)
+    _, fl = plan.as_backprop(torch.from_numpy(rf).cuda(), fields=True)
+    F = fl[0].cpu().numpy().astype(np.complex128)
+    worst = 0.0
+    for b, k in enumerate(plan.bins):
+        kx, kz = oracle.kz(k * w.fs / w.nt, C, w.pitch, w.n_elem)
+        prop = np.abs(kz.imag) == 0
+        P0 = np.fft.fft(F[b, 2])
+        P1 = np.fft.fft(F[b, 9])
+        pred = P0 * np.exp(1j * kz * 7 * w.dz)
+        scale = np.max(np.abs(P0))
+        worst = max(worst, float(np.max(np.abs(P1[prop] - pred[prop])) / scale))
+    assert worst < 1e-5, worst
+
+
+# ---------------------------------------------------------- full workloads --
+@pytest.fixture(scope="module")
+def w1_frames():
+    w = synth.workload(1)
+    frames = [synth.make_frame(w, f) for f in range(3)]
+    g = geometry_of(w)
+    A = oracle.pattern(w.n_elem, 3, w.pattern_m)
+    orc = [oracle.as_tax(g, rf, A) for rf, _ in frames]
+    return w, frames, orc
+
+
+def test_workload1_parity(w1_frames):
+    w, frames, orc = w1_frames
+    plan = _pam().Plan.from_workload(w)
+    for f in range(2):
+        out = _run_tax(plan, frames[f][0])
+        m = compare_xcorr(out, orc[f])
+        assert m["peak_margin"] > 10 * REL_L2_TOL, m
+
+
+def test_workload1_batched_frames(w1_frames):
+    """Three frames in one call with max_frames = 2 (two kernel batches)."""
+    w, frames, orc = w1_frames
+    plan = _pam().Plan.from_workload(w, max_frames=2)
+    rf = np.stack([fr[0] for fr in frames])
+    out = _run_tax(plan, rf)
+    for f in range(3):
+        compare_xcorr(out, orc[f], f=f)
+
+
+@pytest.fixture(scope="module")
+def w2_frame():
+    w = synth.workload(2)
+    rf, src = synth.make_frame(w, 0)
+    orc = oracle.as_tax(geometry_of(w), rf, oracle.pattern(w.n_elem, 3, w.pattern_m))
+    return w, rf, src, orc
+
+
+def test_workload2_parity(w2_frame):
+    """The 128-element, 128 x 512, 300-bin frame in the one-frame launch
+    configuration that bench.py times."""
+    w, rf, src, orc = w2_frame
+    plan = _pam().Plan.from_workload(w, max_frames=1)
+    out = _run_tax(plan, rf)
+    m = compare_xcorr(out, orc)
+    assert m["peak_margin"] > 10 * REL_L2_TOL, m
+    jz, ix = m["peak"]
+    assert any(abs(ix - s.ix) <= 1 and abs(jz - s.iz) <= 2 for s in src), (m["peak"], src)
+
+
+def test_workload2_backprop_matches_image_as(w2_frame):
+    """Eq. 3 full-aperture energy equals the summed-aperture energy of the TAX
+    call (Pattern-16 masks sum to one)."""
+    w, rf, src, orc = w2_frame
+    plan = _pam().Plan.from_workload(w)
+    e = plan.as_backprop(torch.from_numpy(rf).cuda())
+    assert rel_l2(e[0].cpu().numpy(), orc["image_as"]) < REL_L2_TOL
+
+
+# ----------------------------------------------------------------- variants --
+def test_dax_parity(w1_frames):
+    w, frames, _ = w1_frames
+    pam = _pam()
+    plan = pam.Plan.from_workload(w, n_apod=2)
+    rf = frames[0][0]
+    out = plan.as_dax(torch.from_numpy(rf).cuda(), rho_n=True, rho_pairs=True, image_as=True)
+    orc = oracle.as_xcorr(geometry_of(w), rf, oracle.pattern(w.n_elem, 2, w.pattern_m))
+    compare_xcorr(out, orc)
+
+
+def test_evanescent_zero_parity():
+    w = _tiny(32, 256, 20, f_lo=0.3e6, f_hi=4e6)
+    rf = synth.random_rf(32, 256, seed=21)
+    plan = _plan(w, evanescent_zero=True)
+    out = _run_tax(plan, rf)
+    orc = oracle.as_tax(_geom(w, evanescent_zero=True), rf, oracle.pattern(32, 3, 2))
+    compare_xcorr(out, orc, check_peak=False)
+
+
+def test_identical_apertures_give_unit_ncc():
+    w = _tiny(64, 512, 40)
+    rf = synth.random_rf(64, 512, seed=22)
+    plan = _plan(w, apod=np.ones((3, 64), np.float32))
+    out = _run_tax(plan, rf)
+    assert float(torch.max(torch.abs(out["rho_pairs"] - 1))) <= NCC_TOL
+    assert float(torch.max(torch.abs(out["rho_n"] - 1))) <= NCC_TOL
+
+
+def test_point_source_lands_on_its_pixel():
+    from oracle_pins import as_point_source_rf
+    ne, nt, fs = 64, 512, 20e6
+    w = _tiny(ne, nt, 40, f_lo=2e6, f_hi=8e6, z0=4e-3, dz=0.4e-3)
+    rf = as_point_source_rf(ne, nt, fs, 0.3e-3, w.bins(), 23, w.z0 + 17 * w.dz)
+    plan = _plan(w)
+    out = _run_tax(plan, rf)
+    assert peak(out["image"][0].cpu().numpy()) == (17, 23)
+    assert peak(out["image_as"][0].cpu().numpy()) == (17, 23)
+
+
+# --------------------------------------------------------------- edge cases --
+def test_zero_input():
+    w = _tiny(32, 256, 10)
+    plan = _plan(w)
+    out = _run_tax(plan, np.zeros((32, 256), np.float32))
+    assert float(out["image"].abs().max()) == 0.0
+    assert torch.all(out["rho_n"] == 1.0)
+    assert torch.all(out["rho_pairs"] == np.float32(1e-3))
+
+
+def test_one_bin_one_row():
+    w = _tiny(64, 512, 1, bins=1, f_lo=3e6, f_hi=3.02e6)
+    assert w.bins().size == 1
+    rf = synth.random_rf(64, 512, seed=23)
+    plan = _plan(w)
+    out = _run_tax(plan, rf)
+    orc = oracle.as_tax(_geom(w), rf, oracle.pattern(64, 3, 2))
+    compare_xcorr(out, orc, check_peak=False)
+
+
+def test_largest_nt():
+    w = _tiny(128, 8192, 20, bins=12, fs=40e6, f_lo=0.5e6, f_hi=8e6)
+    rf = synth.random_rf(128, 8192, seed=24)
+    plan = _plan(w, pattern_m=16)
+    out = _run_tax(plan, rf)
+    orc = oracle.as_tax(_geom(w), rf, oracle.pattern(128, 3, 16))
+    compare_xcorr(out, orc, check_peak=False)
+
+
+def test_empty_call_and_determinism():
+    w = _tiny(32, 256, 30)
+    rf = torch.from_numpy(synth.random_rf(32, 256, seed=25)).cuda()
+    plan = _plan(w)
+    a = plan.as_tax(rf, rho_pairs=True)
+    b = plan.as_tax(rf, rho_pairs=True)
+    torch.cuda.synchronize()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    plan.sync()
+
+
+def test_bad_pointers_are_rejected():
+    pam = _pam()
+    w = _tiny(32, 256, 10)
+    plan = _plan(w)
+    L = pam.load()
+    rf = torch.zeros(1, 32, 256, device="cuda")
+    img = torch.zeros(1, 10, 32, device="cuda")
+    base = int(rf.data_ptr())
+    assert L.pam_as_tax(plan.handle, base + 4, 1, int(img.data_ptr()), None, None, None, None) == 1
+    host = np.zeros((32, 256), np.float32)
+    assert L.pam_as_tax(plan.handle, host.ctypes.data, 1, int(img.data_ptr()), None, None, None, None) == 1
+    assert L.pam_as_tax(plan.handle, base, 0, int(img.data_ptr()), None, None, None, None) == 0
+    assert L.pam_as_tax(plan.handle, base, -1, int(img.data_ptr()), None, None, None, None) == 1
+    assert L.pam_as_backprop(plan.handle, base, 1, 3, int(img.data_ptr()), None, None) == 1
+    with pytest.raises(TypeError):
+        plan.as_tax(torch.zeros(1, 32, 256))
+
+
+def test_host_entry_point_matches_device(w1_frames):
+    w, frames, orc = w1_frames
+    plan = _pam().Plan.from_workload(w, max_frames=2)
+    rf = np.stack([fr[0] for fr in frames])
+    img = np.zeros((3, w.nz, w.nx), np.float32)
+    rho = np.zeros((3, w.nz, w.nx), np.float32)
+    plan.as_xcorr_host(rf, img, rho)
+    dev = plan.as_tax(torch.from_numpy(rf).cuda())
+    assert np.array_equal(img, dev["image"].cpu().numpy())
+    assert np.array_equal(rho, dev["rho_n"].cpu().numpy())
+    for f in range(3):
+        assert rel_l2(img[f], orc[f]["image"]) <= REL_L2_TOL
+
+
+def test_profile_counters():
+    w = _tiny(32, 256, 10)
+    plan = _plan(w)
+    rf = torch.from_numpy(synth.random_rf(32, 256, seed=26)).cuda()
+    plan.profile_enable(True)
+    for _ in range(3):
+        plan.as_tax(rf)
+    ms, n, k = plan.profile_read()
+    assert n == 3 and k == 15 and ms > 0
+    plan.profile_enable(False)
