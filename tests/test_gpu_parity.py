@@ -227,9 +227,9 @@ def test_one_bin_one_row():
 
 
 def test_largest_nt():
-    w = _tiny(128, 8192, 20, bins=12, fs=40e6, f_lo=0.5e6, f_hi=8e6)
+    w = _tiny(128, 8192, 20, bins=12, fs=40e6, f_lo=0.5e6, f_hi=8e6, pattern_m=16)
     rf = synth.random_rf(128, 8192, seed=24)
-    plan = _plan(w, pattern_m=16)
+    plan = _plan(w)
     out = _run_tax(plan, rf)
     orc = oracle.as_tax(_geom(w), rf, oracle.pattern(128, 3, 16))
     compare_xcorr(out, orc, check_peak=False)
