@@ -14,17 +14,27 @@
 
 namespace {
 
-thread_local std::string g_err;
+// Message of the calling thread's last failure, in a fixed buffer so that
+// reporting an error never allocates.
+thread_local char g_err[512];
 
-pam_status fail(pam_status s, const std::string &msg)
+}  // namespace
+
+pam_status pam::set_error(pam_status s, const char *msg)
 {
-    g_err = msg;
+    std::snprintf(g_err, sizeof(g_err), "%s", msg ? msg : "");
     return s;
 }
 
+namespace {
+
+pam_status fail(pam_status s, const std::string &msg) { return pam::set_error(s, msg.c_str()); }
+
 pam_status cuda_fail(cudaError_t e, const char *where)
 {
-    return fail(PAM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    char m[512];
+    std::snprintf(m, sizeof(m), "%s: %s", where, cudaGetErrorString(e));
+    return pam::set_error(PAM_ERR_CUDA, m);
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
@@ -488,6 +498,6 @@ const char *pam_status_string(pam_status s)
     return "PAM_ERR_UNKNOWN";
 }
 
-const char *pam_last_error(void) { return g_err.c_str(); }
+const char *pam_last_error(void) { return g_err; }
 
 }  // extern "C"

@@ -245,10 +245,12 @@ cudaError_t launch_lateral(const pam_plan_s &p, int n_frames, int napq, const fl
     return cudaGetLastError();
 }
 
-cudaError_t prepare_fft_kernels(const pam_plan_s &p)
+// The attribute is per kernel, not per plan: it is set to the largest
+// supported nt so that plans of different sizes can coexist.
+cudaError_t prepare_fft_kernels(const pam_plan_s &)
 {
     return cudaFuncSetAttribute(time_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)time_fft_smem(p.nt));
+                                (int)time_fft_smem(8192));
 }
 
 }  // namespace pam

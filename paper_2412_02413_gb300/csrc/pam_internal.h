@@ -72,6 +72,9 @@ cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split
 cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, float *out_main,
                             float *rho_n, float *rho_pairs, float *image_as, cudaStream_t st);
 cudaError_t prepare_kernels(const pam_plan_s &p);
+
+// Records `msg` as the calling thread's pam_last_error() text and returns s.
+pam_status set_error(pam_status s, const char *msg);
 int choose_split(const pam_plan_s &p, int n_frames);
 
 }  // namespace pam

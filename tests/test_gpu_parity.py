@@ -279,6 +279,21 @@ def test_host_entry_point_matches_device(w1_frames):
         assert rel_l2(img[f], orc[f]["image"]) <= REL_L2_TOL
 
 
+def test_plans_of_different_sizes_coexist():
+    """A plan with a smaller time FFT created later must not break an earlier
+    plan with a larger one (kernel attributes are process-wide)."""
+    big = _tiny(32, 4096, 10, bins=5, fs=40e6, f_lo=1e6, f_hi=8e6)
+    small = _tiny(32, 256, 10)
+    pb = _plan(big)
+    rf_big = synth.random_rf(32, 4096, seed=27)
+    ref = _run_tax(pb, rf_big)["image"].clone()
+    ps = _plan(small)
+    _run_tax(ps, synth.random_rf(32, 256, seed=28))
+    again = _run_tax(pb, rf_big)["image"]
+    torch.cuda.synchronize()
+    assert torch.equal(ref, again)
+
+
 def test_profile_counters():
     w = _tiny(32, 256, 10)
     plan = _plan(w)
