@@ -145,6 +145,34 @@ pam_status pam_as_dax(pam_plan_t p, const float *rf, int n_frames, float *image_
 pam_status pam_as_xcorr_host(pam_plan_t p, const float *rf_host, int n_frames,
                              float *image_host, float *rho_n_host, void *stream);
 
+/* Size of the device array that pam_as_tax_static works in. It is part of the
+ * library image on every GPU that loads the library. */
+#define PAM_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* AS-TAX (as pam_as_tax) without allocating any memory, for callers that
+ * cannot allocate GPU memory: code running inside a host framework that owns
+ * every device allocation, real-time loops with a fixed memory footprint, or
+ * plug-ins that must not bypass their process's allocator. Such callers
+ * cannot create a plan, because pam_plan_create calls cudaMalloc. The paper
+ * has no counterpart; this is an interface for deployment.
+ *   d          geometry as for pam_plan_create; n_apod must be 3. max_frames is
+ *              ignored: frames run one after another.
+ *   rf         device float32 [n_frames][n_elem][n_samples]
+ *   image_tax  device [n_frames][nz][nx]; rho_n device [n_frames][nz][nx] or NULL
+ * The plan tables and the workspace live in one static device array of
+ * PAM_STATIC_SCRATCH_BYTES. A geometry that needs more (for example a very
+ * large nz * nx or n_bins) is rejected with PAM_ERR_INVALID_ARG and a message
+ * that gives the size it needs. The first call on a device sets that device
+ * up: it looks up the array's device address and sets kernel attributes. Make
+ * that first call before any stream capture. Every call shares the one array
+ * and leaves its contents behind: calls that overlap on the GPU (concurrent
+ * streams or host threads on the same device) race and must be serialised by
+ * the caller. The call calls no cudaMalloc, cudaFree or other allocating
+ * routine; the bins and apodizations go to the device by cudaMemcpyAsync
+ * from the stack. */
+pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf, int n_frames, float *image_tax,
+                             float *rho_n, void *stream);
+
 /* Waits for the plan's work on `stream` and reads the device status word.
  * Returns PAM_ERR_TIMEOUT if a kernel reported an expired wait (then clears
  * it), PAM_ERR_CUDA on a runtime error, PAM_OK otherwise. */

@@ -57,6 +57,7 @@ _SIGS = {
     "pam_as_tax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pam_as_dax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pam_as_xcorr_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
+    "pam_as_tax_static": (ctypes.c_int, [ctypes.POINTER(PlanDesc), _VP, ctypes.c_int, _VP, _VP, _VP]),
     "pam_sync": (ctypes.c_int, [_VP, _VP]),
     "pam_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
