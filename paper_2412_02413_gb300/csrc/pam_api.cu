@@ -60,7 +60,7 @@ void free_plan_memory(pam_plan_s *p)
 {
     auto fr = [](void *q) { if (q) cudaFree(q); };
     fr(p->t.bins); fr(p->t.apod); fr(p->t.ones); fr(p->t.tw_t); fr(p->t.tw_x);
-    fr(p->t.dds); fr(p->t.ecoef); fr(p->t.live); fr(p->t.bin_evan);
+    fr(p->t.phase); fr(p->t.live); fr(p->t.bin_evan);
     fr(p->w.S); fr(p->w.Q); fr(p->w.part); fr(p->w.rho_tmp); fr(p->w.e_tmp);
     fr(p->w.fmax); fr(p->w.status); fr(p->w.rf_stage); fr(p->w.img_stage); fr(p->w.rho_stage);
     p->t = pam::Tables{};
@@ -181,8 +181,7 @@ pam_status alloc_plan(pam_plan_s *p)
     PAM_TRY(dalloc(&p->t.ones, ne));
     PAM_TRY(dalloc(&p->t.tw_t, (size_t)p->nt));
     PAM_TRY(dalloc(&p->t.tw_x, nx));
-    PAM_TRY(dalloc(&p->t.dds, nb * nx));
-    PAM_TRY(dalloc(&p->t.ecoef, nb * nx));
+    PAM_TRY(dalloc(&p->t.phase, nb * nx));
     PAM_TRY(dalloc(&p->t.live, nb * nx));
     PAM_TRY(dalloc(&p->t.bin_evan, nb));
     PAM_TRY(dalloc(&p->w.S, F * nb * ne));

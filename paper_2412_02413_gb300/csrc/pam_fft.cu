@@ -1,5 +1,5 @@
 // pam_fft.cu -- plan tables (FP64), the per-channel time FFT that keeps the
-// selected bins (Eq. 1, F_t), and the apodized lateral DFT (Eq. 1, F_x;
+// selected bins (Eq. 1, F_t), and the apodized lateral FFT (Eq. 1, F_x;
 // apodization patterns of Sec. II-A and II-C).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,14 +31,15 @@ __device__ uint64_t turns_to_word(double turns)
 
 // One thread per (bin, lateral bin u). FP64 throughout (Eq. 2):
 //   w = 2 pi k fs / nt, kx = 2 pi u' / (nx pitch), kz = sqrt((w/c)^2 - kx^2).
-// Propagating: the phase kz*z in turns, as an exact fixed-point accumulator
-// word. The anchor holds kz*z0 and the step holds kz*dz per row, so row j has
-// phase anchor + j*step (mod 2^64): the 2 pi range reduction is exact integer
-// wrap-around. Evanescent: amplitude exp(-kappa z) = exp2(ecoef * z).
+// Propagating components get the phase kz*z in turns as a fixed-point
+// accumulator: a 64-bit anchor holds kz*z0 and a 64-bit step holds kz*dz per
+// row, so row j has phase anchor + j*step (mod 2^64). The 2 pi range
+// reduction is therefore exact integer wrap-around. The kernels read the top
+// 32 bits of that sum. Evanescent components get amplitude
+// exp(-kappa z) = exp2(ecoef * z).
 __global__ void tables_kernel(const int *__restrict__ bins, int n_bins, int nx, int nt, double fs,
                               double c, double pitch, double z0, double dz, int evanescent_zero,
-                              ulonglong2 *__restrict__ dds, float *__restrict__ ecoef,
-                              float *__restrict__ live, int *__restrict__ bin_evan,
+                              uint4 *__restrict__ phase, float *__restrict__ live, int *__restrict__ bin_evan,
                               float2 *__restrict__ tw_t, float2 *__restrict__ tw_x)
 {
     const double two_pi = 6.283185307179586476925286766559;
@@ -49,22 +50,21 @@ __global__ void tables_kernel(const int *__restrict__ bins, int n_bins, int nx, 
         double k0 = two_pi * (double)bins[b] * fs / (double)nt / c;
         double kx = two_pi * (double)up / ((double)nx * pitch);
         double d = k0 * k0 - kx * kx;
-        ulonglong2 w;
+        uint4 w;
         if (d >= 0.0) {
             double kz = sqrt(d);
-            w.x = turns_to_word(kz * z0 / two_pi);
-            w.y = turns_to_word(kz * dz / two_pi);
-            ecoef[idx] = 0.0f;
+            uint64_t a = turns_to_word(kz * z0 / two_pi);
+            uint64_t s = turns_to_word(kz * dz / two_pi);
+            w = make_uint4((unsigned)(a >> 32), (unsigned)(s >> 32), (unsigned)(s & 0xffffffffull),
+                           __float_as_uint(0.0f));
             live[idx] = 1.0f;
         } else {
             double kappa = sqrt(-d);
-            w.x = 0;
-            w.y = 0;
-            ecoef[idx] = (float)(-kappa * 1.4426950408889634073599246810019);
+            w = make_uint4(0u, 0u, 0u, __float_as_uint((float)(-kappa * 1.4426950408889634073599246810019)));
             live[idx] = evanescent_zero ? 0.0f : 1.0f;
             if (!evanescent_zero) atomicOr(&bin_evan[b], 1);
         }
-        dds[idx] = w;
+        phase[idx] = w;
     }
     if (idx < nt) {
         double s, co;
@@ -78,132 +78,136 @@ __global__ void tables_kernel(const int *__restrict__ bins, int n_bins, int nx, 
     }
 }
 
-// ----------------------------------------------------------- time FFT ----
-// One CTA per (pair of channels, frame). The pair is packed as z = a + i b,
-// transformed by an nt-point Stockham auto-sort FFT (radix-4 stages, then one
-// radix-2 stage when log2 nt is odd) in shared memory, and split back with
-//   A[k] = (Z[k] + conj Z[nt-k]) / 2,  B[k] = (Z[k] - conj Z[nt-k]) / (2i).
-// Only the selected bins leave the CTA: S[f][b][e].
-constexpr int TFFT_THREADS = 256;
-
-__global__ void __launch_bounds__(TFFT_THREADS)
-time_fft_kernel(const float *__restrict__ rf, int ne, int nt, const float2 *__restrict__ tw,
-                const int *__restrict__ bins, int n_bins, float2 *__restrict__ S,
-                unsigned *__restrict__ fmax)
+// ------------------------------------------------------ Stockham FFT ----
+// Forward FFTs (exp(-2 pi i m / n)) of `batch` contiguous n-point sequences in
+// shared memory. Radix-4 stages, then one radix-2 stage when log2 n is odd.
+// Auto-sort ordering, so the output is in natural order. tw[m] holds
+// exp(-2 pi i m / n) for m < n. x and y are ping-pong buffers; the return
+// value is the buffer with the result. Every thread of the CTA must call it.
+__device__ float2 *stockham(float2 *x, float2 *y, int n, int log2n, int batch, const float2 *tw, int tid, int nth)
 {
-    extern __shared__ __align__(16) float2 sbuf[];
-    float2 *x = sbuf, *y = sbuf + nt;
-    const int f = blockIdx.y;
-    const int e0 = 2 * blockIdx.x, e1 = e0 + 1;
-    const bool has_b = e1 < ne;
-    const float *ra = rf + ((size_t)f * ne + e0) * nt;
-    const float *rb = rf + ((size_t)f * ne + (has_b ? e1 : e0)) * nt;
-    if (blockIdx.x == 0 && threadIdx.x == 0) fmax[f] = 0u;
-
-    for (int t4 = threadIdx.x; t4 < nt / 4; t4 += TFFT_THREADS) {
-        float4 a = reinterpret_cast<const float4 *>(ra)[t4];
-        float4 b = has_b ? reinterpret_cast<const float4 *>(rb)[t4] : make_float4(0.f, 0.f, 0.f, 0.f);
-        x[4 * t4 + 0] = make_float2(a.x, b.x);
-        x[4 * t4 + 1] = make_float2(a.y, b.y);
-        x[4 * t4 + 2] = make_float2(a.z, b.z);
-        x[4 * t4 + 3] = make_float2(a.w, b.w);
-    }
-    __syncthreads();
-
+    const int q4 = n >> 2;
+    const int lq4 = log2n - 2;
     int Ns = 1;
-    const int q4 = nt / 4;
-    for (; 4 * Ns <= nt; Ns *= 4) {
-        const int tstride = nt / (4 * Ns);
-        for (int j = threadIdx.x; j < q4; j += TFFT_THREADS) {
+    for (; 4 * Ns <= n; Ns <<= 2) {
+        const int ts = n / (4 * Ns);
+        for (int t = tid; t < batch * q4; t += nth) {
+            const int bt = t >> lq4, j = t & (q4 - 1);
+            const float2 *xb = x + bt * n;
+            float2 *yb = y + bt * n;
             const int k = j & (Ns - 1);
-            float2 v0 = x[j], v1 = x[j + q4], v2 = x[j + 2 * q4], v3 = x[j + 3 * q4];
+            float2 v0 = xb[j], v1 = xb[j + q4], v2 = xb[j + 2 * q4], v3 = xb[j + 3 * q4];
             if (Ns > 1) {
-                v1 = cmul(v1, tw[k * tstride]);
-                v2 = cmul(v2, tw[2 * k * tstride]);
-                v3 = cmul(v3, tw[3 * k * tstride]);
+                v1 = cmul(v1, tw[k * ts]);
+                v2 = cmul(v2, tw[2 * k * ts]);
+                v3 = cmul(v3, tw[3 * k * ts]);
             }
-            // forward 4-point DFT: X_s = sum_r v_r (-i)^(r s)
             float2 s02 = cadd(v0, v2), d02 = csub(v0, v2);
             float2 s13 = cadd(v1, v3), d13 = csub(v1, v3);
             float2 md13 = make_float2(d13.y, -d13.x);   // -i * d13
             const int base = (j - k) * 4 + k;
-            y[base] = cadd(s02, s13);
-            y[base + Ns] = cadd(d02, md13);
-            y[base + 2 * Ns] = csub(s02, s13);
-            y[base + 3 * Ns] = csub(d02, md13);
+            yb[base] = cadd(s02, s13);
+            yb[base + Ns] = cadd(d02, md13);
+            yb[base + 2 * Ns] = csub(s02, s13);
+            yb[base + 3 * Ns] = csub(d02, md13);
         }
         __syncthreads();
         float2 *tmp = x; x = y; y = tmp;
     }
-    if (Ns < nt) {  // one radix-2 stage with Ns = nt/2
-        const int h = nt / 2;
-        for (int j = threadIdx.x; j < h; j += TFFT_THREADS) {
-            const int k = j & (Ns - 1);
-            float2 v0 = x[j], v1 = cmul(x[j + h], tw[k]);
-            const int base = (j - k) * 2 + k;
-            y[base] = cadd(v0, v1);
-            y[base + Ns] = csub(v0, v1);
+    if (Ns < n) {  // radix-2 stage with Ns = n/2
+        const int h = n >> 1;
+        for (int t = tid; t < batch * h; t += nth) {
+            const int bt = t >> (log2n - 1), j = t & (h - 1);
+            const float2 *xb = x + bt * n;
+            float2 *yb = y + bt * n;
+            float2 v0 = xb[j], v1 = cmul(xb[j + h], tw[j]);
+            yb[j] = cadd(v0, v1);
+            yb[j + h] = csub(v0, v1);
         }
         __syncthreads();
-        float2 *tmp = x; x = y; y = tmp;
+        x = y;
     }
-
-    for (int b = threadIdx.x; b < n_bins; b += TFFT_THREADS) {
-        const int k = bins[b];
-        float2 zk = x[k], zm = x[nt - k];
-        // A = (zk + conj zm)/2 ; B = (zk - conj zm)/(2i)
-        float2 A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        float dr = zk.x - zm.x, di = zk.y + zm.y;
-        float2 B = make_float2(0.5f * di, -0.5f * dr);
-        float2 *dst = S + ((size_t)f * n_bins + b) * ne;
-        dst[e0] = A;
-        if (has_b) dst[e1] = B;
-    }
+    return x;
 }
 
-// -------------------------------------------------------- lateral DFT ----
-// Q[f][b][q][u] = (1/nx) sum_e apod_q[e] S[f][b][e] exp(-2 pi i u e / nx)
-// times the live mask (PAM_EVANESCENT_ZERO). The 1/nx of the inverse lateral
-// transform is applied here. Threads (q, u); one CTA loops over BPB bins.
-constexpr int LAT_BPB = 4;
+// ----------------------------------------------------------- time FFT ----
+// One CTA per (channel, frame). The nt real samples are packed as
+// z[n] = x[2n] + i x[2n+1] and transformed by an nt/2-point FFT in shared
+// memory. The two half-length spectra are then separated:
+//   E[k] = (Z[k] + conj Z[M-k]) / 2,  O[k] = (Z[k] - conj Z[M-k]) / (2i),
+//   X[k] = E[k] + exp(-2 pi i k / nt) O[k].
+// Only the selected bins leave the CTA, as S[f][b][e]. Block (0, f) also
+// clears the frame's rho maximum for the epilogue.
+constexpr int TFFT_THREADS = 256;
 
-__global__ void __launch_bounds__(384)
-lateral_kernel(const float2 *__restrict__ S, int ne, int nx, int n_bins, int napq,
-               const float *__restrict__ apod, const float2 *__restrict__ twx,
-               const float *__restrict__ live, float2 *__restrict__ Q)
+__global__ void __launch_bounds__(TFFT_THREADS)
+time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const float2 *__restrict__ tw,
+                const int *__restrict__ bins, int n_bins, float2 *__restrict__ S, unsigned *__restrict__ fmax)
 {
-    extern __shared__ __align__(16) float2 sS[];   // [ne]
-    float *sA = reinterpret_cast<float *>(sS + ne); // [napq][ne]
-    float2 *sT = reinterpret_cast<float2 *>(sA + ((napq * ne + 1) & ~1)); // [nx]
-    const int f = blockIdx.y;
-    const int tid = threadIdx.x;
-    const int q = tid / nx, u = tid % nx;
-    for (int i = tid; i < napq * ne; i += blockDim.x) sA[i] = apod[i];
-    for (int i = tid; i < nx; i += blockDim.x) sT[i] = twx[i];
-    const float inv_nx = 1.0f / (float)nx;
-    const int b_begin = blockIdx.x * LAT_BPB;
-    const int b_end = min(n_bins, b_begin + LAT_BPB);
-    for (int b = b_begin; b < b_end; ++b) {
-        __syncthreads();
-        for (int i = tid; i < ne; i += blockDim.x) sS[i] = S[((size_t)f * n_bins + b) * ne + i];
-        __syncthreads();
-        if (q < napq) {
-            float re = 0.f, im = 0.f;
-            int m = 0;  // (u * e) mod nx, advanced incrementally
-            for (int e = 0; e < ne; ++e) {
-                float a = sA[q * ne + e];
-                float2 s = sS[e], w = sT[m];
-                float xr = a * s.x, xi = a * s.y;
-                re = fmaf(xr, w.x, fmaf(-xi, w.y, re));
-                im = fmaf(xr, w.y, fmaf(xi, w.x, im));
-                m += u;
-                if (m >= nx) m -= nx;
-            }
-            float l = live[(size_t)b * nx + u] * inv_nx;
-            Q[(((size_t)f * n_bins + b) * napq + q) * nx + u] = make_float2(re * l, im * l);
-        }
+    extern __shared__ __align__(16) float2 sbuf[];
+    const int M = nt >> 1;
+    float2 *x = sbuf, *y = sbuf + M, *tws = sbuf + 2 * M;
+    const int f = blockIdx.y, e = blockIdx.x;
+    const float4 *src = reinterpret_cast<const float4 *>(rf + ((size_t)f * ne + e) * nt);
+    if (e == 0 && threadIdx.x == 0) fmax[f] = 0u;
+    float4 *x4 = reinterpret_cast<float4 *>(x);
+    for (int i = threadIdx.x; i < nt / 4; i += TFFT_THREADS) x4[i] = src[i];  // (x0,x1),(x2,x3) pairs
+    for (int m = threadIdx.x; m < M; m += TFFT_THREADS) tws[m] = tw[2 * m];    // exp(-2 pi i m / M)
+    __syncthreads();
+    float2 *Z = stockham(x, y, M, log2nt - 1, 1, tws, threadIdx.x, TFFT_THREADS);
+    for (int b = threadIdx.x; b < n_bins; b += TFFT_THREADS) {
+        const int k = bins[b];                                 // 0 < k < M
+        const float2 zk = Z[k], zm = Z[M - k];
+        const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+        S[((size_t)f * n_bins + b) * ne + e] = cadd(E, cmul(tw[k], O));
     }
 }
+
+// -------------------------------------------------------- lateral FFT ----
+// Q[f][b][q][u] = live[b][u] / nx * sum_e apod_q[e] S[f][b][e] exp(-2 pi i u e / nx).
+// One CTA per (bin, frame): the napq apodized rows are transformed together
+// by the shared-memory FFT. The 1/nx of the inverse lateral transform is
+// applied here.
+constexpr int LAT_THREADS = 128;
+
+__global__ void __launch_bounds__(LAT_THREADS)
+lateral_kernel(const float2 *__restrict__ S, int ne, int nx, int log2nx, int n_bins, int napq,
+               const float *__restrict__ apod, const float2 *__restrict__ twx, const float *__restrict__ live,
+               float2 *__restrict__ Q)
+{
+    extern __shared__ __align__(16) float2 lbuf[];
+    float2 *x = lbuf, *y = lbuf + napq * nx, *tws = lbuf + 2 * napq * nx;
+    const int f = blockIdx.y, b = blockIdx.x;
+    const float2 *s = S + ((size_t)f * n_bins + b) * ne;
+    for (int i = threadIdx.x; i < napq * nx; i += LAT_THREADS) {
+        const int q = i / nx, e = i - q * nx;
+        const float2 v = s[e];
+        const float a = apod[q * ne + e];
+        x[i] = make_float2(a * v.x, a * v.y);
+    }
+    for (int i = threadIdx.x; i < nx; i += LAT_THREADS) tws[i] = twx[i];
+    __syncthreads();
+    const float2 *X = stockham(x, y, nx, log2nx, napq, tws, threadIdx.x, LAT_THREADS);
+    const float inv_nx = 1.0f / (float)nx;
+    float2 *dst = Q + ((size_t)f * n_bins + b) * napq * nx;
+    for (int i = threadIdx.x; i < napq * nx; i += LAT_THREADS) {
+        const int u = i & (nx - 1);
+        const float l = live[(size_t)b * nx + u] * inv_nx;
+        dst[i] = make_float2(X[i].x * l, X[i].y * l);
+    }
+}
+
+int ilog2i(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+size_t time_fft_smem(int nt) { return (size_t)3 * (nt / 2) * sizeof(float2); }
+
+size_t lateral_smem(int nx, int napq) { return ((size_t)2 * napq * nx + nx) * sizeof(float2); }
 
 }  // namespace
 
@@ -216,32 +220,23 @@ cudaError_t launch_tables(const pam_plan_s &p, cudaStream_t st)
     int blocks = (n + 255) / 256;
     tables_kernel<<<blocks, 256, 0, st>>>(p.t.bins, p.n_bins, p.nx, p.nt, p.d.fs_hz, p.d.c_mps, p.d.pitch_m,
                                           p.d.z0_m, p.d.dz_m, (p.d.flags & PAM_EVANESCENT_ZERO) ? 1 : 0,
-                                          p.t.dds, p.t.ecoef, p.t.live, p.t.bin_evan, p.t.tw_t, p.t.tw_x);
+                                          p.t.phase, p.t.live, p.t.bin_evan, p.t.tw_t, p.t.tw_x);
     return cudaGetLastError();
-}
-
-static size_t time_fft_smem(int nt) { return (size_t)2 * nt * sizeof(float2); }
-
-static size_t lateral_smem(int ne, int nx, int napq)
-{
-    return (size_t)ne * sizeof(float2) + (size_t)((napq * ne + 1) & ~1) * sizeof(float) + (size_t)nx * sizeof(float2);
 }
 
 cudaError_t launch_time_fft(const pam_plan_s &p, const float *rf, int n_frames, cudaStream_t st)
 {
-    dim3 grid((p.ne + 1) / 2, n_frames);
-    time_fft_kernel<<<grid, TFFT_THREADS, time_fft_smem(p.nt), st>>>(rf, p.ne, p.nt, p.t.tw_t, p.t.bins,
-                                                                      p.n_bins, p.w.S, p.w.fmax);
+    dim3 grid(p.ne, n_frames);
+    time_fft_kernel<<<grid, TFFT_THREADS, time_fft_smem(p.nt), st>>>(rf, p.ne, p.nt, ilog2i(p.nt), p.t.tw_t,
+                                                                      p.t.bins, p.n_bins, p.w.S, p.w.fmax);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lateral(const pam_plan_s &p, int n_frames, int napq, const float *apod, cudaStream_t st)
 {
-    dim3 grid((p.n_bins + LAT_BPB - 1) / LAT_BPB, n_frames);
-    int threads = napq * p.nx;
-    threads = (threads + 31) / 32 * 32;
-    lateral_kernel<<<grid, threads, lateral_smem(p.ne, p.nx, napq), st>>>(p.w.S, p.ne, p.nx, p.n_bins, napq, apod,
-                                                                          p.t.tw_x, p.t.live, p.w.Q);
+    dim3 grid(p.n_bins, n_frames);
+    lateral_kernel<<<grid, LAT_THREADS, lateral_smem(p.nx, napq), st>>>(p.w.S, p.ne, p.nx, ilog2i(p.nx), p.n_bins,
+                                                                        napq, apod, p.t.tw_x, p.t.live, p.w.Q);
     return cudaGetLastError();
 }
 

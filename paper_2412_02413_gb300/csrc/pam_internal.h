@@ -39,8 +39,11 @@ struct Tables {
     float *ones = nullptr;        // [n_elem]
     float2 *tw_t = nullptr;       // [nt]   exp(-2 pi i m / nt)
     float2 *tw_x = nullptr;       // [nx]   exp(-2 pi i m / nx)
-    ulonglong2 *dds = nullptr;    // [n_bins][nx] fixed-point phase (turns * 2^64): anchor at z0, step per row
-    float *ecoef = nullptr;       // [n_bins][nx] -kappa*log2(e) for evanescent components, else 0
+    // [n_bins][nx] per lateral bin u: {anchor_hi, step_hi, step_lo, ecoef bits}. The phase of row j,
+    // in turns * 2^32, is anchor_hi + j*step_hi + hi32(j*step_lo) (mod 2^32): the top word of the
+    // 64-bit fixed-point accumulator anchor + j*step. ecoef = -kappa*log2(e) for evanescent
+    // components (amplitude exp2(ecoef*z)), 0 otherwise.
+    uint4 *phase = nullptr;
     float *live = nullptr;        // [n_bins][nx] 1, or 0 for dropped evanescent components
     int *bin_evan = nullptr;      // [n_bins] 1 if any live evanescent component in the bin
 };

@@ -82,15 +82,16 @@ template <> struct IDft<8> {
     }
 };
 
-// exp(2 pi i * w / 2^64) for a fixed-point phase word w. The top 32 bits,
-// read as a signed turn count in [-1/2, 1/2), carry the angle; sincospif
-// takes it in half-turns.
-__device__ __forceinline__ float2 dds_phasor(uint64_t w)
+// exp(2 pi i * w / 2^32) for a 32-bit fixed-point phase word w (the top word
+// of the exact 64-bit phase accumulator). Read as a signed turn count in
+// [-1/2, 1/2), the angle is already range-reduced, so the hardware sine and
+// cosine approximations (absolute error about 5e-7 on [-pi, pi]) apply
+// directly.
+__device__ __forceinline__ float2 phase_cis(unsigned w)
 {
-    const int hi = (int)(uint32_t)(w >> 32);
-    const float t = (float)hi * 4.6566128730773926e-10f;  // 2^-31
+    const float ang = (float)(int)w * 1.4629180792671596e-9f;  // 2 pi / 2^32
     float s, c;
-    sincospif(t, &s, &c);
+    __sincosf(ang, &s, &c);
     return make_float2(c, s);
 }
 
@@ -122,15 +123,15 @@ constexpr size_t prop_smem_bytes()
 {
     using S = Shape<NX>;
     return (size_t)2 * NAP * NX * sizeof(float2)          // spectra, two stages
-           + (size_t)2 * NX * sizeof(ulonglong2)          // phase words
-           + (size_t)2 * NX * sizeof(float)               // evanescent coefficients
+           + (size_t)2 * NX * sizeof(uint4)               // phase words + evanescent coefficients
+           + (size_t)(NX / 2) * sizeof(float2)            // exp(+2 pi i m / (nx/2))
            + (size_t)PROP_WARPS * NAP * S::RPW * 2 * S::RS * sizeof(float2);  // transposes
 }
 
 template <int NAP, int NX, bool FIELDS>
 __global__ void __launch_bounds__(PROP_THREADS, 2)
-prop_corr_kernel(const float2 *__restrict__ Q, const ulonglong2 *__restrict__ dds,
-                 const float *__restrict__ ecoef, const int *__restrict__ bin_evan, int n_bins, int nz,
+prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
+                 const int *__restrict__ bin_evan, int n_bins, int nz,
                  float z0f, float dzf, int n_split, float *__restrict__ part, float2 *__restrict__ fields)
 {
     using S = Shape<NX>;
@@ -141,9 +142,9 @@ prop_corr_kernel(const float2 *__restrict__ Q, const ulonglong2 *__restrict__ dd
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2 *sQ = reinterpret_cast<float2 *>(smem_raw);
-    ulonglong2 *sD = reinterpret_cast<ulonglong2 *>(sQ + 2 * NAP * NX);
-    float *sE = reinterpret_cast<float *>(sD + 2 * NX);
-    float2 *sT = reinterpret_cast<float2 *>(sE + 2 * NX);
+    uint4 *sD = reinterpret_cast<uint4 *>(sQ + 2 * NAP * NX);
+    float2 *sW = reinterpret_cast<float2 *>(sD + 2 * NX);
+    float2 *sT = sW + H;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
@@ -156,19 +157,17 @@ prop_corr_kernel(const float2 *__restrict__ Q, const ulonglong2 *__restrict__ dd
 
     float2 *myT = sT + (size_t)warp * (NAP * RPW * 2 * RS);
 
-    // second-factor twiddles exp(+2 pi i n2 k1 / H)
-    float2 tw1[8];
-#pragma unroll
-    for (int k1 = 0; k1 < 8; ++k1) {
+    // second-factor twiddles exp(+2 pi i m / H), m < H
+    for (int m = tid; m < H; m += PROP_THREADS) {
         float s, c;
-        sincospif(2.0f * (float)((n2 * k1) % H) / (float)H, &s, &c);
-        tw1[k1] = make_float2(c, s);
+        sincospif(2.0f * (float)m / (float)H, &s, &c);
+        sW[m] = make_float2(c, s);
     }
     // Radix-2 DIF split folded into the phase: lanes of half g take
     // x_g[n'] = exp(2 pi i g n'/nx) (P[n'] + (-1)^g P[n'+H]).
-    const uint64_t g_unit = g ? (1ull << (64 - S::LOG2NX)) : 0ull;
-    const uint64_t g_half = g ? (1ull << 63) : 0ull;
-    const uint64_t jw = (uint64_t)jj;
+    const unsigned g_unit = g ? (1u << (32 - S::LOG2NX)) : 0u;
+    const unsigned g_half = g ? 0x80000000u : 0u;
+    const unsigned jw = (unsigned)jj;
     const float zj = z0f + (float)jj * dzf;
 
     float acc[NOUT][NACC];
@@ -177,19 +176,16 @@ prop_corr_kernel(const float2 *__restrict__ Q, const ulonglong2 *__restrict__ dd
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[o][a] = 0.0f;
 
-    constexpr int NQ4 = NAP * NX / 2, ND4 = NX, NE4 = NX / 4;
-    constexpr int NT4 = NQ4 + ND4 + NE4;
+    constexpr int NQ4 = NAP * NX / 2, ND4 = NX;
+    constexpr int NT4 = NQ4 + ND4;
     auto stage_in = [&](int b, int stage) {
         const uint4 *gq = reinterpret_cast<const uint4 *>(Q + ((size_t)f * n_bins + b) * NAP * NX);
-        const uint4 *gd = reinterpret_cast<const uint4 *>(dds + (size_t)b * NX);
-        const uint4 *ge = reinterpret_cast<const uint4 *>(ecoef + (size_t)b * NX);
+        const uint4 *gd = phase + (size_t)b * NX;
         uint4 *dq = reinterpret_cast<uint4 *>(sQ + stage * NAP * NX);
-        uint4 *dd = reinterpret_cast<uint4 *>(sD + stage * NX);
-        uint4 *de = reinterpret_cast<uint4 *>(sE + stage * NX);
+        uint4 *dd = sD + stage * NX;
         for (int i = tid; i < NT4; i += PROP_THREADS) {
             if (i < NQ4) cp_async16(dq + i, gq + i);
-            else if (i < NQ4 + ND4) cp_async16(dd + (i - NQ4), gd + (i - NQ4));
-            else cp_async16(de + (i - NQ4 - ND4), ge + (i - NQ4 - ND4));
+            else cp_async16(dd + (i - NQ4), gd + (i - NQ4));
         }
         cp_async_commit();
     };
@@ -202,21 +198,22 @@ prop_corr_kernel(const float2 *__restrict__ Q, const ulonglong2 *__restrict__ dd
         const int stage = (b - b_begin) & 1;
         if (b + 1 < b_end) stage_in(b + 1, stage ^ 1);
         const float2 *cQ = sQ + stage * NAP * NX;
-        const ulonglong2 *cD = sD + stage * NX;
-        const float *cE = sE + stage * NX;
+        const uint4 *cD = sD + stage * NX;
         const bool evan = bin_evan[b] != 0;
 
-        // Eq. 2 phasors of this lane's 16 lateral bins at depth z_j
+        // Eq. 2 phasors of this lane's 16 lateral bins at depth z_j. The row's
+        // phase word is anchor + j*step_hi + hi32(j*step_lo); dropping the
+        // carry out of the low word costs at most 2^-32 turn.
         float2 ph0[8], ph1[8];
 #pragma unroll
         for (int n1 = 0; n1 < 8; ++n1) {
             const int u0 = L2 * n1 + n2;
-            const ulonglong2 d0 = cD[u0], d1 = cD[u0 + H];
-            const uint64_t off = g_unit * (uint64_t)u0;
-            ph0[n1] = dds_phasor(d0.x + jw * d0.y + off);
-            ph1[n1] = dds_phasor(d1.x + jw * d1.y + off + g_half);
+            const uint4 d0 = cD[u0], d1 = cD[u0 + H];
+            const unsigned off = g_unit * (unsigned)u0;
+            ph0[n1] = phase_cis(d0.x + jw * d0.y + __umulhi(jw, d0.z) + off);
+            ph1[n1] = phase_cis(d1.x + jw * d1.y + __umulhi(jw, d1.z) + off + g_half);
             if (evan) {
-                const float a0 = exp2f(cE[u0] * zj), a1 = exp2f(cE[u0 + H] * zj);
+                const float a0 = exp2f(__uint_as_float(d0.w) * zj), a1 = exp2f(__uint_as_float(d1.w) * zj);
                 ph0[n1] = make_float2(ph0[n1].x * a0, ph0[n1].y * a0);
                 ph1[n1] = make_float2(ph1[n1].x * a1, ph1[n1].y * a1);
             }
@@ -234,7 +231,8 @@ prop_corr_kernel(const float2 *__restrict__ Q, const ulonglong2 *__restrict__ dd
             IDft<8>::run(x);
             float2 *reg = myT + ((q * RPW + r) * 2 + g) * RS;
 #pragma unroll
-            for (int k1 = 0; k1 < 8; ++k1) reg[k1 * TS + n2] = k1 ? cmul(x[k1], tw1[k1]) : x[k1];
+            for (int k1 = 0; k1 < 8; ++k1)
+                reg[k1 * TS + n2] = k1 ? cmul(x[k1], sW[(n2 * k1) & (H - 1)]) : x[k1];
         }
         __syncwarp();
 
@@ -303,67 +301,96 @@ prop_corr_kernel(const float2 *__restrict__ Q, const ulonglong2 *__restrict__ dd
 
 // --------------------------------------------------------- epilogue ----
 
-__device__ __forceinline__ double ncc_pair(float c, float aq, float ar, double eps)
+// Eq. 4 (with the Appendix A completion) for one pixel and one pair:
+// C_qr / (sqrt(A_qq) sqrt(A_rr)). A pair with no energy gives eps, and the
+// result is clamped below at eps (Sec. II-A). FP32 with correctly rounded
+// sqrt and division: three roundings, below 3e-7 relative.
+__device__ __forceinline__ float ncc_pair(float c, float aq, float ar, float eps)
 {
-    // Eq. 4 with an FP64 denominator; zero denominator -> eps; clamp at eps.
-    double den = sqrt((double)aq * (double)ar);
-    double rho = den > 0.0 ? (double)c / den : eps;
+    const float den = sqrtf(aq) * sqrtf(ar);
+    const float rho = den > 0.0f ? c / den : eps;
     return rho < eps ? eps : rho;
 }
 
-constexpr int EPI_THREADS = 256;
+constexpr int EPI_THREADS = 128;
 
+__device__ __forceinline__ float f4get(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+__device__ __forceinline__ void f4set(float4 &v, int i, float x)
+{
+    if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+}
+
+// Sums the per-split partials in split order (deterministic), then forms the
+// NCCs, rho (Eq. 10 for TAX), the coherent energy E = sum_k |sum_q p_q|^2 =
+// sum A_qq + 2 sum C_qr, and the frame's maximum rho. Four pixels per thread.
 template <int NAP>
 __global__ void __launch_bounds__(EPI_THREADS)
-epi_reduce_kernel(const float *__restrict__ part, int n_split, int npix, float eps,
-                  float *__restrict__ out_main, float *__restrict__ rho_tmp, float *__restrict__ e_tmp,
-                  float *__restrict__ rho_pairs, float *__restrict__ image_as, unsigned *__restrict__ fmax)
+epi_reduce_kernel(const float4 *__restrict__ part, int n_split, int npix4, float eps,
+                  float4 *__restrict__ out_main, float4 *__restrict__ rho_tmp, float4 *__restrict__ e_tmp,
+                  float4 *__restrict__ rho_pairs, float4 *__restrict__ image_as, unsigned *__restrict__ fmax)
 {
     constexpr int NACC = Acc<NAP>::N;
     const int f = blockIdx.y;
     const int x = blockIdx.x * EPI_THREADS + threadIdx.x;
-    float rho = 0.0f;
-    if (x < npix) {
-        float a[NACC];
+    float rmax = 0.0f;
+    if (x < npix4) {
+        float4 a[NACC];
 #pragma unroll
-        for (int c = 0; c < NACC; ++c) a[c] = 0.0f;
+        for (int c = 0; c < NACC; ++c) a[c] = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int s = 0; s < n_split; ++s) {
-            const float *src = part + (size_t)(f * n_split + s) * NACC * npix + x;
+            const float4 *src = part + (size_t)(f * n_split + s) * NACC * npix4 + x;
 #pragma unroll
-            for (int c = 0; c < NACC; ++c) a[c] += src[(size_t)c * npix];
+            for (int c = 0; c < NACC; ++c) {
+                const float4 v = src[(size_t)c * npix4];
+                a[c].x += v.x; a[c].y += v.y; a[c].z += v.z; a[c].w += v.w;
+            }
         }
-        const size_t o = (size_t)f * npix + x;
+        const size_t o = (size_t)f * npix4 + x;
         if constexpr (NAP == 1) {
             out_main[o] = a[0];
         } else {
-            float E;
-            if constexpr (NAP == 2) {
-                double r12 = ncc_pair(a[2], a[0], a[1], eps);
-                rho = (float)r12;
-                if (rho_pairs) rho_pairs[o] = rho;
-                E = a[0] + a[1] + 2.0f * a[2];
-            } else {
-                double r12 = ncc_pair(a[3], a[0], a[1], eps);
-                double r23 = ncc_pair(a[4], a[1], a[2], eps);
-                double r31 = ncc_pair(a[5], a[2], a[0], eps);
-                if (rho_pairs) {
-                    rho_pairs[(size_t)f * 3 * npix + x] = (float)r12;
-                    rho_pairs[(size_t)f * 3 * npix + npix + x] = (float)r23;
-                    rho_pairs[(size_t)f * 3 * npix + 2 * npix + x] = (float)r31;
+            float4 rho, E, r12v, r23v, r31v;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float r, e;
+                if constexpr (NAP == 2) {
+                    const float r12 = ncc_pair(f4get(a[2], i), f4get(a[0], i), f4get(a[1], i), eps);
+                    f4set(r12v, i, r12);
+                    r = r12;
+                    e = f4get(a[0], i) + f4get(a[1], i) + 2.0f * f4get(a[2], i);
+                } else {
+                    const float r12 = ncc_pair(f4get(a[3], i), f4get(a[0], i), f4get(a[1], i), eps);
+                    const float r23 = ncc_pair(f4get(a[4], i), f4get(a[1], i), f4get(a[2], i), eps);
+                    const float r31 = ncc_pair(f4get(a[5], i), f4get(a[2], i), f4get(a[0], i), eps);
+                    f4set(r12v, i, r12);
+                    f4set(r23v, i, r23);
+                    f4set(r31v, i, r31);
+                    r = cbrtf(r12 * r23 * r31);  // Eq. 10
+                    e = (f4get(a[0], i) + f4get(a[1], i) + f4get(a[2], i)) +
+                        2.0f * (f4get(a[3], i) + f4get(a[4], i) + f4get(a[5], i));
                 }
-                rho = cbrtf((float)(r12 * r23 * r31));  // Eq. 10
-                E = (a[0] + a[1] + a[2]) + 2.0f * (a[3] + a[4] + a[5]);
+                f4set(rho, i, r);
+                f4set(E, i, fmaxf(e, 0.0f));
+                rmax = fmaxf(rmax, r);
             }
-            E = fmaxf(E, 0.0f);
             rho_tmp[o] = rho;
             e_tmp[o] = E;
             if (image_as) image_as[o] = E;
+            if (rho_pairs) {
+                if constexpr (NAP == 2) {
+                    rho_pairs[o] = r12v;
+                } else {
+                    rho_pairs[(size_t)f * 3 * npix4 + x] = r12v;
+                    rho_pairs[(size_t)f * 3 * npix4 + npix4 + x] = r23v;
+                    rho_pairs[(size_t)f * 3 * npix4 + 2 * npix4 + x] = r31v;
+                }
+            }
         }
     }
     if constexpr (NAP > 1) {
         // block max of rho (all rho > 0, so the float bits order like unsigned ints)
         __shared__ float wmax[EPI_THREADS / 32];
-        float m = rho;
+        float m = rmax;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
         if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
@@ -377,18 +404,21 @@ epi_reduce_kernel(const float *__restrict__ part, int n_split, int npix, float e
     }
 }
 
+// rho_n = rho / max (Sec. II-A: the maximum becomes exactly 1) and the image
+// I = rho_n^2 E (Eq. 5 / Eq. 11). Four pixels per thread.
 __global__ void __launch_bounds__(EPI_THREADS)
-epi_normalize_kernel(const float *__restrict__ rho_tmp, const float *__restrict__ e_tmp,
-                     const unsigned *__restrict__ fmax, int npix, float *__restrict__ image,
-                     float *__restrict__ rho_n)
+epi_normalize_kernel(const float4 *__restrict__ rho_tmp, const float4 *__restrict__ e_tmp,
+                     const unsigned *__restrict__ fmax, int npix4, float4 *__restrict__ image,
+                     float4 *__restrict__ rho_n)
 {
     const int f = blockIdx.y;
     const int x = blockIdx.x * EPI_THREADS + threadIdx.x;
-    if (x >= npix) return;
-    const size_t o = (size_t)f * npix + x;
+    if (x >= npix4) return;
+    const size_t o = (size_t)f * npix4 + x;
     const float m = __uint_as_float(fmax[f]);
-    const float rn = rho_tmp[o] / m;   // rho_n (Sec. II-A): maximum becomes exactly 1
-    image[o] = rn * rn * e_tmp[o];     // Eq. 5 / Eq. 11
+    const float4 r = rho_tmp[o], e = e_tmp[o];
+    const float4 rn = make_float4(r.x / m, r.y / m, r.z / m, r.w / m);
+    image[o] = make_float4(rn.x * rn.x * e.x, rn.y * rn.y * e.y, rn.z * rn.z * e.z, rn.w * rn.w * e.w);
     if (rho_n) rho_n[o] = rn;
 }
 
@@ -398,7 +428,7 @@ cudaError_t launch_prop_t(const pam_plan_s &p, int n_frames, int n_split, float 
     using S = Shape<NX>;
     dim3 grid((p.nz + S::RPC - 1) / S::RPC, n_split, n_frames);
     prop_corr_kernel<NAP, NX, FIELDS><<<grid, PROP_THREADS, prop_smem_bytes<NAP, NX>(), st>>>(
-        p.w.Q, p.t.dds, p.t.ecoef, p.t.bin_evan, p.n_bins, p.nz, (float)p.d.z0_m, (float)p.d.dz_m, n_split,
+        p.w.Q, p.t.phase, p.t.bin_evan, p.n_bins, p.nz, (float)p.d.z0_m, (float)p.d.dz_m, n_split,
         p.w.part, reinterpret_cast<float2 *>(fields));
     return cudaGetLastError();
 }
@@ -461,22 +491,25 @@ cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split
 cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, float *out_main,
                             float *rho_n, float *rho_pairs, float *image_as, cudaStream_t st)
 {
-    const int npix = p.nz * p.nx;
-    dim3 grid((npix + EPI_THREADS - 1) / EPI_THREADS, n_frames);
+    const int npix4 = p.nz * p.nx / 4;  // nx is a multiple of 16
+    dim3 grid((npix4 + EPI_THREADS - 1) / EPI_THREADS, n_frames);
+    const float4 *part = reinterpret_cast<const float4 *>(p.w.part);
+    auto v4 = [](float *q) { return reinterpret_cast<float4 *>(q); };
     if (napq == 1) {
-        epi_reduce_kernel<1><<<grid, EPI_THREADS, 0, st>>>(p.w.part, n_split, npix, p.d.eps, out_main, nullptr,
+        epi_reduce_kernel<1><<<grid, EPI_THREADS, 0, st>>>(part, n_split, npix4, p.d.eps, v4(out_main), nullptr,
                                                            nullptr, nullptr, nullptr, nullptr);
         return cudaGetLastError();
     }
     if (napq == 2)
-        epi_reduce_kernel<2><<<grid, EPI_THREADS, 0, st>>>(p.w.part, n_split, npix, p.d.eps, nullptr, p.w.rho_tmp,
-                                                           p.w.e_tmp, rho_pairs, image_as, p.w.fmax);
+        epi_reduce_kernel<2><<<grid, EPI_THREADS, 0, st>>>(part, n_split, npix4, p.d.eps, nullptr, v4(p.w.rho_tmp),
+                                                           v4(p.w.e_tmp), v4(rho_pairs), v4(image_as), p.w.fmax);
     else
-        epi_reduce_kernel<3><<<grid, EPI_THREADS, 0, st>>>(p.w.part, n_split, npix, p.d.eps, nullptr, p.w.rho_tmp,
-                                                           p.w.e_tmp, rho_pairs, image_as, p.w.fmax);
+        epi_reduce_kernel<3><<<grid, EPI_THREADS, 0, st>>>(part, n_split, npix4, p.d.eps, nullptr, v4(p.w.rho_tmp),
+                                                           v4(p.w.e_tmp), v4(rho_pairs), v4(image_as), p.w.fmax);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    epi_normalize_kernel<<<grid, EPI_THREADS, 0, st>>>(p.w.rho_tmp, p.w.e_tmp, p.w.fmax, npix, out_main, rho_n);
+    epi_normalize_kernel<<<grid, EPI_THREADS, 0, st>>>(v4(p.w.rho_tmp), v4(p.w.e_tmp), p.w.fmax, npix4, v4(out_main),
+                                                       v4(rho_n));
     return cudaGetLastError();
 }
 

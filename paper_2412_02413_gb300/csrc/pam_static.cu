@@ -98,8 +98,7 @@ size_t carve(pam_plan_s &p, int n_split, unsigned char *base)
     p.t.apod = static_cast<float *>(take(3 * ne * sizeof(float)));
     p.t.tw_t = static_cast<float2 *>(take((size_t)p.nt * sizeof(float2)));
     p.t.tw_x = static_cast<float2 *>(take(nx * sizeof(float2)));
-    p.t.dds = static_cast<ulonglong2 *>(take(nb * nx * sizeof(ulonglong2)));
-    p.t.ecoef = static_cast<float *>(take(nb * nx * sizeof(float)));
+    p.t.phase = static_cast<uint4 *>(take(nb * nx * sizeof(uint4)));
     p.t.live = static_cast<float *>(take(nb * nx * sizeof(float)));
     p.t.bin_evan = static_cast<int *>(take(nb * sizeof(int)));
     p.w.S = static_cast<float2 *>(take(nb * ne * sizeof(float2)));
