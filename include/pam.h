@@ -111,6 +111,15 @@ int pam_plan_bins(pam_plan_t p, int *bins_out);
 /* Copies the plan's apodizations to host memory [n_apod][n_elem]. Returns n_apod. */
 int pam_plan_apod(pam_plan_t p, float *apod_out);
 
+/* Pins the number of bin chunks that the fused propagate-and-correlate
+ * kernel splits Omega into for one row tile: 0 = automatic (about two CTAs
+ * per SM), n >= 1 = n chunks, capped at n_bins and at what the workspace
+ * holds. Splits of up to 8 are reduced on chip inside a thread-block cluster,
+ * larger ones through global partial sums. Results are deterministic for a
+ * given split. Different splits round differently, by the order of the sums
+ * over bins. */
+pam_status pam_plan_set_split(pam_plan_t p, int n_split);
+
 /* AS back-propagation energy map, Eq. 3, for one apodization.
  *   rf          device float32 [n_frames][n_elem][n_samples]
  *   apod_index  -1 = full aperture (all ones); 0..n_apod-1 = plan aperture q

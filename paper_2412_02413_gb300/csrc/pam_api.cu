@@ -229,6 +229,22 @@ cudaError_t prof_record(pam_plan_s *p, cudaStream_t st)
 cudaError_t prof_begin(pam_plan_s *p, cudaStream_t st) { return prof_record(p, st); }
 cudaError_t prof_end(pam_plan_s *p, cudaStream_t st) { return prof_record(p, st); }
 
+pam::EpiOut epi_out(const pam_plan_s *p, float *main, float *rho_n, float *rho_pairs, float *image_as)
+{
+    pam::EpiOut o;
+    o.eps = p->d.eps;
+    o.npix = p->nz * p->nx;
+    o.out_main = main;
+    o.rho_n = rho_n;
+    o.rho_pairs = rho_pairs;
+    o.image_as = image_as;
+    o.rho_tmp = p->w.rho_tmp;
+    o.e_tmp = p->w.e_tmp;
+    o.fmax = p->w.fmax;
+    o.status = p->w.status;
+    return o;
+}
+
 pam_status run_xcorr(pam_plan_t p, const float *rf, int n_frames, float *image, float *rho_n,
                      float *rho_pairs, float *image_as, cudaStream_t st)
 {
@@ -242,16 +258,16 @@ pam_status run_xcorr(pam_plan_t p, const float *rf, int n_frames, float *image, 
         e = pam::launch_lateral(*p, Fc, p->n_apod, p->t.apod, st);
         if (e != cudaSuccess) return cuda_fail(e, "lateral DFT launch");
         int ns = pam::choose_split(*p, Fc);
+        pam::EpiOut out = epi_out(p, image + (size_t)f0 * npix, rho_n ? rho_n + (size_t)f0 * npix : nullptr,
+                                  rho_pairs ? rho_pairs + (size_t)f0 * npairs * npix : nullptr,
+                                  image_as ? image_as + (size_t)f0 * npix : nullptr);
         if ((e = prof_begin(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
-        e = pam::launch_prop(*p, Fc, p->n_apod, ns, nullptr, st);
+        e = pam::launch_prop(*p, Fc, p->n_apod, ns, nullptr, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "propagate/correlate launch");
         if ((e = prof_end(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
-        p->kernels += 5;
-        e = pam::launch_epilogue(*p, Fc, p->n_apod, ns, image + (size_t)f0 * npix,
-                                 rho_n ? rho_n + (size_t)f0 * npix : nullptr,
-                                 rho_pairs ? rho_pairs + (size_t)f0 * npairs * npix : nullptr,
-                                 image_as ? image_as + (size_t)f0 * npix : nullptr, st);
+        e = pam::launch_epilogue(*p, Fc, p->n_apod, ns, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "epilogue launch");
+        p->kernels += 3 + pam::epilogue_kernels(p->n_apod, ns);
     }
     return PAM_OK;
 }
@@ -350,13 +366,14 @@ pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod
         if (e != cudaSuccess) return cuda_fail(e, "lateral DFT launch");
         int ns = pam::choose_split(*p, Fc);
         float *fl = fields ? fields + (size_t)f0 * p->n_bins * npix * 2 : nullptr;
+        pam::EpiOut out = epi_out(p, energy + (size_t)f0 * npix, nullptr, nullptr, nullptr);
         if ((e = prof_begin(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
-        e = pam::launch_prop(*p, Fc, 1, ns, fl, st);
+        e = pam::launch_prop(*p, Fc, 1, ns, fl, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "propagate launch");
         if ((e = prof_end(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
-        p->kernels += 4;
-        e = pam::launch_epilogue(*p, Fc, 1, ns, energy + (size_t)f0 * npix, nullptr, nullptr, nullptr, st);
+        e = pam::launch_epilogue(*p, Fc, 1, ns, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "epilogue launch");
+        p->kernels += 3 + pam::epilogue_kernels(1, ns);
     }
     return PAM_OK;
 }
@@ -448,6 +465,14 @@ pam_status pam_sync(pam_plan_t p, void *stream)
         cudaMemset(p->w.status, 0, sizeof(int));
         return fail(PAM_ERR_TIMEOUT, "a kernel reported an expired bounded wait");
     }
+    return PAM_OK;
+}
+
+pam_status pam_plan_set_split(pam_plan_t p, int n_split)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (n_split < 0) return fail(PAM_ERR_INVALID_ARG, "n_split must be >= 0");
+    p->split_override = n_split;
     return PAM_OK;
 }
 

@@ -16,6 +16,23 @@ namespace pam {
 // kernel for a lateral length nx (8 warps; 2*nx/16 lanes per row).
 int prop_rows_per_cta(int nx);
 
+// Bin splits up to this size reduce inside a thread-block cluster (portable limit).
+constexpr int kMaxClusterSplit = 8;
+
+// Destination of the per-pixel epilogue (maps of one call, [F][nz][nx]).
+struct EpiOut {
+    float eps = 1e-3f;
+    int npix = 0;                 // nz * nx
+    float *out_main = nullptr;    // AS energy (n_apod 1) or the final image (DAX / TAX)
+    float *rho_n = nullptr;       // optional
+    float *rho_pairs = nullptr;   // optional, [F][n_pairs][nz][nx]
+    float *image_as = nullptr;    // optional
+    float *rho_tmp = nullptr;     // workspace: rho before normalisation
+    float *e_tmp = nullptr;       // workspace: coherent energy
+    unsigned *fmax = nullptr;     // workspace: per-frame max of rho
+    int *status = nullptr;        // device status word (set on an expired bounded wait)
+};
+
 // Accumulators per pixel: |p1|^2 (AS), + |p2|^2, Re p1*p2 (DAX),
 // + |p3|^2, Re p2*p3, Re p3*p1 (TAX).
 inline int n_acc(int n_apod) { return n_apod == 1 ? 1 : (n_apod == 2 ? 3 : 6); }
@@ -63,6 +80,7 @@ struct pam_plan_s {
     std::vector<cudaEvent_t> prof_ev;  // pairs around propagate-and-correlate launches
     size_t prof_used = 0;              // events recorded since the last read
     long long kernels = 0;             // libpam kernel launches since the last read
+    int split_override = 0;            // pam_plan_set_split (0 = automatic)
 };
 
 namespace pam {
@@ -71,9 +89,16 @@ namespace pam {
 cudaError_t launch_tables(const pam_plan_s &p, cudaStream_t st);
 cudaError_t launch_time_fft(const pam_plan_s &p, const float *rf, int n_frames, cudaStream_t st);
 cudaError_t launch_lateral(const pam_plan_s &p, int n_frames, int napq, const float *apod, cudaStream_t st);
-cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields, cudaStream_t st);
-cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, float *out_main,
-                            float *rho_n, float *rho_pairs, float *image_as, cudaStream_t st);
+// The fused propagate-and-correlate kernel. With n_split <= kMaxClusterSplit
+// it runs as clusters and also writes the per-pixel epilogue into `out`.
+cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields,
+                        const EpiOut &out, cudaStream_t st);
+// The rest of the epilogue: the partial reduction (no cluster) and the rho
+// normalisation (DAX / TAX).
+cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, const EpiOut &out,
+                            cudaStream_t st);
+int epilogue_kernels(int napq, int n_split);   // kernels launch_epilogue launches
+bool prop_uses_cluster(int n_split);
 cudaError_t prepare_kernels(const pam_plan_s &p);
 
 // Records `msg` as the calling thread's pam_last_error() text and returns s.

@@ -18,6 +18,7 @@
 // padded shared memory and an (nx/16)-point DFT in registers. A CTA loops over
 // a contiguous chunk of bins. Each bin's spectra and phase words are staged in
 // shared memory with cp.async, double-buffered.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -95,13 +96,58 @@ __device__ __forceinline__ float2 phase_cis(unsigned w)
     return make_float2(c, s);
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+// ---- TMA bulk copies and mbarriers (inline PTX) ----
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
 {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of `bar` with the given parity to complete, for at
+// most about one second (2^31 SM cycles). Returns false on expiry; every
+// caller then reports PAM_ERR_TIMEOUT through the status word instead of
+// hanging.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+// One bulk global -> shared copy that completes `bytes` of transaction on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+constexpr int NSTAGE = 4;  // bins in flight per CTA
 
 template <int NX> struct Shape {
     static constexpr int H = NX / 2;               // half length
@@ -122,17 +168,91 @@ template <int NAP, int NX>
 constexpr size_t prop_smem_bytes()
 {
     using S = Shape<NX>;
-    return (size_t)2 * NAP * NX * sizeof(float2)          // spectra, two stages
-           + (size_t)2 * NX * sizeof(uint4)               // phase words + evanescent coefficients
+    return (size_t)128                                    // full / empty mbarriers
+           + (size_t)NSTAGE * NAP * NX * sizeof(float2)   // spectra, one per stage
+           + (size_t)NSTAGE * NX * sizeof(uint4)          // phase words + evanescent coefficients
            + (size_t)(NX / 2) * sizeof(float2)            // exp(+2 pi i m / (nx/2))
            + (size_t)PROP_WARPS * NAP * S::RPW * 2 * S::RS * sizeof(float2);  // transposes
 }
 
-template <int NAP, int NX, bool FIELDS>
+// Eq. 4 (with the Appendix A completion) for one pixel and one pair:
+// C_qr / (sqrt(A_qq) sqrt(A_rr)). A pair with no energy gives eps, and the
+// result is clamped below at eps (Sec. II-A). FP32 with correctly rounded
+// sqrt and division: three roundings, below 3e-7 relative.
+__device__ __forceinline__ float ncc_pair(float c, float aq, float ar, float eps)
+{
+    const float den = sqrtf(aq) * sqrtf(ar);
+    const float rho = den > 0.0f ? c / den : eps;
+    return rho < eps ? eps : rho;
+}
+
+// The per-pixel end of the method from the bin-summed accumulators a[]:
+// AS (Eq. 3): the energy itself. AS-DAX / AS-TAX: the clamped pair NCCs, rho
+// (rho_12, or Eq. 10's cube root of the three), and the coherent energy
+// E = sum_k |sum_q p_q|^2 = sum A_qq + 2 sum C_qr. Writes the
+// pre-normalisation maps and returns rho (0 for AS).
+template <int NAP>
+__device__ __forceinline__ float pixel_epilogue(const float (&a)[Acc<NAP>::N], const EpiOut &out, int f,
+                                                size_t x)
+{
+    const size_t o = (size_t)f * out.npix + x;
+    if constexpr (NAP == 1) {
+        out.out_main[o] = a[0];
+        return 0.0f;
+    } else {
+        float rho, E;
+        if constexpr (NAP == 2) {
+            rho = ncc_pair(a[2], a[0], a[1], out.eps);
+            if (out.rho_pairs) out.rho_pairs[o] = rho;
+            E = a[0] + a[1] + 2.0f * a[2];
+        } else {
+            const float r12 = ncc_pair(a[3], a[0], a[1], out.eps);
+            const float r23 = ncc_pair(a[4], a[1], a[2], out.eps);
+            const float r31 = ncc_pair(a[5], a[2], a[0], out.eps);
+            if (out.rho_pairs) {
+                float *rp = out.rho_pairs + (size_t)f * 3 * out.npix + x;
+                rp[0] = r12;
+                rp[out.npix] = r23;
+                rp[2 * (size_t)out.npix] = r31;
+            }
+            rho = cbrtf(r12 * r23 * r31);  // Eq. 10
+            E = (a[0] + a[1] + a[2]) + 2.0f * (a[3] + a[4] + a[5]);
+        }
+        E = fmaxf(E, 0.0f);
+        out.rho_tmp[o] = rho;
+        out.e_tmp[o] = E;
+        if (out.image_as) out.image_as[o] = E;
+        return rho;
+    }
+}
+
+// Largest value over the CTA, folded into the frame's maximum. All rho > 0,
+// so their float bits order like unsigned integers.
+__device__ __forceinline__ void block_max_to(float v, unsigned *dst, float *scratch, int nthreads)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d));
+    if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < nthreads / 32 ? scratch[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, d));
+        if (threadIdx.x == 0) atomicMax(dst, __float_as_uint(v));
+    }
+}
+
+// CLUSTER: the n_split CTAs of a row tile form one thread-block cluster. After
+// the bin loop they add their accumulators through distributed shared memory
+// (in rank order, so the sum is deterministic) and finish the per-pixel
+// epilogue themselves. Otherwise each CTA writes its partial sums to `part`
+// for epi_reduce_kernel.
+template <int NAP, int NX, bool FIELDS, bool CLUSTER>
 __global__ void __launch_bounds__(PROP_THREADS, 2)
 prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
                  const int *__restrict__ bin_evan, int n_bins, int nz,
-                 float z0f, float dzf, int n_split, float *__restrict__ part, float2 *__restrict__ fields)
+                 float z0f, float dzf, int n_split, float *__restrict__ part, float2 *__restrict__ fields,
+                 EpiOut out)
 {
     using S = Shape<NX>;
     constexpr int H = S::H, L2 = S::L2, LPR = S::LPR, RPW = S::RPW, RPC = S::RPC, KPL = S::KPL;
@@ -140,10 +260,12 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
     constexpr int NACC = Acc<NAP>::N;
     constexpr int NOUT = KPL * L2;  // 8 pixels per lane
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *sQ = reinterpret_cast<float2 *>(smem_raw);
-    uint4 *sD = reinterpret_cast<uint4 *>(sQ + 2 * NAP * NX);
-    float2 *sW = reinterpret_cast<float2 *>(sD + 2 * NX);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);   // [NSTAGE] data of a stage has landed
+    uint64_t *empty = full + NSTAGE;                            // [NSTAGE] all warps are done with a stage
+    float2 *sQ = reinterpret_cast<float2 *>(smem_raw + 128);
+    uint4 *sD = reinterpret_cast<uint4 *>(sQ + NSTAGE * NAP * NX);
+    float2 *sW = reinterpret_cast<float2 *>(sD + NSTAGE * NX);
     float2 *sT = sW + H;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -176,27 +298,46 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[o][a] = 0.0f;
 
-    constexpr int NQ4 = NAP * NX / 2, ND4 = NX;
-    constexpr int NT4 = NQ4 + ND4;
-    auto stage_in = [&](int b, int stage) {
-        const uint4 *gq = reinterpret_cast<const uint4 *>(Q + ((size_t)f * n_bins + b) * NAP * NX);
-        const uint4 *gd = phase + (size_t)b * NX;
-        uint4 *dq = reinterpret_cast<uint4 *>(sQ + stage * NAP * NX);
-        uint4 *dd = sD + stage * NX;
-        for (int i = tid; i < NT4; i += PROP_THREADS) {
-            if (i < NQ4) cp_async16(dq + i, gq + i);
-            else cp_async16(dd + (i - NQ4), gd + (i - NQ4));
+    // Staging pipeline: thread 0 keeps NSTAGE-1 bins in flight with TMA bulk
+    // copies (spectra + phase words), each completing on the stage's `full`
+    // barrier. Every warp arrives on the stage's `empty` barrier once it has
+    // finished with the stage. Warps can therefore run up to NSTAGE-1 bins
+    // apart, with no CTA-wide barrier per bin.
+    constexpr unsigned BYTES_Q = NAP * NX * sizeof(float2), BYTES_D = NX * sizeof(uint4);
+    if (tid == 0) {
+        for (int st = 0; st < NSTAGE; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], PROP_WARPS);
         }
-        cp_async_commit();
-    };
-
-    if (b_begin < b_end) stage_in(b_begin, 0);
-    cp_async_wait_all();
+        mbar_fence_init();
+    }
     __syncthreads();
+    const int nb = b_end - b_begin;
+    int issued = 0;    // producer (thread 0): bins whose copies have been issued
+    bool ok = true;    // false once a bounded wait expired
+    auto issue_next = [&]() -> bool {
+        const int st = issued % NSTAGE;
+        if (issued >= NSTAGE && !mbar_wait(&empty[st], ((issued / NSTAGE) - 1) & 1)) return false;
+        const int b = b_begin + issued;
+        mbar_expect_tx(&full[st], BYTES_Q + BYTES_D);
+        bulk_g2s(sQ + st * NAP * NX, Q + ((size_t)f * n_bins + b) * NAP * NX, BYTES_Q, &full[st]);
+        bulk_g2s(sD + st * NX, phase + (size_t)b * NX, BYTES_D, &full[st]);
+        ++issued;
+        return true;
+    };
+    if (tid == 0)
+        while (issued < nb && issued < NSTAGE - 1) issue_next();
 
-    for (int b = b_begin; b < b_end; ++b) {
-        const int stage = (b - b_begin) & 1;
-        if (b + 1 < b_end) stage_in(b + 1, stage ^ 1);
+    int done = 0;      // bins this warp has finished
+    for (int i = 0; i < nb; ++i) {
+        if (tid == 0 && issued < nb) ok = issue_next();
+        const int stage = i % NSTAGE;
+        if (ok) ok = mbar_wait(&full[stage], (i / NSTAGE) & 1);
+        if (!__all_sync(0xffffffffu, ok)) {
+            ok = false;
+            break;
+        }
+        const int b = b_begin + i;
         const float2 *cQ = sQ + stage * NAP * NX;
         const uint4 *cD = sD + stage * NX;
         const bool evan = bin_evan[b] != 0;
@@ -273,7 +414,7 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
             }
         }
         if constexpr (FIELDS) {
-            if (row_ok) {
+            if (row_ok) {  // fields of bin b
                 float2 *dst = fields + (((size_t)f * n_bins + b) * nz + j) * NX;
 #pragma unroll
                 for (int o = 0; o < NOUT; ++o) {
@@ -282,127 +423,112 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
                 }
             }
         }
-        cp_async_wait_all();
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[stage]);
+        done = i + 1;
     }
+    if (!ok) {
+        if (lane == 0) atomicOr(out.status, 1);
+        // let copies still in flight land before the CTA's shared memory goes away
+        if (tid == 0)
+            for (int k = done; k < issued; ++k) mbar_wait(&full[k % NSTAGE], (k / NSTAGE) & 1);
+    }
+    const bool aborted = __syncthreads_or(!ok) != 0;
 
-    if (row_ok) {
-        const size_t plane = (size_t)nz * NX;
-        float *dst = part + (size_t)(f * n_split + split) * NACC * plane + (size_t)j * NX;
+    if constexpr (CLUSTER) {
+        namespace cg = cooperative_groups;
+        cg::cluster_group cluster = cg::this_cluster();
+        constexpr int TILE = RPC * NX;  // pixels of the row tile (2048)
+        float *sAcc = reinterpret_cast<float *>(sT);  // [NACC][TILE], reuses the transpose buffers
+        __syncthreads();
+        const int rowl = warp * RPW + r;
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) {
             const int k1 = n2 * KPL + o / L2, k2 = o % L2;
             const int i = 2 * (k1 + 8 * k2) + g;
 #pragma unroll
-            for (int a = 0; a < NACC; ++a) dst[a * plane + i] = acc[o][a];
+            for (int a = 0; a < NACC; ++a) sAcc[a * TILE + rowl * NX + i] = acc[o][a];
+        }
+        cluster.sync();
+        // Each CTA of the cluster finishes one slice of the tile's pixels.
+        const int cs = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
+        const int per = (TILE + cs - 1) / cs;
+        const int p_end = min(TILE, (rank + 1) * per);
+        float rmax = 0.0f;
+        for (int px = rank * per + tid; px < p_end; px += PROP_THREADS) {
+            float a[NACC];
+#pragma unroll
+            for (int c = 0; c < NACC; ++c) a[c] = 0.0f;
+            for (int c = 0; c < cs; ++c) {
+                const float *rem = cluster.map_shared_rank(sAcc, c);
+#pragma unroll
+                for (int aa = 0; aa < NACC; ++aa) a[aa] += rem[aa * TILE + px];
+            }
+            const int row = blockIdx.x * RPC + px / NX;
+            if (row < nz && !aborted) rmax = fmaxf(rmax, pixel_epilogue<NAP>(a, out, f, (size_t)row * NX + (px % NX)));
+        }
+        if constexpr (NAP > 1) {
+            __shared__ float wmax[PROP_THREADS / 32];
+            block_max_to(rmax, out.fmax + f, wmax, PROP_THREADS);
+        }
+        cluster.sync();  // keep this CTA's shared memory alive until every peer has read it
+    } else {
+        if (row_ok && !aborted) {
+            const size_t plane = (size_t)nz * NX;
+            float *dst = part + (size_t)(f * n_split + split) * NACC * plane + (size_t)j * NX;
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) {
+                const int k1 = n2 * KPL + o / L2, k2 = o % L2;
+                const int i = 2 * (k1 + 8 * k2) + g;
+#pragma unroll
+                for (int a = 0; a < NACC; ++a) dst[a * plane + i] = acc[o][a];
+            }
         }
     }
 }
 
 // --------------------------------------------------------- epilogue ----
 
-// Eq. 4 (with the Appendix A completion) for one pixel and one pair:
-// C_qr / (sqrt(A_qq) sqrt(A_rr)). A pair with no energy gives eps, and the
-// result is clamped below at eps (Sec. II-A). FP32 with correctly rounded
-// sqrt and division: three roundings, below 3e-7 relative.
-__device__ __forceinline__ float ncc_pair(float c, float aq, float ar, float eps)
+// Sums the per-split partials in split order (deterministic) and finishes
+// the per-pixel epilogue. One warp per accumulator sums 32 groups of four
+// pixels (every partial load of a thread is independent, so they overlap);
+// warp 0 then combines the accumulators of its pixels.
+template <int NAP>
+__global__ void __launch_bounds__(32 * Acc<NAP>::N)
+epi_reduce_kernel(const float4 *__restrict__ part, int n_split, int npix4, EpiOut out)
 {
-    const float den = sqrtf(aq) * sqrtf(ar);
-    const float rho = den > 0.0f ? c / den : eps;
-    return rho < eps ? eps : rho;
+    constexpr int NACC = Acc<NAP>::N;
+    __shared__ float4 sA[NACC][32];
+    __shared__ float wmax[NACC];
+    const int f = blockIdx.y;
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x4 = blockIdx.x * 32 + lane;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (x4 < npix4) {
+        const float4 *src = part + ((size_t)f * n_split * NACC + c) * npix4 + x4;
+        const size_t stride = (size_t)NACC * npix4;
+#pragma unroll 4
+        for (int s = 0; s < n_split; ++s) {
+            const float4 v = src[s * stride];
+            a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+        }
+    }
+    sA[c][lane] = a;
+    __syncthreads();
+    float rmax = 0.0f;
+    if (c == 0 && x4 < npix4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float acc[NACC];
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) acc[k] = reinterpret_cast<const float *>(&sA[k][lane])[i];
+            rmax = fmaxf(rmax, pixel_epilogue<NAP>(acc, out, f, (size_t)x4 * 4 + i));
+        }
+    }
+    if constexpr (NAP > 1) block_max_to(rmax, out.fmax + f, wmax, 32 * NACC);
 }
 
 constexpr int EPI_THREADS = 128;
-
-__device__ __forceinline__ float f4get(const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
-__device__ __forceinline__ void f4set(float4 &v, int i, float x)
-{
-    if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
-}
-
-// Sums the per-split partials in split order (deterministic), then forms the
-// NCCs, rho (Eq. 10 for TAX), the coherent energy E = sum_k |sum_q p_q|^2 =
-// sum A_qq + 2 sum C_qr, and the frame's maximum rho. Four pixels per thread.
-template <int NAP>
-__global__ void __launch_bounds__(EPI_THREADS)
-epi_reduce_kernel(const float4 *__restrict__ part, int n_split, int npix4, float eps,
-                  float4 *__restrict__ out_main, float4 *__restrict__ rho_tmp, float4 *__restrict__ e_tmp,
-                  float4 *__restrict__ rho_pairs, float4 *__restrict__ image_as, unsigned *__restrict__ fmax)
-{
-    constexpr int NACC = Acc<NAP>::N;
-    const int f = blockIdx.y;
-    const int x = blockIdx.x * EPI_THREADS + threadIdx.x;
-    float rmax = 0.0f;
-    if (x < npix4) {
-        float4 a[NACC];
-#pragma unroll
-        for (int c = 0; c < NACC; ++c) a[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int s = 0; s < n_split; ++s) {
-            const float4 *src = part + (size_t)(f * n_split + s) * NACC * npix4 + x;
-#pragma unroll
-            for (int c = 0; c < NACC; ++c) {
-                const float4 v = src[(size_t)c * npix4];
-                a[c].x += v.x; a[c].y += v.y; a[c].z += v.z; a[c].w += v.w;
-            }
-        }
-        const size_t o = (size_t)f * npix4 + x;
-        if constexpr (NAP == 1) {
-            out_main[o] = a[0];
-        } else {
-            float4 rho, E, r12v, r23v, r31v;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float r, e;
-                if constexpr (NAP == 2) {
-                    const float r12 = ncc_pair(f4get(a[2], i), f4get(a[0], i), f4get(a[1], i), eps);
-                    f4set(r12v, i, r12);
-                    r = r12;
-                    e = f4get(a[0], i) + f4get(a[1], i) + 2.0f * f4get(a[2], i);
-                } else {
-                    const float r12 = ncc_pair(f4get(a[3], i), f4get(a[0], i), f4get(a[1], i), eps);
-                    const float r23 = ncc_pair(f4get(a[4], i), f4get(a[1], i), f4get(a[2], i), eps);
-                    const float r31 = ncc_pair(f4get(a[5], i), f4get(a[2], i), f4get(a[0], i), eps);
-                    f4set(r12v, i, r12);
-                    f4set(r23v, i, r23);
-                    f4set(r31v, i, r31);
-                    r = cbrtf(r12 * r23 * r31);  // Eq. 10
-                    e = (f4get(a[0], i) + f4get(a[1], i) + f4get(a[2], i)) +
-                        2.0f * (f4get(a[3], i) + f4get(a[4], i) + f4get(a[5], i));
-                }
-                f4set(rho, i, r);
-                f4set(E, i, fmaxf(e, 0.0f));
-                rmax = fmaxf(rmax, r);
-            }
-            rho_tmp[o] = rho;
-            e_tmp[o] = E;
-            if (image_as) image_as[o] = E;
-            if (rho_pairs) {
-                if constexpr (NAP == 2) {
-                    rho_pairs[o] = r12v;
-                } else {
-                    rho_pairs[(size_t)f * 3 * npix4 + x] = r12v;
-                    rho_pairs[(size_t)f * 3 * npix4 + npix4 + x] = r23v;
-                    rho_pairs[(size_t)f * 3 * npix4 + 2 * npix4 + x] = r31v;
-                }
-            }
-        }
-    }
-    if constexpr (NAP > 1) {
-        // block max of rho (all rho > 0, so the float bits order like unsigned ints)
-        __shared__ float wmax[EPI_THREADS / 32];
-        float m = rmax;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
-        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            m = threadIdx.x < EPI_THREADS / 32 ? wmax[threadIdx.x] : 0.0f;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
-            if (threadIdx.x == 0) atomicMax(&fmax[f], __float_as_uint(m));
-        }
-    }
-}
 
 // rho_n = rho / max (Sec. II-A: the maximum becomes exactly 1) and the image
 // I = rho_n^2 E (Eq. 5 / Eq. 11). Four pixels per thread.
@@ -422,95 +548,144 @@ epi_normalize_kernel(const float4 *__restrict__ rho_tmp, const float4 *__restric
     if (rho_n) rho_n[o] = rn;
 }
 
-template <int NAP, int NX, bool FIELDS>
-cudaError_t launch_prop_t(const pam_plan_s &p, int n_frames, int n_split, float *fields, cudaStream_t st)
+template <int NAP, int NX, bool FIELDS, bool CLUSTER>
+cudaError_t launch_prop_t(const pam_plan_s &p, int n_frames, int n_split, float *fields, const EpiOut &out,
+                          cudaStream_t st)
 {
     using S = Shape<NX>;
-    dim3 grid((p.nz + S::RPC - 1) / S::RPC, n_split, n_frames);
-    prop_corr_kernel<NAP, NX, FIELDS><<<grid, PROP_THREADS, prop_smem_bytes<NAP, NX>(), st>>>(
-        p.w.Q, p.t.phase, p.t.bin_evan, p.n_bins, p.nz, (float)p.d.z0_m, (float)p.d.dz_m, n_split,
-        p.w.part, reinterpret_cast<float2 *>(fields));
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nz + S::RPC - 1) / S::RPC, n_split, n_frames);
+    cfg.blockDim = dim3(PROP_THREADS);
+    cfg.dynamicSmemBytes = prop_smem_bytes<NAP, NX>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (CLUSTER) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 1;
+        attr[0].val.clusterDim.y = (unsigned)n_split;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaError_t e = cudaLaunchKernelEx(&cfg, prop_corr_kernel<NAP, NX, FIELDS, CLUSTER>, p.w.Q, p.t.phase,
+                                       p.t.bin_evan, p.n_bins, p.nz, (float)p.d.z0_m, (float)p.d.dz_m, n_split,
+                                       p.w.part, reinterpret_cast<float2 *>(fields), out);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int NX, bool CLUSTER>
+cudaError_t launch_prop_nc(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields,
+                           const EpiOut &out, cudaStream_t st)
+{
+    if (napq == 1) {
+        return fields ? launch_prop_t<1, NX, true, CLUSTER>(p, n_frames, n_split, fields, out, st)
+                      : launch_prop_t<1, NX, false, CLUSTER>(p, n_frames, n_split, nullptr, out, st);
+    }
+    if (napq == 2) return launch_prop_t<2, NX, false, CLUSTER>(p, n_frames, n_split, nullptr, out, st);
+    return launch_prop_t<3, NX, false, CLUSTER>(p, n_frames, n_split, nullptr, out, st);
 }
 
 template <int NX>
 cudaError_t launch_prop_nx(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields,
-                           cudaStream_t st)
+                           const EpiOut &out, cudaStream_t st)
 {
-    if (napq == 1) {
-        return fields ? launch_prop_t<1, NX, true>(p, n_frames, n_split, fields, st)
-                      : launch_prop_t<1, NX, false>(p, n_frames, n_split, nullptr, st);
-    }
-    if (napq == 2) return launch_prop_t<2, NX, false>(p, n_frames, n_split, nullptr, st);
-    return launch_prop_t<3, NX, false>(p, n_frames, n_split, nullptr, st);
+    return prop_uses_cluster(n_split) ? launch_prop_nc<NX, true>(p, n_frames, napq, n_split, fields, out, st)
+                                      : launch_prop_nc<NX, false>(p, n_frames, napq, n_split, fields, out, st);
 }
 
-template <int NAP, int NX, bool FIELDS>
+template <int NAP, int NX, bool FIELDS, bool CLUSTER>
 cudaError_t set_smem()
 {
-    return cudaFuncSetAttribute(prop_corr_kernel<NAP, NX, FIELDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)prop_smem_bytes<NAP, NX>());
+    return cudaFuncSetAttribute(prop_corr_kernel<NAP, NX, FIELDS, CLUSTER>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prop_smem_bytes<NAP, NX>());
+}
+
+template <int NX, bool CLUSTER>
+cudaError_t prepare_nc()
+{
+    cudaError_t e;
+    if ((e = set_smem<1, NX, false, CLUSTER>()) != cudaSuccess) return e;
+    if ((e = set_smem<1, NX, true, CLUSTER>()) != cudaSuccess) return e;
+    if ((e = set_smem<2, NX, false, CLUSTER>()) != cudaSuccess) return e;
+    return set_smem<3, NX, false, CLUSTER>();
 }
 
 template <int NX>
 cudaError_t prepare_nx()
 {
-    cudaError_t e;
-    if ((e = set_smem<1, NX, false>()) != cudaSuccess) return e;
-    if ((e = set_smem<1, NX, true>()) != cudaSuccess) return e;
-    if ((e = set_smem<2, NX, false>()) != cudaSuccess) return e;
-    return set_smem<3, NX, false>();
+    cudaError_t e = prepare_nc<NX, true>();
+    return e != cudaSuccess ? e : prepare_nc<NX, false>();
 }
 
 }  // namespace
 
 int prop_rows_per_cta(int nx) { return PROP_WARPS * (32 / (nx / 8)); }
 
+bool prop_uses_cluster(int n_split) { return n_split <= kMaxClusterSplit; }
+
 int choose_split(const pam_plan_s &p, int n_frames)
 {
     const int rows = prop_rows_per_cta(p.nx);
     const long long row_tiles = (p.nz + rows - 1) / rows;
-    const long long target = 2LL * p.num_sms;
-    long long ns = target / (row_tiles * n_frames);
+    long long ns;
+    if (p.split_override > 0) {
+        ns = p.split_override;
+    } else {
+        // About two CTAs per SM (the register limit) over the whole grid. The
+        // cluster reduction is used when this split is small enough anyway:
+        // capping a larger split at the cluster size loses more to load
+        // imbalance than the partial sums cost (128 x 512 frame: 9 -> 8 splits
+        // measured 135 us against 108 + 11 us).
+        const long long target = 2LL * p.num_sms;
+        ns = target / (row_tiles * n_frames);
+    }
     if (ns < 1) ns = 1;
     if (ns > p.n_bins) ns = p.n_bins;
+    // the global-partials path needs n_frames * n_split units of workspace
+    if (!prop_uses_cluster((int)ns) && (size_t)ns * n_frames > p.w.part_units)
+        ns = (long long)(p.w.part_units / n_frames) > 1 ? (long long)(p.w.part_units / n_frames) : 1;
     return (int)ns;
 }
 
-cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields, cudaStream_t st)
+cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields, const EpiOut &out,
+                        cudaStream_t st)
 {
     switch (p.nx) {
-    case 16: return launch_prop_nx<16>(p, n_frames, napq, n_split, fields, st);
-    case 32: return launch_prop_nx<32>(p, n_frames, napq, n_split, fields, st);
-    case 64: return launch_prop_nx<64>(p, n_frames, napq, n_split, fields, st);
-    case 128: return launch_prop_nx<128>(p, n_frames, napq, n_split, fields, st);
+    case 16: return launch_prop_nx<16>(p, n_frames, napq, n_split, fields, out, st);
+    case 32: return launch_prop_nx<32>(p, n_frames, napq, n_split, fields, out, st);
+    case 64: return launch_prop_nx<64>(p, n_frames, napq, n_split, fields, out, st);
+    case 128: return launch_prop_nx<128>(p, n_frames, napq, n_split, fields, out, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, float *out_main,
-                            float *rho_n, float *rho_pairs, float *image_as, cudaStream_t st)
+cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, const EpiOut &out,
+                            cudaStream_t st)
 {
     const int npix4 = p.nz * p.nx / 4;  // nx is a multiple of 16
     dim3 grid((npix4 + EPI_THREADS - 1) / EPI_THREADS, n_frames);
-    const float4 *part = reinterpret_cast<const float4 *>(p.w.part);
     auto v4 = [](float *q) { return reinterpret_cast<float4 *>(q); };
-    if (napq == 1) {
-        epi_reduce_kernel<1><<<grid, EPI_THREADS, 0, st>>>(part, n_split, npix4, p.d.eps, v4(out_main), nullptr,
-                                                           nullptr, nullptr, nullptr, nullptr);
-        return cudaGetLastError();
+    if (!prop_uses_cluster(n_split)) {
+        const float4 *part = reinterpret_cast<const float4 *>(p.w.part);
+        dim3 rgrid((npix4 + 31) / 32, n_frames);
+        if (napq == 1)
+            epi_reduce_kernel<1><<<rgrid, 32 * Acc<1>::N, 0, st>>>(part, n_split, npix4, out);
+        else if (napq == 2)
+            epi_reduce_kernel<2><<<rgrid, 32 * Acc<2>::N, 0, st>>>(part, n_split, npix4, out);
+        else
+            epi_reduce_kernel<3><<<rgrid, 32 * Acc<3>::N, 0, st>>>(part, n_split, npix4, out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    if (napq == 2)
-        epi_reduce_kernel<2><<<grid, EPI_THREADS, 0, st>>>(part, n_split, npix4, p.d.eps, nullptr, v4(p.w.rho_tmp),
-                                                           v4(p.w.e_tmp), v4(rho_pairs), v4(image_as), p.w.fmax);
-    else
-        epi_reduce_kernel<3><<<grid, EPI_THREADS, 0, st>>>(part, n_split, npix4, p.d.eps, nullptr, v4(p.w.rho_tmp),
-                                                           v4(p.w.e_tmp), v4(rho_pairs), v4(image_as), p.w.fmax);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    epi_normalize_kernel<<<grid, EPI_THREADS, 0, st>>>(v4(p.w.rho_tmp), v4(p.w.e_tmp), p.w.fmax, npix4, v4(out_main),
-                                                       v4(rho_n));
+    if (napq == 1) return cudaSuccess;
+    epi_normalize_kernel<<<grid, EPI_THREADS, 0, st>>>(v4(out.rho_tmp), v4(out.e_tmp), out.fmax, npix4,
+                                                       v4(out.out_main), v4(out.rho_n));
     return cudaGetLastError();
+}
+
+int epilogue_kernels(int napq, int n_split)
+{
+    return (prop_uses_cluster(n_split) ? 0 : 1) + (napq > 1 ? 1 : 0);
 }
 
 cudaError_t prepare_kernels(const pam_plan_s &p)

@@ -103,8 +103,10 @@ size_t carve(pam_plan_s &p, int n_split, unsigned char *base)
     p.t.bin_evan = static_cast<int *>(take(nb * sizeof(int)));
     p.w.S = static_cast<float2 *>(take(nb * ne * sizeof(float2)));
     p.w.Q = static_cast<float2 *>(take(nb * 3 * nx * sizeof(float2)));
-    p.w.part = static_cast<float *>(take((size_t)n_split * 6 * npix * sizeof(float)));
-    p.w.part_units = (size_t)n_split;
+    // split reductions up to the cluster size stay on chip; larger ones need partials
+    const size_t units = pam::prop_uses_cluster(n_split) ? 0 : (size_t)n_split;
+    p.w.part = static_cast<float *>(take(units * 6 * npix * sizeof(float)));
+    p.w.part_units = units;
     p.w.rho_tmp = static_cast<float *>(take(npix * sizeof(float)));
     p.w.e_tmp = static_cast<float *>(take(npix * sizeof(float)));
     p.w.fmax = static_cast<unsigned *>(take(sizeof(unsigned)));
@@ -186,9 +188,11 @@ extern "C" pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf,
     e = cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "device query");
 
-    // Largest bin split whose workspace fits the fixed scratch.
+    // Bin split of the automatic choice, capped at the cluster size so that the
+    // split reduction needs no scratch.
+    p.w.part_units = (size_t)-1;
     int ns = pam::choose_split(p, 1);
-    while (ns > 1 && carve(p, ns, nullptr) > kScratchBytes) --ns;
+    if (ns > pam::kMaxClusterSplit) ns = pam::kMaxClusterSplit;
     const size_t need = carve(p, ns, nullptr);
     if (need > kScratchBytes) {
         char m[200];
@@ -220,10 +224,18 @@ extern "C" pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf,
     for (int f = 0; f < n_frames; ++f) {
         if ((e = pam::launch_time_fft(p, rf + f * fr_in, 1, st)) != cudaSuccess) return cuda_fail(e, "time FFT");
         if ((e = pam::launch_lateral(p, 1, 3, p.t.apod, st)) != cudaSuccess) return cuda_fail(e, "lateral DFT");
-        if ((e = pam::launch_prop(p, 1, 3, ns, nullptr, st)) != cudaSuccess) return cuda_fail(e, "propagate/correlate");
-        if ((e = pam::launch_epilogue(p, 1, 3, ns, image_tax + f * npix, rho_n ? rho_n + f * npix : nullptr, nullptr,
-                                      nullptr, st)) != cudaSuccess)
-            return cuda_fail(e, "epilogue");
+        pam::EpiOut out;
+        out.eps = d->eps;
+        out.npix = (int)npix;
+        out.out_main = image_tax + f * npix;
+        out.rho_n = rho_n ? rho_n + f * npix : nullptr;
+        out.rho_tmp = p.w.rho_tmp;
+        out.e_tmp = p.w.e_tmp;
+        out.fmax = p.w.fmax;
+        out.status = p.w.status;
+        if ((e = pam::launch_prop(p, 1, 3, ns, nullptr, out, st)) != cudaSuccess)
+            return cuda_fail(e, "propagate/correlate");
+        if ((e = pam::launch_epilogue(p, 1, 3, ns, out, st)) != cudaSuccess) return cuda_fail(e, "epilogue");
     }
     return PAM_OK;
 }

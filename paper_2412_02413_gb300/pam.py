@@ -53,6 +53,7 @@ _SIGS = {
     "pam_destroy": (None, [_VP]),
     "pam_plan_bins": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "pam_plan_apod": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
+    "pam_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_as_backprop": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
     "pam_as_tax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pam_as_dax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
@@ -267,6 +268,10 @@ class Plan:
         _check(load().pam_as_xcorr_host(self._h, rf_host.ctypes.data, F, image_out.ctypes.data,
                                         None if rho_n_out is None else rho_n_out.ctypes.data,
                                         _stream_ptr(stream)))
+
+    def set_split(self, n_split: int = 0):
+        """Bin chunks per row tile of the fused kernel (0 = automatic)."""
+        _check(load().pam_plan_set_split(self._h, int(n_split)))
 
     def profile_enable(self, on: bool = True):
         """Record CUDA events around each propagate-and-correlate launch."""

@@ -70,11 +70,12 @@ def test_small_tax_parity(ne, nt, nz, nbins):
     compare_xcorr(out, orc, check_peak=False)
 
 
-@pytest.mark.parametrize("apod_index", [-1, 1])
-def test_backprop_energy_and_fields(apod_index):
+@pytest.mark.parametrize("apod_index,split", [(-1, 0), (1, 0), (-1, 2)])
+def test_backprop_energy_and_fields(apod_index, split):
     w = _tiny(16, 128, 9)
     rf = synth.random_rf(16, 128, seed=7)
     plan = _plan(w)
+    plan.set_split(split)
     e, fl = plan.as_backprop(torch.from_numpy(rf).cuda(), apod_index=apod_index, fields=True)
     torch.cuda.synchronize()
     a = None if apod_index < 0 else oracle.pattern(16, 3, 2)[apod_index]
@@ -125,6 +126,18 @@ def test_workload1_parity(w1_frames):
         out = _run_tax(plan, frames[f][0])
         m = compare_xcorr(out, orc[f])
         assert m["peak_margin"] > 10 * REL_L2_TOL, m
+
+
+@pytest.mark.parametrize("split", [1, 3, 8, 12])
+def test_split_paths_match_oracle(w1_frames, split):
+    """Splits up to 8 reduce inside a thread-block cluster, larger ones through
+    global partial sums; both must agree with the oracle."""
+    w, frames, orc = w1_frames
+    plan = _pam().Plan.from_workload(w)
+    plan.set_split(split)
+    compare_xcorr(_run_tax(plan, frames[0][0]), orc[0])
+    e = plan.as_backprop(torch.from_numpy(frames[0][0]).cuda())
+    assert rel_l2(e[0].cpu().numpy(), orc[0]["image_as"]) < REL_L2_TOL
 
 
 def test_workload1_batched_frames(w1_frames):
@@ -298,9 +311,11 @@ def test_profile_counters():
     w = _tiny(32, 256, 10)
     plan = _plan(w)
     rf = torch.from_numpy(synth.random_rf(32, 256, seed=26)).cuda()
-    plan.profile_enable(True)
-    for _ in range(3):
-        plan.as_tax(rf)
-    ms, n, k = plan.profile_read()
-    assert n == 3 and k == 15 and ms > 0
+    for split, kernels in ((4, 4), (16, 5)):   # cluster path / global-partials path
+        plan.set_split(split)
+        plan.profile_enable(True)
+        for _ in range(3):
+            plan.as_tax(rf)
+        ms, n, k = plan.profile_read()
+        assert n == 3 and k == 3 * kernels and ms > 0
     plan.profile_enable(False)

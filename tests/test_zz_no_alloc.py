@@ -62,7 +62,7 @@ def test_static_entry_rejects_oversize_geometry():
     from paper_2412_02413_gb300 import pam
     L = pam.load()
     w = synth.workload(2)
-    w.nz = 4096                      # 4096 x 128 pixels need far more than the fixed array
+    w.nz = 32768                     # 32768 x 128 pixels need far more than the fixed array
     bins = np.ascontiguousarray(w.bins(), dtype=np.int32)
     d = _desc(pam, w, bins)
     rf = torch.zeros(1, w.n_elem, w.nt, device="cuda")
