@@ -286,6 +286,46 @@ def run_ours(args):
     t_e2e = dist.max_over_ranks(t_e2e, device=dev)
     e2e_value = dist.sum_over_ranks(e2e_steps * F, device=dev) / t_e2e
 
+    # Batched forms: 64 frames per call, the plain FP32 path and the tensor-core forms.
+    forms = {}
+    if not args.no_forms:
+        ref_img = None
+        for form in ("fp32", "bf16", "fp16", "bf16split"):
+            fp = pam.Plan.from_workload(w, max_frames=args.batch, form=form)
+            fo = {"image": torch.empty(args.batch, w.nz, w.nx, device=dev),
+                  "rho_n": torch.empty(args.batch, w.nz, w.nx, device=dev)}
+            nb = max(1, P // args.batch)
+
+            def bstep(i):
+                s0 = (i % nb) * args.batch
+                fp.as_tax(pool[s0:s0 + args.batch], outs=fo, stream=stream)
+
+            for i in range(3):
+                bstep(i)
+            torch.cuda.synchronize()
+            fp.profile_enable(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(args.batch_steps):
+                bstep(i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            kms, kn, kl = fp.profile_read()
+            fms = e0.elapsed_time(e1)
+            bstep(0)
+            torch.cuda.synchronize()
+            img = fo["image"].double()
+            entry = {"frames_per_call": args.batch, "value": args.batch * args.batch_steps / (fms / 1000.0),
+                     "unit": "frames/s", "ms_per_frame": fms / (args.batch * args.batch_steps),
+                     "main_kernel_us_per_frame": 1000.0 * kms / max(kn, 1) / args.batch}
+            if form == "fp32":
+                ref_img = img
+            else:
+                entry["rel_l2_vs_fp32"] = float(torch.linalg.norm(img - ref_img) / torch.linalg.norm(ref_img))
+            forms[form] = entry
+            fp.close()
+
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tf = fp32_peak_tflops(sm_max)
@@ -319,6 +359,7 @@ def run_ours(args):
                          "flops_per_launch": flops, "avg_launch_us": avg_launch_s * 1e6,
                          "share_of_step": (prop_ms / ms) if ms > 0 else None},
             "clocks": ck,
+            "forms": forms,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -338,6 +379,9 @@ def main():
     ap.add_argument("--pool", type=int, default=POOL_FRAMES)
     ap.add_argument("--cpu-budget", type=float, default=8.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched plain / tensor-core forms")
+    ap.add_argument("--batch", type=int, default=64, help="frames per call of the batched forms")
+    ap.add_argument("--batch-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -64,6 +64,19 @@ typedef enum {
 
 /* descriptor flags */
 #define PAM_EVANESCENT_ZERO 0x1u /* drop components with kx^2 > (w/c)^2 instead of decaying them */
+/* Tensor-core form of the propagation (at most one of these; default = plain FP32 FFT path).
+ * For a bin w_k and depth row z_j, the element-to-pixel propagator of Eq. 1-2 is circulant:
+ *   p~(x_i, z_j) = sum_e c_j[(i - e) mod nx] a_q[e] S[e],
+ *   c_j[d] = (1/nx) sum_u exp(i kz_u z_j) exp(+2 pi i u d / nx).
+ * The plan tabulates c_j (from the FP64 phase words) in 16-bit form. Each call runs the
+ * sum over elements as a tcgen05 GEMM [pixels x elements] x [elements x frames], with FP32
+ * accumulation in tensor memory. The three apodizations are disjoint K-slices of one GEMM.
+ * Requirements: nx == 128, n_apod 2 or 3, apertures with disjoint element sets.
+ * Typical relative L2 error of I_TAX against the FP64 oracle at 128 elements, 300 bins:
+ * BF16 about 5e-4, FP16 about 6e-5, BF16 split about 2e-6. */
+#define PAM_FORM_GEMM_BF16 0x10u       /* BF16 operands */
+#define PAM_FORM_GEMM_FP16 0x20u       /* FP16 operands (frames scaled by a power of 2) */
+#define PAM_FORM_GEMM_BF16_SPLIT 0x40u /* BF16 hi + lo split: hi*hi + hi*lo + lo*hi */
 
 /* Acquisition and imaging geometry (Sec. II-A, Fig. 1; band selection Sec. II-D). */
 typedef struct {
@@ -84,7 +97,7 @@ typedef struct {
     const float *apod;    /* host [n_apod][n_elem] real weights, or NULL for Pattern-m */
     int pattern_m;        /* Pattern-m (Sec. II-A): element e in aperture q iff floor(e/m) mod n_apod == q */
     float eps;            /* NCC floor (Sec. II-A, usually 0.001), 0 < eps <= 1 */
-    unsigned flags;       /* PAM_EVANESCENT_ZERO */
+    unsigned flags;       /* PAM_EVANESCENT_ZERO, at most one PAM_FORM_GEMM_* */
     int max_frames;       /* frames per kernel batch; larger calls run in batches of this size */
 } pam_plan_desc;
 

@@ -63,6 +63,7 @@ void free_plan_memory(pam_plan_s *p)
     fr(p->t.phase); fr(p->t.live); fr(p->t.bin_evan);
     fr(p->w.S); fr(p->w.Q); fr(p->w.part); fr(p->w.rho_tmp); fr(p->w.e_tmp);
     fr(p->w.fmax); fr(p->w.status); fr(p->w.rf_stage); fr(p->w.img_stage); fr(p->w.rho_stage);
+    fr(p->t.c_hi); fr(p->t.c_lo); fr(p->t.ktab); fr(p->t.kwgt); fr(p->w.Bhi); fr(p->w.Blo); fr(p->w.smax);
     p->t = pam::Tables{};
     p->w = pam::Workspace{};
 }
@@ -108,7 +109,10 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     if (d->n_apod < 1 || d->n_apod > 3) return fail(PAM_ERR_INVALID_ARG, "n_apod must be 1, 2 or 3");
     if (!(d->eps > 0.0f) || !(d->eps <= 1.0f)) return fail(PAM_ERR_INVALID_ARG, "eps must be in (0, 1]");
     if (d->max_frames < 1 || d->max_frames > 65535) return fail(PAM_ERR_INVALID_ARG, "max_frames must be in [1, 65535]");
-    if (d->flags & ~PAM_EVANESCENT_ZERO) return fail(PAM_ERR_INVALID_ARG, "unknown flag bits");
+    const unsigned form_bits = PAM_FORM_GEMM_BF16 | PAM_FORM_GEMM_FP16 | PAM_FORM_GEMM_BF16_SPLIT;
+    if (d->flags & ~(PAM_EVANESCENT_ZERO | form_bits)) return fail(PAM_ERR_INVALID_ARG, "unknown flag bits");
+    const unsigned form = d->flags & form_bits;
+    if (form & (form - 1)) return fail(PAM_ERR_INVALID_ARG, "at most one PAM_FORM_GEMM_* flag");
 
     const int nt = d->n_samples;
     p->bins.clear();
@@ -158,6 +162,49 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     p->n_bins = (int)p->bins.size();
     p->n_apod = na;
     p->max_frames = d->max_frames;
+    p->form = (int)form;
+    if (form) {
+        // Tensor-core form: apertures become disjoint K ranges of one GEMM. Each range
+        // holds the aperture's elements (padded with empty columns to a multiple of 8)
+        // twice: once to pair with Re c, once with Im c.
+        if (nx != 128) return fail(PAM_ERR_UNSUPPORTED, "the tensor-core form needs nx == 128");
+        if (na < 2) return fail(PAM_ERR_INVALID_ARG, "the tensor-core form is built for AS-DAX and AS-TAX");
+        p->ktab_h.clear();
+        p->kwgt_h.clear();
+        int k = 0;
+        for (int q = 0; q < na; ++q) {
+            std::vector<int> els;
+            for (int e = 0; e < ne; ++e) {
+                if (p->apod[(size_t)q * ne + e] == 0.0f) continue;
+                for (int r = 0; r < q; ++r)
+                    if (p->apod[(size_t)r * ne + e] != 0.0f)
+                        return fail(PAM_ERR_UNSUPPORTED, "the tensor-core form needs disjoint apertures");
+                els.push_back(e);
+            }
+            const int padded = (int)((els.size() + 7) / 8 * 8);
+            p->kq[q] = k;
+            for (int half = 0; half < 2; ++half)
+                for (int t = 0; t < padded; ++t) {
+                    const bool real_el = t < (int)els.size();
+                    p->ktab_h.push_back(real_el ? (short)(els[t] | (half << 14)) : (short)-1);
+                    p->kwgt_h.push_back(real_el ? p->apod[(size_t)q * ne + els[t]] : 0.0f);
+                }
+            k += 2 * padded;
+        }
+        for (int q = na; q < 4; ++q) p->kq[q] = k;
+        p->K = k;
+        if (k == 0 || k > pam::kMaxGemmK) return fail(PAM_ERR_UNSUPPORTED, "aperture element counts exceed the GEMM depth");
+        // Pattern-m apertures with m a multiple of 8 make every chunk of 8 K columns a run of
+        // consecutive elements, which the GEMM kernel expands with aligned 16-byte copies.
+        p->fast_expand = true;
+        for (int c = 0; c < k / 8 && p->fast_expand; ++c) {
+            const short k0 = p->ktab_h[(size_t)c * 8];
+            for (int t = 1; t < 8; ++t) {
+                const short kt = p->ktab_h[(size_t)c * 8 + t];
+                if (k0 < 0 ? kt >= 0 : kt != (short)(k0 + t)) p->fast_expand = false;
+            }
+        }
+    }
     return PAM_OK;
 }
 
@@ -196,6 +243,21 @@ pam_status alloc_plan(pam_plan_s *p)
     PAM_TRY(dalloc(&p->w.e_tmp, F * npix));
     PAM_TRY(dalloc(&p->w.fmax, F));
     PAM_TRY(dalloc(&p->w.status, 1));
+    if (p->form) {
+        const bool split = p->form == PAM_FORM_GEMM_BF16_SPLIT;
+        const size_t rows = nb * (size_t)p->nz * nx;
+        const size_t groups = (F + pam::kFramesPerGroup - 1) / pam::kFramesPerGroup;
+        const size_t tile16 = (size_t)p->K * 2 * pam::kFramesPerGroup * 2 / 16;   // uint4 per (group, bin) tile
+        PAM_TRY(dalloc(&p->t.c_hi, rows));
+        if (split) PAM_TRY(dalloc(&p->t.c_lo, rows));
+        PAM_TRY(dalloc(&p->t.ktab, (size_t)p->K));
+        PAM_TRY(dalloc(&p->t.kwgt, (size_t)p->K));
+        PAM_TRY(dalloc(&p->w.Bhi, groups * nb * tile16));
+        if (split) PAM_TRY(dalloc(&p->w.Blo, groups * nb * tile16));
+        PAM_TRY(dalloc(&p->w.smax, F));
+        PAM_TRY(cudaMemcpy(p->t.ktab, p->ktab_h.data(), p->K * sizeof(short), cudaMemcpyHostToDevice));
+        PAM_TRY(cudaMemcpy(p->t.kwgt, p->kwgt_h.data(), p->K * sizeof(float), cudaMemcpyHostToDevice));
+    }
     PAM_TRY(cudaMemset(p->w.status, 0, sizeof(int)));
     PAM_TRY(cudaMemcpy(p->t.bins, p->bins.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
     PAM_TRY(cudaMemcpy(p->t.apod, p->apod.data(), p->apod.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -255,6 +317,20 @@ pam_status run_xcorr(pam_plan_t p, const float *rf, int n_frames, float *image, 
         int Fc = std::min(p->max_frames, n_frames - f0);
         cudaError_t e = pam::launch_time_fft(*p, rf + (size_t)f0 * fr_in, Fc, st);
         if (e != cudaSuccess) return cuda_fail(e, "time FFT launch");
+        if (p->form) {
+            // tensor-core form: pack operands, GEMM per (row, bin), epilogue from its sums
+            pam::EpiOut out = epi_out(p, image + (size_t)f0 * npix, rho_n ? rho_n + (size_t)f0 * npix : nullptr,
+                                      rho_pairs ? rho_pairs + (size_t)f0 * npairs * npix : nullptr,
+                                      image_as ? image_as + (size_t)f0 * npix : nullptr);
+            if ((e = prof_begin(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
+            e = pam::launch_prec(*p, Fc, st);
+            if (e != cudaSuccess) return cuda_fail(e, "tensor-core form launch");
+            if ((e = prof_end(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
+            e = pam::launch_epilogue(*p, Fc, p->n_apod, 1, out, st, true);
+            if (e != cudaSuccess) return cuda_fail(e, "epilogue launch");
+            p->kernels += 1 + pam::prec_kernels() + 2;
+            continue;
+        }
         e = pam::launch_lateral(*p, Fc, p->n_apod, p->t.apod, st);
         if (e != cudaSuccess) return cuda_fail(e, "lateral DFT launch");
         int ns = pam::choose_split(*p, Fc);
@@ -305,7 +381,9 @@ pam_status pam_plan_create(const pam_plan_desc *d, pam_plan_t *out)
         return s;
     }
     e = pam::prepare_kernels(*p);
+    if (e == cudaSuccess && p->form) e = pam::prepare_prec_kernels();
     if (e == cudaSuccess) e = pam::launch_tables(*p, 0);
+    if (e == cudaSuccess && p->form) e = pam::launch_prec_tables(*p, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
         free_plan_memory(p);

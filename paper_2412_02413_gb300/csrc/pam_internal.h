@@ -12,6 +12,10 @@
 
 namespace pam {
 
+// Frames per CTA of the tensor-core form (N = 2 * frames GEMM columns).
+constexpr int kFramesPerGroup = 32;
+constexpr int kMaxGemmK = 320;     // 2 x padded element count of the tensor-core form
+
 // Rows of the depth grid handled by one CTA of the fused propagate-and-correlate
 // kernel for a lateral length nx (8 warps; 2*nx/16 lanes per row).
 int prop_rows_per_cta(int nx);
@@ -46,6 +50,9 @@ struct Workspace {
     float *e_tmp = nullptr;     // [max_frames][nz][nx]              sum_k |sum_q p_q|^2
     unsigned *fmax = nullptr;   // [max_frames]                      max rho bits per frame
     int *status = nullptr;      // device status word
+    // tensor-core form: packed S operand tiles and the per-frame power-of-2 scale
+    uint4 *Bhi = nullptr, *Blo = nullptr;   // [groups][n_bins][K * 2 * kFramesPerGroup * 2 bytes]
+    unsigned *smax = nullptr;               // [max_frames] max |Re S|, |Im S| bits
     // host-buffer entry point staging (allocated on first use)
     float *rf_stage = nullptr, *img_stage = nullptr, *rho_stage = nullptr;
 };
@@ -62,6 +69,12 @@ struct Tables {
     // components (amplitude exp2(ecoef*z)), 0 otherwise.
     uint4 *phase = nullptr;
     float *live = nullptr;        // [n_bins][nx] 1, or 0 for dropped evanescent components
+    // tensor-core form: per (bin, depth row) the propagator point-spread c_j[d], d < nx,
+    // as packed 16-bit (re, im) pairs; hi part and the rounding residual (lo)
+    uint32_t *c_hi = nullptr;     // [n_bins][nz][nx]
+    uint32_t *c_lo = nullptr;     // [n_bins][nz][nx] (split form only)
+    short *ktab = nullptr;        // [K] element of each K column, +0x4000 for the imaginary half, -1 = pad
+    float *kwgt = nullptr;        // [K] apodization weight of that element
     int *bin_evan = nullptr;      // [n_bins] 1 if any live evanescent component in the bin
 };
 
@@ -81,6 +94,13 @@ struct pam_plan_s {
     size_t prof_used = 0;              // events recorded since the last read
     long long kernels = 0;             // libpam kernel launches since the last read
     int split_override = 0;            // pam_plan_set_split (0 = automatic)
+    // tensor-core form (PAM_FORM_GEMM_*): 0 = plain FP32 path
+    int form = 0;
+    int K = 0;                         // GEMM depth: 2 x padded element count
+    int kq[4] = {0, 0, 0, 0};          // K range of aperture q: [kq[q], kq[q+1])
+    bool fast_expand = false;          // every K chunk of 8 is 8 consecutive elements (or empty)
+    std::vector<short> ktab_h;         // host copies of Tables::ktab / kwgt
+    std::vector<float> kwgt_h;
 };
 
 namespace pam {
@@ -96,10 +116,17 @@ cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split
 // The rest of the epilogue: the partial reduction (no cluster) and the rho
 // normalisation (DAX / TAX).
 cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, const EpiOut &out,
-                            cudaStream_t st);
+                            cudaStream_t st, bool from_partials = false);
 int epilogue_kernels(int napq, int n_split);   // kernels launch_epilogue launches
 bool prop_uses_cluster(int n_split);
 cudaError_t prepare_kernels(const pam_plan_s &p);
+
+// Tensor-core form (pam_prec.cu): plan-time point-spread table, and the per-call
+// operand packing + GEMM whose per-pixel sums feed launch_epilogue (split 1).
+cudaError_t launch_prec_tables(const pam_plan_s &p, cudaStream_t st);
+cudaError_t launch_prec(const pam_plan_s &p, int n_frames, cudaStream_t st);
+cudaError_t prepare_prec_kernels();
+int prec_kernels();   // kernels launch_prec launches
 
 // Records `msg` as the calling thread's pam_last_error() text and returns s.
 pam_status set_error(pam_status s, const char *msg);

@@ -660,12 +660,12 @@ cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split
 }
 
 cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, const EpiOut &out,
-                            cudaStream_t st)
+                            cudaStream_t st, bool from_partials)
 {
     const int npix4 = p.nz * p.nx / 4;  // nx is a multiple of 16
     dim3 grid((npix4 + EPI_THREADS - 1) / EPI_THREADS, n_frames);
     auto v4 = [](float *q) { return reinterpret_cast<float4 *>(q); };
-    if (!prop_uses_cluster(n_split)) {
+    if (from_partials || !prop_uses_cluster(n_split)) {
         const float4 *part = reinterpret_cast<const float4 *>(p.w.part);
         dim3 rgrid((npix4 + 31) / 32, n_frames);
         if (napq == 1)

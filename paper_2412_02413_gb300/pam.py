@@ -19,6 +19,8 @@ from . import build as _build
 
 PAM_OK = 0
 PAM_EVANESCENT_ZERO = 0x1
+# tensor-core forms of the propagation (include/pam.h PAM_FORM_GEMM_*)
+FORMS = {"fp32": 0x0, "bf16": 0x10, "fp16": 0x20, "bf16split": 0x40}
 _STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_UNSUPPORTED", 3: "PAM_ERR_OOM",
            4: "PAM_ERR_CUDA", 5: "PAM_ERR_TIMEOUT", 6: "PAM_ERR_NUMERIC"}
 
@@ -122,7 +124,7 @@ class Plan:
     def __init__(self, n_elem: int, pitch: float, fs: float, c: float, n_samples: int, nz: int,
                  z0: float, dz: float, bins: Optional[Sequence[int]] = None, f_lo: float = 0.0,
                  f_hi: float = 0.0, n_apod: int = 3, apod=None, pattern_m: int = 16, eps: float = 1e-3,
-                 evanescent_zero: bool = False, max_frames: int = 1, nx: int = 0):
+                 evanescent_zero: bool = False, max_frames: int = 1, nx: int = 0, form: str = "fp32"):
         _require_cuda()
         L = load()
         d = PlanDesc()
@@ -141,7 +143,9 @@ class Plan:
             self._apod_keep = np.ascontiguousarray(np.asarray(apod, dtype=np.float32))
             d.apod = self._apod_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         d.pattern_m, d.eps = int(pattern_m), float(eps)
-        d.flags = PAM_EVANESCENT_ZERO if evanescent_zero else 0
+        if form not in FORMS:
+            raise ValueError(f"form must be one of {sorted(FORMS)}")
+        d.flags = (PAM_EVANESCENT_ZERO if evanescent_zero else 0) | FORMS[form]
         d.max_frames = int(max_frames)
         h = _VP()
         _check(L.pam_plan_create(ctypes.byref(d), ctypes.byref(h)))
@@ -149,6 +153,7 @@ class Plan:
         self.n_elem, self.n_samples, self.nz, self.n_apod = int(n_elem), int(n_samples), int(nz), int(n_apod)
         self.nx = self.n_elem if not nx else int(nx)
         self.max_frames = int(max_frames)
+        self.form = form
         self.bins = self._query_bins()
         self.apod = self._query_apod()
 

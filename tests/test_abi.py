@@ -75,7 +75,8 @@ def test_desc_defaults(lib):
     ("n_elem", 4, 1), ("n_elem", 300, 1), ("pitch_m", 0.0, 1), ("fs_hz", -1.0, 1),
     ("c_mps", float("nan"), 1), ("n_samples", 1000, 2), ("n_samples", 32, 1), ("n_samples", 16384, 2),
     ("nz", 0, 1), ("z0_m", -1e-3, 1), ("dz_m", 0.0, 1), ("n_apod", 4, 1), ("eps", 0.0, 1),
-    ("eps", 1.5, 1), ("max_frames", 0, 1), ("flags", 0x10, 1), ("nx", 128, 2), ("pattern_m", 0, 1),
+    ("eps", 1.5, 1), ("max_frames", 0, 1), ("flags", 0x100, 1), ("flags", 0x30, 1), ("flags", 0x10, 2),
+    ("nx", 128, 2), ("pattern_m", 0, 1),
     ("f_lo_hz", 9e6, 1),
 ])
 def test_bad_descriptor_is_rejected(lib, field, value, status):

@@ -319,3 +319,55 @@ def test_profile_counters():
         ms, n, k = plan.profile_read()
         assert n == 3 and k == 3 * kernels and ms > 0
     plan.profile_enable(False)
+
+
+# ------------------------------------------------------ tensor-core form --
+# The propagation as a tcgen05 GEMM with 16-bit operands. Tolerances are those
+# stated for the chosen forms: relative L2 <= 1e-2 on the energy maps and the
+# same brightest pixel; NCC deviations are reported. The hi + lo split recovers
+# close to FP32 agreement.
+FORM_TOL = {"bf16": (1e-2, 5e-2), "fp16": (1e-2, 2e-2), "bf16split": (1e-4, 1e-3)}
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16", "bf16split"])
+def test_gemm_form_workload2(w2_frame, form):
+    w, rf, src, orc = w2_frame
+    plan = _pam().Plan.from_workload(w, max_frames=1, form=form)
+    out = _run_tax(plan, rf)
+    img = out["image"][0].cpu().numpy()
+    err = {k: rel_l2(out[k][0].cpu().numpy(), orc[k]) for k in ("image", "image_as")}
+    ncc = float(np.max(np.abs(out["rho_pairs"][0].cpu().numpy() - orc["rho_pairs"])))
+    rn = float(np.max(np.abs(out["rho_n"][0].cpu().numpy() - orc["rho_n"])))
+    print(f"\n{form}: rel L2 image {err['image']:.3e} image_as {err['image_as']:.3e} "
+          f"max|dNCC| {ncc:.3e} max|d rho_n| {rn:.3e}")
+    l2_tol, ncc_tol = FORM_TOL[form]
+    assert err["image"] <= l2_tol and err["image_as"] <= l2_tol, err
+    assert ncc <= ncc_tol and rn <= ncc_tol, (ncc, rn)
+    assert peak(img) == peak(orc["image"])
+
+
+@pytest.mark.parametrize("form", ["bf16", "fp16"])
+def test_gemm_form_frame_groups(form):
+    """20 frames: two groups of 16 frames (the second one ragged) in one call,
+    each frame against the oracle."""
+    w = _tiny(128, 512, 24, bins=12, fs=40e6, f_lo=1e6, f_hi=8e6, pattern_m=16)
+    frames = synth.random_rf(128, 512, seed=31, n_frames=20)
+    frames[3] *= 1000.0                # frame scale must not matter (per-frame power-of-2 scaling)
+    plan = _plan(w, max_frames=20, form=form)
+    out = _run_tax(plan, frames)
+    g = _geom(w)
+    A = oracle.pattern(128, 3, 16)
+    worst = 0.0
+    for f in (0, 3, 15, 16, 19):
+        orc = oracle.as_tax(g, frames[f], A)
+        worst = max(worst, rel_l2(out["image_as"][f].cpu().numpy(), orc["image_as"]))
+    assert worst <= FORM_TOL[form][0], worst
+
+
+def test_gemm_form_rejects_unsupported():
+    pam = _pam()
+    with pytest.raises(pam.PamError):
+        _plan(_tiny(64, 512, 8), form="bf16")                       # nx must be 128
+    w = _tiny(128, 512, 8, pattern_m=16)
+    with pytest.raises(pam.PamError):
+        _plan(w, apod=np.ones((3, 128), np.float32), form="bf16")    # apertures must be disjoint
