@@ -164,46 +164,36 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     p->max_frames = d->max_frames;
     p->form = (int)form;
     if (form) {
-        // Tensor-core form: apertures become disjoint K ranges of one GEMM. Each range
-        // holds the aperture's elements (padded with empty columns to a multiple of 8)
-        // twice: once to pair with Re c, once with Im c.
+        // Tensor-core form: each aperture is a K range of one GEMM made of the aligned
+        // 8-element blocks it touches (elements of the block outside the aperture get
+        // weight 0). A block takes 16 K columns: 8 pairing with Re c, 8 with Im c.
         if (nx != 128) return fail(PAM_ERR_UNSUPPORTED, "the tensor-core form needs nx == 128");
         if (na < 2) return fail(PAM_ERR_INVALID_ARG, "the tensor-core form is built for AS-DAX and AS-TAX");
         p->ktab_h.clear();
         p->kwgt_h.clear();
         int k = 0;
         for (int q = 0; q < na; ++q) {
-            std::vector<int> els;
-            for (int e = 0; e < ne; ++e) {
-                if (p->apod[(size_t)q * ne + e] == 0.0f) continue;
-                for (int r = 0; r < q; ++r)
-                    if (p->apod[(size_t)r * ne + e] != 0.0f)
-                        return fail(PAM_ERR_UNSUPPORTED, "the tensor-core form needs disjoint apertures");
-                els.push_back(e);
-            }
-            const int padded = (int)((els.size() + 7) / 8 * 8);
             p->kq[q] = k;
-            for (int half = 0; half < 2; ++half)
-                for (int t = 0; t < padded; ++t) {
-                    const bool real_el = t < (int)els.size();
-                    p->ktab_h.push_back(real_el ? (short)(els[t] | (half << 14)) : (short)-1);
-                    p->kwgt_h.push_back(real_el ? p->apod[(size_t)q * ne + els[t]] : 0.0f);
-                }
-            k += 2 * padded;
+            for (int m = 0; m < nx / 8; ++m) {
+                bool used = false;
+                for (int t = 0; t < 8; ++t) used = used || (8 * m + t < ne && p->apod[(size_t)q * ne + 8 * m + t] != 0.0f);
+                if (!used) continue;
+                for (int half = 0; half < 2; ++half)
+                    for (int t = 0; t < 8; ++t) {
+                        const int e = 8 * m + t;
+                        p->ktab_h.push_back(e < ne ? (short)(e | (half << 14)) : (short)-1);
+                        p->kwgt_h.push_back(e < ne ? p->apod[(size_t)q * ne + e] : 0.0f);
+                    }
+                k += 16;
+            }
         }
         for (int q = na; q < 4; ++q) p->kq[q] = k;
         p->K = k;
-        if (k == 0 || k > pam::kMaxGemmK) return fail(PAM_ERR_UNSUPPORTED, "aperture element counts exceed the GEMM depth");
-        // Pattern-m apertures with m a multiple of 8 make every chunk of 8 K columns a run of
-        // consecutive elements, which the GEMM kernel expands with aligned 16-byte copies.
-        p->fast_expand = true;
-        for (int c = 0; c < k / 8 && p->fast_expand; ++c) {
-            const short k0 = p->ktab_h[(size_t)c * 8];
-            for (int t = 1; t < 8; ++t) {
-                const short kt = p->ktab_h[(size_t)c * 8 + t];
-                if (k0 < 0 ? kt >= 0 : kt != (short)(k0 + t)) p->fast_expand = false;
-            }
-        }
+        if (k == 0) return fail(PAM_ERR_INVALID_ARG, "every aperture is empty");
+        if (k > pam::kMaxGemmK)
+            return fail(PAM_ERR_UNSUPPORTED,
+                        "the apertures touch too many 8-element blocks for the tensor-core form "
+                        "(at most 24 block-aperture pairs)");
     }
     return PAM_OK;
 }

@@ -14,7 +14,7 @@ namespace pam {
 
 // Frames per CTA of the tensor-core form (N = 2 * frames GEMM columns).
 constexpr int kFramesPerGroup = 32;
-constexpr int kMaxGemmK = 320;     // 2 x padded element count of the tensor-core form
+constexpr int kMaxGemmK = 384;     // GEMM depth of the tensor-core form: 16 per (aperture, 8-element block)
 
 // Rows of the depth grid handled by one CTA of the fused propagate-and-correlate
 // kernel for a lateral length nx (8 warps; 2*nx/16 lanes per row).
@@ -96,9 +96,8 @@ struct pam_plan_s {
     int split_override = 0;            // pam_plan_set_split (0 = automatic)
     // tensor-core form (PAM_FORM_GEMM_*): 0 = plain FP32 path
     int form = 0;
-    int K = 0;                         // GEMM depth: 2 x padded element count
+    int K = 0;                         // GEMM depth: 16 per (aperture, 8-element block) pair
     int kq[4] = {0, 0, 0, 0};          // K range of aperture q: [kq[q], kq[q+1])
-    bool fast_expand = false;          // every K chunk of 8 is 8 consecutive elements (or empty)
     std::vector<short> ktab_h;         // host copies of Tables::ktab / kwgt
     std::vector<float> kwgt_h;
 };

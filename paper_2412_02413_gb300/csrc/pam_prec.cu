@@ -7,17 +7,18 @@
 //   c_j[d] = (1/nx) sum_u exp(i kz_u z_j) exp(+2 pi i u d / nx),
 // i.e. the inverse lateral DFT of the row's propagator phasors. The plan
 // tabulates c_j once per (bin, row) from the exact FP64 phase words, in
-// 16-bit form. A call then evaluates the sum over elements for 16 frames at a
+// 16-bit form. A call then evaluates the sum over elements for 32 frames at a
 // time as one tcgen05 GEMM per (bin, row) with M = 128 pixels,
-// N = 2 x 16 (Re, Im of each frame) and K = 2 x elements:
-//   A[i][k] = Re or Im c_j[(i - e_k) mod nx]   (expanded in shared memory)
+// N = 2 x 32 (Re, Im of each frame) and K = 16 per element block of 8:
+//   A[i][k] = Re or Im c_j[(i - e_k) mod nx]   (8 x 8 Toeplitz blocks in shared memory)
 //   B[k][n] = +-Re or Im of a S / sigma          (packed per call)
-// so that the real GEMM yields Re and Im of the complex sum. Disjoint
-// apertures are disjoint K ranges: one MMA chain per aperture accumulates
-// into its own tensor-memory region. The epilogue reads the accumulators
-// with tcgen05.ld and adds |p_q|^2 and Re conj(p_q) p_r into per-pixel
-// registers across all bins (Eq. 3-4). The NCC/TAX epilogue kernels then
-// finish exactly as in the FP32 path.
+// so that the real GEMM yields Re and Im of the complex sum. Each aperture is
+// its own K range (the element blocks it touches; elements outside it carry
+// weight 0): one MMA chain per aperture accumulates into its own
+// tensor-memory region. The fold reads the accumulators with tcgen05.ld and
+// adds |p_q|^2 and Re conj(p_q) p_r into per-pixel registers across all bins
+// (Eq. 3-4). The NCC/TAX epilogue kernels then finish exactly as in the FP32
+// path.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -31,18 +32,9 @@ namespace {
 constexpr int NXP = 128;                    // lateral length of this form
 constexpr int FG = kFramesPerGroup;         // frames per CTA
 constexpr int NG = 2 * FG;                  // GEMM N
-constexpr int CS_A = NXP / 8 * 128;         // bytes between K chunks of A (core matrices 8 x 16 B)
 constexpr int CS_B = NG / 8 * 128;          // bytes between K chunks of B
-constexpr int GEMM_THREADS = 256;             // 8 warps: 2 per tensor-memory lane quarter
-constexpr int TMEM_COLS = 256;              // >= 3 apertures x NG
-constexpr int DS_LEN = 136;                 // entries of one shifted copy of the reversed c vector
 
-// Offset (in 16-bit entries) of 8-entry block q of the copy of D shifted by sh,
-// for half `part` (0 = Re, 1 = Im). Blocks with the same q sit next to each
-// other for the 8 shifts, so the 8 lanes of a quarter warp, whose shifts are
-// distinct, read 8 different 16-byte bank groups.
-__device__ __forceinline__ int ds_off(int part, int sh, int q) { return ((part * (DS_LEN / 8) + q) * 8 + sh) * 8; }
-
+__host__ __device__ __forceinline__ int K_of(int4 kq) { return kq.w; }
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 // ---- 16-bit conversions ----
@@ -116,30 +108,12 @@ __device__ __forceinline__ unsigned umma_idesc()
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((unsigned)(NG >> 3) << 17) | ((unsigned)(NXP >> 4) << 24);
 }
 
-__device__ __forceinline__ void umma(unsigned tmem_d, uint64_t a, uint64_t b, unsigned idesc, unsigned accumulate)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
 __device__ __forceinline__ void umma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(unsigned taddr, float (&v)[8])
-{
-    unsigned r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = __uint_as_float(r[t]);
-}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 // ------------------------------------------------------- plan tables ----
@@ -243,463 +217,334 @@ prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, 
 }
 
 // ------------------------------------------------------------- GEMM ----
-// One CTA per (depth row j, group of 32 frames); 8 warps. Bins run in
-// sequence: bulk-copy the bin's B tile(s) and the row's c words, expand A
-// (the circulant) into shared memory, issue the MMA chains (thread 0), wait
-// for their commit, and fold the accumulators into per-pixel sums. Warp w
-// reads tensor-memory lane quarter w % 4 (pixels 32 (w%4) .. +31) for frames
-// 16 (w/4) .. +15, so each thread keeps 16 frames x n_acc sums in registers.
-template <int NAP, bool FP16, bool SPLIT>
-__global__ void __launch_bounds__(GEMM_THREADS, 1)
-prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ clo, const uint8_t *__restrict__ Bhi,
-                 const uint8_t *__restrict__ Blo, const short *__restrict__ ktab, int K, int4 kq, int n_bins, int nz,
-                 int F, const unsigned *__restrict__ smax, float *__restrict__ part, int *__restrict__ status,
-                 bool fast)
+// The A operand (the circulant) needs no expansion. Write pixel i = 8g + r
+// and element e = 8m + t with g, m < 16 blocks of 8. The entry
+// c[(i - e) mod 128] = c[(8 (g - m) + r - t) mod 128] depends on the two
+// blocks only through d = (g - m) mod 16, so the 128 x 128 matrix is built
+// from 16 distinct 8 x 8 Toeplitz blocks T_d[r][t] = c[(8 d + r - t) mod 128].
+// Each is exactly one 8-row x 16-byte core matrix of the canonical K-major
+// layout. Shared memory holds T_(n mod 16) for n = 0..31 (Re parts, then Im
+// parts, BLK_BYTES apart); the MMA of element block m starts at n = 16 - m, so
+// that row group g (SBO = 128 bytes) reads n = 16 - m + g, i.e. T_(g - m).
+// One K step of 16 is one element block: 8 columns pairing with Re c, then 8
+// pairing with Im c (LBO = BLK_BYTES).
+//
+// One CTA per (depth row j, group of 32 frames); warp-specialised, with no
+// CTA-wide barrier inside the bin loop:
+//   warps 0-7: build the Toeplitz blocks of bin b+1, then fold the
+//     accumulators of bin b into per-pixel sums. Warp w reads tensor-memory
+//     lane quarter w % 4 (pixels 32 (w%4) .. +31) for frames 16 (w/4) .. +15;
+//   warp 8: bulk copies of each bin's B tile and c words into a ring of NST
+//     stages;
+//   warps 9 .. 8+NAP: the MMA chain of aperture q = warp - 9 into one of two
+//     tensor-memory accumulator sets. One issuing warp per aperture: a single
+//     thread issuing every chain cannot keep up with N = 64 MMAs, which the
+//     tensor core finishes in about 48 cycles each.
+// mbarriers: full[s] (copy landed), aready[s] (blocks built; 8 warp arrivals),
+// sfree[s] (MMAs of the stage done; NAP commits), afull[t] (accumulator set t
+// written; NAP commits), tfree[t] (set t read out; 8 warp arrivals). Every wait
+// is bounded; on expiry the CTA raises a shared abort flag and the device
+// status word, each role drains the copies or MMAs it issued, and the CTA exits.
+constexpr int BLK_BYTES = 32 * 128;       // 32 core matrices of one part (Re or Im)
+constexpr int A_BYTES = 2 * BLK_BYTES;    // Re and Im
+constexpr int FW = FG / 2;                // frames per compute warp
+constexpr int MAX_NST = 4;
+constexpr size_t GEMM_SMEM_LIMIT = 232448;  // opt-in shared memory per CTA
+constexpr size_t GEMM_SMEM_EXTRA = 24 * 8 + 16;
+template <int NAP>
+constexpr int gemm_threads() { return 384; }   // 8 build/fold warps, 1 copy warp, NAP MMA warps (+ idle)
+constexpr int REG_LAUNCH = 168, REG_CTRL = 40, REG_FOLD = 224;
+static_assert(2 * 128 * REG_FOLD + 128 * REG_CTRL <= 384 * REG_LAUNCH, "register split exceeds the launch budget");
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
-    constexpr int NACC = NAP == 2 ? 3 : 6;
-    constexpr int FH = FG / 2;                                // frames per epilogue thread
-    extern __shared__ __align__(1024) uint8_t sm[];
-    const int KC = K / 8;                                     // K chunks of 8
-    uint8_t *sA = sm;                                         // KC * CS_A
-    uint8_t *sB = sA + (size_t)KC * CS_A;                     // KC * CS_B
-    uint8_t *sBl = sB + (size_t)KC * CS_B;                    // KC * CS_B (split)
-    uint32_t *sC = reinterpret_cast<uint32_t *>(sBl + (SPLIT ? (size_t)KC * CS_B : 0));  // [2][NXP]
-    short *sK = reinterpret_cast<short *>(sC + 2 * NXP);      // [K]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sK + ((K + 7) & ~7));  // [2]: data, mma
-    unsigned *tslot = reinterpret_cast<unsigned *>(bar + 2);
-    unsigned short *sDs = reinterpret_cast<unsigned short *>(bar + 4);   // [2 halves][8 shifts][DS_LEN]
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int j = blockIdx.x, grp = blockIdx.y;
-    const int quarter = warp & 3, fhalf = warp >> 2;
-    const int i_epi = 32 * quarter + lane;                   // pixel of this thread's accumulator lane
-    const int i_exp = tid & (NXP - 1), hpar = tid >> 7;      // expansion: pixel row, parity of its K chunks
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
-    }
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    for (int k = tid; k < K; k += GEMM_THREADS) sK[k] = ktab[k];
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const unsigned tmem = *tslot;
-    const unsigned idesc = umma_idesc<FP16>();
-    const int kqa[4] = {kq.x, kq.y, kq.z, kq.w};
-    const unsigned bytesB = (unsigned)K * NG * 2;
-    const size_t tileB = bytesB;
-
-    float acc[FH][NACC];
-#pragma unroll
-    for (int f = 0; f < FH; ++f)
-#pragma unroll
-        for (int a = 0; a < NACC; ++a) acc[f][a] = 0.f;
-
-    unsigned ph_data = 0, ph_mma = 0;
-    bool ok = true, data_pending = false, mma_pending = false;
-    for (int b = 0; b < n_bins; ++b) {
-        if (tid == 0) {
-            mbar_expect_tx(&bar[0], (SPLIT ? 2u : 1u) * (bytesB + NXP * 4u));
-            bulk_g2s(sB, Bhi + ((size_t)grp * n_bins + b) * tileB, bytesB, &bar[0]);
-            bulk_g2s(sC, chi + ((size_t)b * nz + j) * NXP, NXP * 4, &bar[0]);
-            if (SPLIT) {
-                bulk_g2s(sBl, Blo + ((size_t)grp * n_bins + b) * tileB, bytesB, &bar[0]);
-                bulk_g2s(sC + NXP, clo + ((size_t)b * nz + j) * NXP, NXP * 4, &bar[0]);
-            }
-        }
-        ok = __syncthreads_and(mbar_wait(&bar[0], ph_data)) != 0;
-        ph_data ^= 1u;
-        if (!ok) {
-            data_pending = true;
-            break;
-        }
-#pragma unroll 1
-        for (int pass = 0; pass < (SPLIT ? 2 : 1); ++pass) {
-            // A[i][k] = (Re or Im) c[(i - e_k) mod 128]: row i of the circulant, one 16-byte
-            // core-matrix row per K chunk.
-            const uint32_t *cw = sC + pass * NXP;
-            if (fast) {
-                // Every K chunk is 8 consecutive elements e0..e0+7 of one half, so its row-i
-                // segment is D[(e0 - i) mod 128 .. +8) with D[m] = c[(-m) mod 128]: one aligned
-                // 16-byte load from the copy of D shifted by (e0 - i) mod 8. The copies are built
-                // 8 entries at a time: D_s[8q + t] = c[-(8q + s + t)].
-                for (int pq = tid; pq < 8 * (DS_LEN / 8); pq += GEMM_THREADS) {
-                    const int sh = pq / (DS_LEN / 8), q = pq % (DS_LEN / 8);
-                    unsigned w[8];
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) w[t] = cw[(-(8 * q + sh + t)) & (NXP - 1)];
-                    const uint4 re = make_uint4(__byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
-                                                __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
-                    const uint4 im = make_uint4(__byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
-                                                __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
-                    *reinterpret_cast<uint4 *>(sDs + ds_off(0, sh, q)) = re;
-                    *reinterpret_cast<uint4 *>(sDs + ds_off(1, sh, q)) = im;
-                }
-                __syncthreads();
-                for (int ch = hpar; ch < KC; ch += 2) {
-                    const short kt = sK[ch * 8];
-                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                    if (kt >= 0) {
-                        const int e0 = kt & 0x3FFF, part_im = (kt >> 14) & 1;
-                        const int m0 = (e0 - i_exp) & (NXP - 1);
-                        v = *reinterpret_cast<const uint4 *>(sDs + ds_off(part_im, m0 & 7, m0 >> 3));
-                    }
-                    *reinterpret_cast<uint4 *>(sA + (size_t)ch * CS_A + (i_exp / 8) * 128 + (i_exp % 8) * 16) = v;
-                }
-            } else {
-                for (int ch = hpar; ch < KC; ch += 2) {
-                    unsigned w4[4];
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        unsigned h2 = 0;
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const short kt = sK[ch * 8 + 2 * t + h];
-                            unsigned v = 0;
-                            if (kt >= 0) {
-                                const int e = kt & 0x3FFF, imag = (kt >> 14) & 1;
-                                v = (cw[(i_exp - e) & (NXP - 1)] >> (16 * imag)) & 0xFFFFu;
-                            }
-                            h2 |= v << (16 * h);
-                        }
-                        w4[t] = h2;
-                    }
-                    *reinterpret_cast<uint4 *>(sA + (size_t)ch * CS_A + (i_exp / 8) * 128 + (i_exp % 8) * 16) =
-                        make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            tc_fence_before();
-            __syncthreads();
-            tc_fence_after();
-            if (tid == 0) {
-#pragma unroll
-                for (int q = 0; q < NAP; ++q) {
-                    const unsigned dq = tmem + (unsigned)(q * NG);
-                    for (int s = kqa[q] / 16; s < kqa[q + 1] / 16; ++s) {
-                        const uint64_t da = umma_desc(smem_u32(sA) + s * 2 * CS_A, CS_A, 128);
-                        const uint64_t dbh = umma_desc(smem_u32(sB) + s * 2 * CS_B, CS_B, 128);
-                        const bool first = pass == 0 && s == kqa[q] / 16;
-                        if (pass == 0) {
-                            umma(dq, da, dbh, idesc, first ? 0u : 1u);
-                            if (SPLIT) umma(dq, da, umma_desc(smem_u32(sBl) + s * 2 * CS_B, CS_B, 128), idesc, 1u);
-                        } else {
-                            umma(dq, da, dbh, idesc, 1u);
-                        }
-                    }
-                }
-                umma_commit(&bar[1]);
-            }
-            ok = __syncthreads_and(mbar_wait(&bar[1], ph_mma)) != 0;
-            ph_mma ^= 1u;
-            tc_fence_after();
-            if (!ok) {
-                mma_pending = true;
-                break;
-            }
-        }
-        if (!ok) break;
-        // fold this bin's fields into the per-pixel sums (4 frames per tensor-memory read)
-        const unsigned lane_base = tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(fhalf * 2 * FH);
-#pragma unroll
-        for (int fc = 0; fc < FH / 4; ++fc) {
-            float r[NAP][8];
-#pragma unroll
-            for (int q = 0; q < NAP; ++q) tmem_ld8(lane_base + (unsigned)(q * NG + fc * 8), r[q]);
-            tmem_wait_ld();
-#pragma unroll
-            for (int ff = 0; ff < 4; ++ff) {
-                const int f = fc * 4 + ff;
-                const float ar = r[0][2 * ff], ai = r[0][2 * ff + 1];
-                const float br = r[1][2 * ff], bi = r[1][2 * ff + 1];
-                acc[f][0] = fmaf(ar, ar, fmaf(ai, ai, acc[f][0]));
-                acc[f][1] = fmaf(br, br, fmaf(bi, bi, acc[f][1]));
-                if constexpr (NAP == 2) {
-                    acc[f][2] = fmaf(ar, br, fmaf(ai, bi, acc[f][2]));
-                } else {
-                    const float cr = r[2][2 * ff], ci = r[2][2 * ff + 1];
-                    acc[f][2] = fmaf(cr, cr, fmaf(ci, ci, acc[f][2]));
-                    acc[f][3] = fmaf(ar, br, fmaf(ai, bi, acc[f][3]));
-                    acc[f][4] = fmaf(br, cr, fmaf(bi, ci, acc[f][4]));
-                    acc[f][5] = fmaf(cr, ar, fmaf(ci, ai, acc[f][5]));
-                }
-            }
-        }
-        tc_fence_before();
-        __syncthreads();
-    }
-    if (!ok && tid == 0) {
-        atomicOr(status, 1);
-        // let the copies / MMAs still in flight finish before shared and tensor memory go away
-        if (data_pending) mbar_wait(&bar[0], ph_data ^ 1u);
-        if (mma_pending) mbar_wait(&bar[1], ph_mma ^ 1u);
-    }
-    // Partial sums of the whole bin range, rescaled by sigma^2, as split 0 of the FP32 path's layout.
-    const size_t npix = (size_t)nz * NXP;
-#pragma unroll
-    for (int f = 0; f < FH; ++f) {
-        const int fr = grp * FG + fhalf * FH + f;
-        if (fr < F && ok) {
-            const float s2 = ldexpf(1.0f, 2 * frame_exp(smax[fr]));
-#pragma unroll
-            for (int a = 0; a < NACC; ++a)
-                part[((size_t)fr * NACC + a) * npix + (size_t)j * NXP + i_epi] = acc[f][a] * s2;
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Software-pipelined GEMM (16-bit operands, no split; K <= 256). Two sets of
-// shared-memory buffers (A, B, c, shifted copies) and two tensor-memory
-// accumulator sets let the CUDA cores expand A for bin b+1 and fold the sums
-// of bin b while the tensor core runs the MMAs of the neighbouring bin:
-//   wait data(b+1), expand(b+1) | MMA(b) running
-//   wait MMA(b), load(b+2), issue MMA(b+1)
-//   fold sums of bin b           | MMA(b+1) running
-constexpr int TMEM_COLS_PIPE = 512;   // 2 x 3 apertures x NG
+// MMA issued by one elected lane of a converged warp (operands stay warp-uniform).
+__device__ __forceinline__ void umma_elect(unsigned tmem_d, uint64_t a, uint64_t b, unsigned idesc, unsigned accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 
-template <int NAP, bool FP16>
-__global__ void __launch_bounds__(GEMM_THREADS, 1)
-prec_gemm_pipe_kernel(const uint32_t *__restrict__ chi, const uint8_t *__restrict__ Bhi, const short *__restrict__ ktab,
-                      int K, int4 kq, int n_bins, int nz, int F, const unsigned *__restrict__ smax,
-                      float *__restrict__ part, int *__restrict__ status, bool fast)
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v)
+{
+    unsigned r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                 "[%16];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr));
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[t]);
+}
+
+// Shared memory of one pipeline stage: NPART x (A blocks, B tile, c words).
+__host__ __device__ constexpr size_t gemm_stage_bytes(int K, int npart)
+{
+    return (size_t)npart * (A_BYTES + (size_t)K * NG * 2 + NXP * 4);
+}
+int gemm_stages(int K, bool split)
+{
+    const size_t st = gemm_stage_bytes(K, split ? 2 : 1);
+    const size_t n = (GEMM_SMEM_LIMIT - GEMM_SMEM_EXTRA) / st;
+    return (int)(n < MAX_NST ? n : MAX_NST);
+}
+size_t gemm_smem(int K, bool split)
+{
+    return gemm_stages(K, split) * gemm_stage_bytes(K, split ? 2 : 1) + GEMM_SMEM_EXTRA;
+}
+
+// steps: element block of K step st in bits 4 (st % 16) of steps[st / 16].
+template <int NAP, bool FP16, bool SPLIT>
+__global__ void __launch_bounds__(gemm_threads<NAP>(), 1)
+prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ clo, const uint8_t *__restrict__ Bhi,
+                 const uint8_t *__restrict__ Blo, ulonglong2 steps, int4 kq, int n_bins, int nz, int F, int NST,
+                 const unsigned *__restrict__ smax, float *__restrict__ part, int *__restrict__ status)
 {
     constexpr int NACC = NAP == 2 ? 3 : 6;
-    constexpr int FH = FG / 2;
+    constexpr int NPART = SPLIT ? 2 : 1;
     constexpr int ACC_COLS = NAP * NG;
+    constexpr unsigned TMEM_ALLOC = 2 * ACC_COLS <= 256 ? 256u : 512u;
+    static_assert(2 * ACC_COLS <= 512, "two accumulator sets must fit in tensor memory");
     extern __shared__ __align__(1024) uint8_t sm[];
-    const int KC = K / 8;
-    const size_t szA = (size_t)KC * CS_A, szB = (size_t)KC * CS_B;
-    uint8_t *sA[2] = {sm, sm + szA};
-    uint8_t *sB[2] = {sm + 2 * szA, sm + 2 * szA + szB};
-    uint32_t *sC0 = reinterpret_cast<uint32_t *>(sm + 2 * szA + 2 * szB);              // [2][NXP]
-    unsigned short *sD0 = reinterpret_cast<unsigned short *>(sC0 + 2 * NXP);           // [2][2][8][DS_LEN]
-    short *sK = reinterpret_cast<short *>(sD0 + 2 * 2 * 8 * DS_LEN);                   // [K]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sK + ((K + 7) & ~7));                 // data[2], mma[2]
-    unsigned *tslot = reinterpret_cast<unsigned *>(bar + 4);
+    const size_t bytesB = (size_t)K_of(kq) * NG * 2;
+    const size_t stage = gemm_stage_bytes(K_of(kq), NPART);
+    auto sA = [&](int s) { return sm + s * stage; };
+    auto sB = [&](int s) { return sm + s * stage + NPART * A_BYTES; };
+    auto sC = [&](int s) { return reinterpret_cast<uint32_t *>(sm + s * stage + NPART * (A_BYTES + bytesB)); };
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + NST * stage);    // [MAX_NST]
+    uint64_t *aready = full + MAX_NST, *sfree = aready + MAX_NST;      // [MAX_NST]
+    uint64_t *afull = sfree + MAX_NST, *tfree = afull + 2;             // [2]
+    uint64_t *dbar = tfree + 2;                                         // [4] per-warp drain
+    unsigned *tslot = reinterpret_cast<unsigned *>(dbar + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int j = blockIdx.x, grp = blockIdx.y;
-    const int quarter = warp & 3, fhalf = warp >> 2;
-    const int i_epi = 32 * quarter + lane;
-    const int i_exp = tid & (NXP - 1), hpar = tid >> 7;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                     "r"(TMEM_COLS_PIPE)
+                     "r"(TMEM_ALLOC)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        for (int x = 0; x < 4; ++x) mbar_init(&bar[x], 1);
+        for (int s = 0; s < MAX_NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&aready[s], 8);
+            mbar_init(&sfree[s], NAP);
+        }
+        for (int t = 0; t < 2; ++t) {
+            mbar_init(&afull[t], NAP);
+            mbar_init(&tfree[t], 8);
+        }
+        for (int q = 0; q < 4; ++q) mbar_init(&dbar[q], 1);
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    for (int k = tid; k < K; k += GEMM_THREADS) sK[k] = ktab[k];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = *tslot;
-    const unsigned idesc = umma_idesc<FP16>();
-    const int kqa[4] = {kq.x, kq.y, kq.z, kq.w};
-    const unsigned bytesB = (unsigned)K * NG * 2;
+    // Register split between the warpgroups (launch: 384 x 168 = 64512): the
+    // copy / MMA warpgroup drops to REG_CTRL, the two build/fold warpgroups rise
+    // to REG_FOLD (2 x 128 x REG_FOLD + 128 x REG_CTRL <= 64512). The host checks
+    // that the kernel was built with 168 registers per thread before launching.
+    if (warp >= 8)
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(REG_CTRL));
+    else
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(REG_FOLD));
 
-    float acc[FH][NACC];
-#pragma unroll
-    for (int f = 0; f < FH; ++f)
-#pragma unroll
-        for (int a = 0; a < NACC; ++a) acc[f][a] = 0.f;
-
-    int loads_issued = 0, loads_done = 0, mmas_issued = 0, mmas_done = 0;  // thread 0's bookkeeping
-    auto issue_load = [&](int b) {
-        if (tid == 0) {
-            const int bb = b & 1;
-            mbar_expect_tx(&bar[bb], bytesB + NXP * 4u);
-            bulk_g2s(sB[bb], Bhi + ((size_t)grp * n_bins + b) * bytesB, bytesB, &bar[bb]);
-            bulk_g2s(sC0 + bb * NXP, chi + ((size_t)b * nz + j) * NXP, NXP * 4, &bar[bb]);
-            ++loads_issued;
+    // Bounded wait that also gives up when another thread has aborted.
+    auto wait = [&](uint64_t *bar, unsigned parity) -> bool {
+        if (mbar_try_wait(bar, parity)) return true;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(bar, parity)) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > (1ll << 31)) {
+                *abort_flag = 1;
+                atomicOr(status, 1);
+                return false;
+            }
         }
+        return true;
     };
-    // Waits are per thread; the go / abort decision is made uniform at the one
-    // CTA barrier of each bin (__syncthreads_and before the MMA issue).
-    auto wait_data = [&](int b) -> bool {
-        const bool r = mbar_wait(&bar[b & 1], (b >> 1) & 1);
-        if (r && tid == 0) ++loads_done;
-        return r;
-    };
-    auto expand = [&](int b) {
-        const int bb = b & 1;
-        const uint32_t *cw = sC0 + bb * NXP;
-        unsigned short *sDs = sD0 + bb * 2 * 8 * DS_LEN;
-        uint8_t *A = sA[bb];
-        if (fast) {
-            for (int pq = tid; pq < 8 * (DS_LEN / 8); pq += GEMM_THREADS) {
-                const int sh = pq / (DS_LEN / 8), q = pq % (DS_LEN / 8);
+
+    if (warp >= 9 + NAP) {
+        // spare warp of the control warpgroup (AS-DAX): nothing to do
+    } else if (warp >= 8) {
+        // -------- warp 8: bulk-copy ring; warps 9..: MMA chain of aperture q --------
+        const int q = warp - 9;
+        const bool producer = q < 0;
+        const unsigned idesc = umma_idesc<FP16>();
+        const int s0 = (q <= 0 ? kq.x : q == 1 ? kq.y : kq.z) / 16;
+        const int s1 = (q <= 0 ? kq.y : q == 1 ? kq.z : kq.w) / 16;
+        int issued = 0;
+        auto load = [&](int b) {
+            if (lane == 0) {
+                const int s = b % NST;
+                const size_t ob = ((size_t)grp * n_bins + b) * bytesB, oc = ((size_t)b * nz + j) * NXP;
+                mbar_expect_tx(&full[s], (unsigned)(NPART * (bytesB + NXP * 4)));
+                bulk_g2s(sB(s), Bhi + ob, (unsigned)bytesB, &full[s]);
+                bulk_g2s(sC(s), chi + oc, NXP * 4, &full[s]);
+                if (SPLIT) {
+                    bulk_g2s(sB(s) + bytesB, Blo + ob, (unsigned)bytesB, &full[s]);
+                    bulk_g2s(sC(s) + NXP, clo + oc, NXP * 4, &full[s]);
+                }
+            }
+            issued = b + 1;
+        };
+        if (producer)
+            for (int b = 0; b < n_bins && b < NST; ++b) load(b);
+        bool ok = true, any = false;
+        if (producer) {
+            for (int b = NST; b < n_bins && ok; ++b) {
+                // stage of bin b - NST is free once every aperture's MMAs of that bin are done
+                ok = __all_sync(0xffffffffu, wait(&sfree[b % NST], (unsigned)(b / NST - 1) & 1u));
+                if (ok) load(b);
+            }
+        } else {
+            for (int b = 0; b < n_bins && ok; ++b) {
+                const int s = b % NST, t = b & 1;
+                const unsigned ps = (unsigned)(b / NST) & 1u;
+                ok = wait(&full[s], ps) && wait(&aready[s], ps);
+                if (ok && b >= 2) ok = wait(&tfree[t], (unsigned)((b - 2) >> 1) & 1u);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t da0 = umma_desc(smem_u32(sA(s)), BLK_BYTES, 128);
+                const uint64_t db0 = umma_desc(smem_u32(sB(s)), CS_B, 128);
+                const unsigned dq = tmem + (unsigned)(t * ACC_COLS + q * NG);
+                for (int st = s0; st < s1; ++st) {
+                    const unsigned m = (unsigned)((st < 16 ? steps.x >> (4 * st) : steps.y >> (4 * (st - 16))) & 15u);
+                    const uint64_t da = da0 + (uint64_t)((16u - m) * 8u);   // start address field: +128 B per block
+                    const uint64_t db = db0 + (uint64_t)(st * (2 * CS_B / 16));
+                    umma_elect(dq, da, db, idesc, st == s0 ? 0u : 1u);
+                    if (SPLIT) {
+                        umma_elect(dq, da, db + (uint64_t)(bytesB / 16), idesc, 1u);             // hi x lo
+                        umma_elect(dq, da + (uint64_t)(A_BYTES / 16), db, idesc, 1u);           // lo x hi
+                    }
+                }
+                any = true;
+                __syncwarp();
+                if (lane == 0) {
+                    umma_commit(&sfree[s]);
+                    umma_commit(&afull[t]);
+                }
+            }
+        }
+        if (!ok && lane == 0) {
+            if (any) {
+                umma_commit(&dbar[q]);       // tracks every MMA this thread issued
+                mbar_wait(&dbar[q], 0);
+            }
+            // at most one copy per stage can still be in flight: the last one issued there
+            for (int b = issued - NST < 0 ? 0 : issued - NST; b < issued; ++b)
+                mbar_wait(&full[b % NST], (unsigned)(b / NST) & 1u);
+        }
+    } else {
+        // ---------------- build + fold (warps 0-7) ----------------
+        const int quarter = warp & 3, fh = warp >> 2;
+        const int i_epi = 32 * quarter + lane;
+        float acc[FW][NACC];
+#pragma unroll
+        for (int f = 0; f < FW; ++f)
+#pragma unroll
+            for (int a = 0; a < NACC; ++a) acc[f][a] = 0.f;
+
+        // Thread (part, n, r) writes row r of block n: the 8 entries
+        // c[(8 (n mod 16) + r - t) mod 128], t = 0..7, as one 16-byte row of
+        // Re parts and one of Im parts.
+        auto build = [&](int b) -> bool {
+            const int s = b % NST;
+            if (!wait(&full[s], (unsigned)(b / NST) & 1u)) return false;
+#pragma unroll
+            for (int pidx = 0; pidx < NPART; ++pidx) {
+                const int n = tid >> 3, r = tid & 7;
+                const uint32_t *cw = sC(s) + pidx * NXP;
+                const int m0 = 8 * (n & 15) + r;
                 unsigned w[8];
 #pragma unroll
-                for (int t = 0; t < 8; ++t) w[t] = cw[(-(8 * q + sh + t)) & (NXP - 1)];
-                *reinterpret_cast<uint4 *>(sDs + ds_off(0, sh, q)) =
+                for (int t = 0; t < 8; ++t) w[t] = cw[(m0 - t) & (NXP - 1)];
+                uint8_t *A = sA(s) + pidx * A_BYTES + n * 128 + r * 16;
+                *reinterpret_cast<uint4 *>(A) =
                     make_uint4(__byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
                                __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
-                *reinterpret_cast<uint4 *>(sDs + ds_off(1, sh, q)) =
+                *reinterpret_cast<uint4 *>(A + BLK_BYTES) =
                     make_uint4(__byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
                                __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
             }
-            __syncthreads();
-            for (int ch = hpar; ch < KC; ch += 2) {
-                const short kt = sK[ch * 8];
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (kt >= 0) {
-                    const int e0 = kt & 0x3FFF, part_im = (kt >> 14) & 1;
-                    const int m0 = (e0 - i_exp) & (NXP - 1);
-                    v = *reinterpret_cast<const uint4 *>(sDs + ds_off(part_im, m0 & 7, m0 >> 3));
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&aready[s]);
+            return true;
+        };
+        auto fold = [&](int b) -> bool {
+            const int t = b & 1;
+            if (!wait(&afull[t], (unsigned)(b >> 1) & 1u)) return false;
+            tc_fence_after();
+            const unsigned base =
+                tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(t * ACC_COLS + fh * 2 * FW);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float r[NAP][16];
+#pragma unroll
+                for (int q = 0; q < NAP; ++q) tmem_ld16(base + (unsigned)(q * NG + 16 * h), r[q]);
+                tmem_wait_ld();
+                if (h == 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tfree[t]);
                 }
-                *reinterpret_cast<uint4 *>(A + (size_t)ch * CS_A + (i_exp / 8) * 128 + (i_exp % 8) * 16) = v;
-            }
-        } else {
-            for (int ch = hpar; ch < KC; ch += 2) {
-                unsigned w4[4];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    unsigned h2 = 0;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const short kt = sK[ch * 8 + 2 * t + h];
-                        unsigned v = 0;
-                        if (kt >= 0) {
-                            const int e = kt & 0x3FFF, imag = (kt >> 14) & 1;
-                            v = (cw[(i_exp - e) & (NXP - 1)] >> (16 * imag)) & 0xFFFFu;
-                        }
-                        h2 |= v << (16 * h);
+                for (int ff = 0; ff < 8; ++ff) {
+                    const int f = 8 * h + ff;
+                    const float ar = r[0][2 * ff], ai = r[0][2 * ff + 1];
+                    const float br = r[1][2 * ff], bi = r[1][2 * ff + 1];
+                    acc[f][0] = fmaf(ar, ar, fmaf(ai, ai, acc[f][0]));
+                    acc[f][1] = fmaf(br, br, fmaf(bi, bi, acc[f][1]));
+                    if constexpr (NAP == 2) {
+                        acc[f][2] = fmaf(ar, br, fmaf(ai, bi, acc[f][2]));
+                    } else {
+                        const float cr = r[2][2 * ff], ci = r[2][2 * ff + 1];
+                        acc[f][2] = fmaf(cr, cr, fmaf(ci, ci, acc[f][2]));
+                        acc[f][3] = fmaf(ar, br, fmaf(ai, bi, acc[f][3]));
+                        acc[f][4] = fmaf(br, cr, fmaf(bi, ci, acc[f][4]));
+                        acc[f][5] = fmaf(cr, ar, fmaf(ci, ai, acc[f][5]));
                     }
-                    w4[t] = h2;
-                }
-                *reinterpret_cast<uint4 *>(A + (size_t)ch * CS_A + (i_exp / 8) * 128 + (i_exp % 8) * 16) =
-                    make_uint4(w4[0], w4[1], w4[2], w4[3]);
-            }
-        }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        tc_fence_before();
-    };
-    auto issue_mma = [&](int b) {
-        if (tid == 0) {
-            const int bb = b & 1;
-#pragma unroll
-            for (int q = 0; q < NAP; ++q) {
-                const unsigned dq = tmem + (unsigned)(bb * ACC_COLS + q * NG);
-                for (int s = kqa[q] / 16; s < kqa[q + 1] / 16; ++s) {
-                    const uint64_t da = umma_desc(smem_u32(sA[bb]) + s * 2 * CS_A, CS_A, 128);
-                    const uint64_t db = umma_desc(smem_u32(sB[bb]) + s * 2 * CS_B, CS_B, 128);
-                    umma(dq, da, db, idesc, s == kqa[q] / 16 ? 0u : 1u);
                 }
             }
-            umma_commit(&bar[2 + bb]);
-            ++mmas_issued;
-        }
-    };
-    auto wait_mma = [&](int b) -> bool {
-        const bool r = mbar_wait(&bar[2 + (b & 1)], (b >> 1) & 1);
-        if (r && tid == 0) ++mmas_done;
-        return r;
-    };
-    auto fold = [&](int b) {
-        const unsigned lane_base = tmem + ((unsigned)(32 * quarter) << 16) +
-                                   (unsigned)((b & 1) * ACC_COLS + fhalf * 2 * FH);
-#pragma unroll
-        for (int fc = 0; fc < FH / 4; ++fc) {
-            float r[NAP][8];
-#pragma unroll
-            for (int q = 0; q < NAP; ++q) tmem_ld8(lane_base + (unsigned)(q * NG + fc * 8), r[q]);
-            tmem_wait_ld();
-#pragma unroll
-            for (int ff = 0; ff < 4; ++ff) {
-                const int f = fc * 4 + ff;
-                const float ar = r[0][2 * ff], ai = r[0][2 * ff + 1];
-                const float br = r[1][2 * ff], bi = r[1][2 * ff + 1];
-                acc[f][0] = fmaf(ar, ar, fmaf(ai, ai, acc[f][0]));
-                acc[f][1] = fmaf(br, br, fmaf(bi, bi, acc[f][1]));
-                if constexpr (NAP == 2) {
-                    acc[f][2] = fmaf(ar, br, fmaf(ai, bi, acc[f][2]));
-                } else {
-                    const float cr = r[2][2 * ff], ci = r[2][2 * ff + 1];
-                    acc[f][2] = fmaf(cr, cr, fmaf(ci, ci, acc[f][2]));
-                    acc[f][3] = fmaf(ar, br, fmaf(ai, bi, acc[f][3]));
-                    acc[f][4] = fmaf(br, cr, fmaf(bi, ci, acc[f][4]));
-                    acc[f][5] = fmaf(cr, ar, fmaf(ci, ai, acc[f][5]));
-                }
-            }
-        }
-        tc_fence_before();  // ordered before the next MMA into this set by the next bin's barrier
-    };
+            return true;
+        };
 
-    bool ok = true;
-    if (n_bins > 0) {
-        issue_load(0);
-        if (n_bins > 1) issue_load(1);
-        bool r = wait_data(0);
-        expand(0);
-        ok = __syncthreads_and(r) != 0;
-        tc_fence_after();
-        if (ok) issue_mma(0);
-    }
-    for (int b = 0; b < n_bins && ok; ++b) {
-        bool r = true;
-        if (b + 1 < n_bins) {
-            r = wait_data(b + 1);
-            expand(b + 1);                     // tensor core: MMA(b)
+        bool ok = n_bins == 0 || build(0);
+        for (int b = 0; b < n_bins && ok; ++b) {
+            if (b + 1 < n_bins && !build(b + 1)) ok = false;   // tensor core: MMA(b)
+            if (ok && !fold(b)) ok = false;                     // tensor core: MMA(b+1)
         }
-        r = wait_mma(b) && r;
-        ok = __syncthreads_and(r) != 0;        // A(b+1) complete, acc(b) ready, buffers of bin b free
-        tc_fence_after();
-        if (!ok) break;
-        if (b + 2 < n_bins) issue_load(b + 2);
-        if (b + 1 < n_bins) issue_mma(b + 1);
-        fold(b);                               // tensor core: MMA(b+1)
-    }
-    if (!ok && tid == 0) {
-        atomicOr(status, 1);
-        // let the copies / MMAs still in flight finish before shared and tensor memory go away
-        for (int b = loads_done; b < loads_issued; ++b) mbar_wait(&bar[b & 1], (b >> 1) & 1);
-        for (int b = mmas_done; b < mmas_issued; ++b) mbar_wait(&bar[2 + (b & 1)], (b >> 1) & 1);
-    }
-    const size_t npix = (size_t)nz * NXP;
+        const size_t npix = (size_t)nz * NXP;
 #pragma unroll
-    for (int f = 0; f < FH; ++f) {
-        const int fr = grp * FG + fhalf * FH + f;
-        if (fr < F && ok) {
-            const float s2 = ldexpf(1.0f, 2 * frame_exp(smax[fr]));
+        for (int f = 0; f < FW; ++f) {
+            const int fr = grp * FG + fh * FW + f;
+            if (fr < F && ok) {
+                const float s2 = ldexpf(1.0f, 2 * frame_exp(smax[fr]));
 #pragma unroll
-            for (int a = 0; a < NACC; ++a)
-                part[((size_t)fr * NACC + a) * npix + (size_t)j * NXP + i_epi] = acc[f][a] * s2;
+                for (int a = 0; a < NACC; ++a)
+                    part[((size_t)fr * NACC + a) * npix + (size_t)j * NXP + i_epi] = acc[f][a] * s2;
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS_PIPE)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_ALLOC)
                      : "memory");
-}
-
-size_t gemm_pipe_smem(int K)
-{
-    const size_t kc = (size_t)K / 8;
-    return 2 * kc * CS_A + 2 * kc * CS_B + 2 * NXP * 4 + 2 * 2 * 8 * DS_LEN * 2 + ((K + 7) & ~7) * 2 + 4 * 8 + 16;
-}
-constexpr int kMaxPipeK = 256;
-
-size_t gemm_smem(int K, bool split)
-{
-    const size_t kc = (size_t)K / 8;
-    return kc * CS_A + kc * CS_B * (split ? 2 : 1) + 2 * NXP * 4 + ((K + 7) & ~7) * 2 + 32 + 2 * 8 * DS_LEN * 2;
 }
 
 template <int NAP, bool FP16, bool SPLIT>
@@ -708,15 +553,16 @@ cudaError_t launch_gemm_t(const pam_plan_s &p, int n_frames, cudaStream_t st)
     const int groups = (n_frames + FG - 1) / FG;
     dim3 grid(p.nz, groups);
     const int4 kq = make_int4(p.kq[0], p.kq[1], p.kq[2], p.kq[3]);
-    if (!SPLIT && p.K <= kMaxPipeK) {
-        prec_gemm_pipe_kernel<NAP, FP16><<<grid, GEMM_THREADS, gemm_pipe_smem(p.K), st>>>(
-            p.t.c_hi, reinterpret_cast<const uint8_t *>(p.w.Bhi), p.t.ktab, p.K, kq, p.n_bins, p.nz, n_frames,
-            p.w.smax, p.w.part, p.w.status, p.fast_expand);
-        return cudaGetLastError();
+    if (gemm_stages(p.K, SPLIT) < 2 || p.K / 16 > 32) return cudaErrorInvalidConfiguration;
+    ulonglong2 steps = make_ulonglong2(0ull, 0ull);
+    for (int s = 0; s < p.K / 16; ++s) {
+        const unsigned long long m = (unsigned long long)((p.ktab_h[(size_t)16 * s] & 0x3FFF) >> 3) & 15ull;
+        if (s < 16) steps.x |= m << (4 * s);
+        else steps.y |= m << (4 * (s - 16));
     }
-    prec_gemm_kernel<NAP, FP16, SPLIT><<<grid, GEMM_THREADS, gemm_smem(p.K, SPLIT), st>>>(
+    prec_gemm_kernel<NAP, FP16, SPLIT><<<grid, gemm_threads<NAP>(), gemm_smem(p.K, SPLIT), st>>>(
         p.t.c_hi, p.t.c_lo, reinterpret_cast<const uint8_t *>(p.w.Bhi), reinterpret_cast<const uint8_t *>(p.w.Blo),
-        p.t.ktab, p.K, kq, p.n_bins, p.nz, n_frames, p.w.smax, p.w.part, p.w.status, p.fast_expand);
+        steps, kq, p.n_bins, p.nz, n_frames, gemm_stages(p.K, SPLIT), p.w.smax, p.w.part, p.w.status);
     return cudaGetLastError();
 }
 
@@ -738,8 +584,15 @@ cudaError_t launch_form(const pam_plan_s &p, int n_frames, cudaStream_t st)
 template <int NAP, bool FP16, bool SPLIT>
 cudaError_t set_gemm_smem()
 {
-    return cudaFuncSetAttribute(prec_gemm_kernel<NAP, FP16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)gemm_smem(kMaxGemmK, SPLIT));
+    static_assert(MAX_NST >= 2, "the copy ring needs two stages");
+    cudaError_t e = cudaFuncSetAttribute(prec_gemm_kernel<NAP, FP16, SPLIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM_LIMIT);
+    if (e != cudaSuccess) return e;
+    // The register split (setmaxnreg) is sized for a launch of exactly REG_LAUNCH
+    // registers per thread; with fewer, the increase could never be granted.
+    cudaFuncAttributes a;
+    if ((e = cudaFuncGetAttributes(&a, prec_gemm_kernel<NAP, FP16, SPLIT>)) != cudaSuccess) return e;
+    return a.numRegs == REG_LAUNCH ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
 }  // namespace
@@ -769,15 +622,6 @@ int prec_kernels() { return 3; }
 cudaError_t prepare_prec_kernels()
 {
     cudaError_t e;
-    const int pipe = (int)gemm_pipe_smem(kMaxPipeK);
-    if ((e = cudaFuncSetAttribute(prec_gemm_pipe_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe)))
-        return e;
-    if ((e = cudaFuncSetAttribute(prec_gemm_pipe_kernel<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe)))
-        return e;
-    if ((e = cudaFuncSetAttribute(prec_gemm_pipe_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe)))
-        return e;
-    if ((e = cudaFuncSetAttribute(prec_gemm_pipe_kernel<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pipe)))
-        return e;
     if ((e = set_gemm_smem<2, false, false>()) != cudaSuccess) return e;
     if ((e = set_gemm_smem<3, false, false>()) != cudaSuccess) return e;
     if ((e = set_gemm_smem<2, true, false>()) != cudaSuccess) return e;
