@@ -71,6 +71,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
         : "memory");
     return ok != 0;
 }
+// try_wait that lets the hardware suspend the thread (up to about 10 us) until
+// the phase completes: waiting warps then neither issue nor poll shared memory,
+// which the tensor core reads at full bandwidth.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(10000u)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait (about one second of SM cycles); false on expiry.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
 {
@@ -231,18 +244,22 @@ prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, 
 //
 // One CTA per (depth row j, group of 32 frames); warp-specialised, with no
 // CTA-wide barrier inside the bin loop:
-//   warps 0-7: build the Toeplitz blocks of bin b+1, then fold the
-//     accumulators of bin b into per-pixel sums. Warp w reads tensor-memory
-//     lane quarter w % 4 (pixels 32 (w%4) .. +31) for frames 16 (w/4) .. +15;
-//   warp 8: bulk copies of each bin's B tile and c words into a ring of NST
+//   warp 0: bulk copies of each bin's B tile and c words into a ring of NST
 //     stages;
-//   warps 9 .. 8+NAP: the MMA chain of aperture q = warp - 9 into one of two
+//   warps 1 .. NAP: the MMA chain of aperture q = warp - 1 into one of two
 //     tensor-memory accumulator sets. One issuing warp per aperture: a single
 //     thread issuing every chain cannot keep up with N = 64 MMAs, which the
-//     tensor core finishes in about 48 cycles each.
-// mbarriers: full[s] (copy landed), aready[s] (blocks built; 8 warp arrivals),
-// sfree[s] (MMAs of the stage done; NAP commits), afull[t] (accumulator set t
-// written; NAP commits), tfree[t] (set t read out; 8 warp arrivals). Every wait
+//     tensor core finishes in about 48 cycles each;
+//   warps 4-11: build the Toeplitz blocks of bin b+1, then fold the
+//     accumulators of bin b into per-pixel sums. Warp w reads tensor-memory
+//     lane quarter w % 4 (pixels 32 (w%4) .. +31) for frames 16 ((w-4)/4) .. +15.
+// The issuing warps have the lowest warp numbers: while the build/fold warps
+// issue FMAs back to back, the schedulers favour them, and MMA issue is on
+// the critical path.
+// mbarriers: full[s] (copy landed), sfree[s] (MMAs of the stage done; NAP
+// commits), afull[t] (accumulator set t written; NAP commits), go[t] (16
+// warp arrivals: the 8 build warps for bin b, once its blocks are written,
+// and the 8 fold warps for bin b - 2, once set t is read out). Every wait
 // is bounded; on expiry the CTA raises a shared abort flag and the device
 // status word, each role drains the copies or MMAs it issued, and the CTA exits.
 constexpr int BLK_BYTES = 32 * 128;       // 32 core matrices of one part (Re or Im)
@@ -253,7 +270,7 @@ constexpr size_t GEMM_SMEM_LIMIT = 232448;  // opt-in shared memory per CTA
 constexpr size_t GEMM_SMEM_EXTRA = 24 * 8 + 16;
 template <int NAP>
 constexpr int gemm_threads() { return 384; }   // 8 build/fold warps, 1 copy warp, NAP MMA warps (+ idle)
-constexpr int REG_LAUNCH = 168, REG_CTRL = 40, REG_FOLD = 224;
+constexpr int REG_LAUNCH = 168, REG_CTRL = 96, REG_FOLD = 200;
 static_assert(2 * 128 * REG_FOLD + 128 * REG_CTRL <= 384 * REG_LAUNCH, "register split exceeds the launch budget");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -269,6 +286,14 @@ __device__ __forceinline__ void umma_elect(unsigned tmem_d, uint64_t a, uint64_t
         " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+__device__ __forceinline__ void umma_commit_elect(uint64_t *bar)
+{
+    asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+                 " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v)
@@ -319,9 +344,9 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
     auto sB = [&](int s) { return sm + s * stage + NPART * A_BYTES; };
     auto sC = [&](int s) { return reinterpret_cast<uint32_t *>(sm + s * stage + NPART * (A_BYTES + bytesB)); };
     uint64_t *full = reinterpret_cast<uint64_t *>(sm + NST * stage);    // [MAX_NST]
-    uint64_t *aready = full + MAX_NST, *sfree = aready + MAX_NST;      // [MAX_NST]
-    uint64_t *afull = sfree + MAX_NST, *tfree = afull + 2;             // [2]
-    uint64_t *dbar = tfree + 2;                                         // [4] per-warp drain
+    uint64_t *sfree = full + MAX_NST;                                   // [MAX_NST]
+    uint64_t *go = sfree + MAX_NST, *afull = go + 2;                    // [2], [2]
+    uint64_t *dbar = afull + 2;                                         // [4] per-warp drain
     unsigned *tslot = reinterpret_cast<unsigned *>(dbar + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
 
@@ -336,12 +361,11 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
     if (tid == 0) {
         for (int s = 0; s < MAX_NST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&aready[s], 8);
             mbar_init(&sfree[s], NAP);
         }
         for (int t = 0; t < 2; ++t) {
+            mbar_init(&go[t], 16);
             mbar_init(&afull[t], NAP);
-            mbar_init(&tfree[t], 8);
         }
         for (int q = 0; q < 4; ++q) mbar_init(&dbar[q], 1);
         *abort_flag = 0;
@@ -352,10 +376,10 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
     tc_fence_after();
     const unsigned tmem = *tslot;
     // Register split between the warpgroups (launch: 384 x 168 = 64512): the
-    // copy / MMA warpgroup drops to REG_CTRL, the two build/fold warpgroups rise
+    // copy / MMA warpgroup (warps 0-3) drops to REG_CTRL, the two build/fold warpgroups rise
     // to REG_FOLD (2 x 128 x REG_FOLD + 128 x REG_CTRL <= 64512). The host checks
     // that the kernel was built with 168 registers per thread before launching.
-    if (warp >= 8)
+    if (warp < 4)
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(REG_CTRL));
     else
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(REG_FOLD));
@@ -364,7 +388,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
     auto wait = [&](uint64_t *bar, unsigned parity) -> bool {
         if (mbar_try_wait(bar, parity)) return true;
         const long long t0 = clock64();
-        while (!mbar_try_wait(bar, parity)) {
+        while (!mbar_try_wait_sleep(bar, parity)) {
             if (*abort_flag) return false;
             if (clock64() - t0 > (1ll << 31)) {
                 *abort_flag = 1;
@@ -375,11 +399,11 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
         return true;
     };
 
-    if (warp >= 9 + NAP) {
+    if (warp >= 1 + NAP && warp < 4) {
         // spare warp of the control warpgroup (AS-DAX): nothing to do
-    } else if (warp >= 8) {
-        // -------- warp 8: bulk-copy ring; warps 9..: MMA chain of aperture q --------
-        const int q = warp - 9;
+    } else if (warp < 4) {
+        // -------- warp 0: bulk-copy ring; warps 1..NAP: MMA chain of aperture q --------
+        const int q = warp - 1;
         const bool producer = q < 0;
         const unsigned idesc = umma_idesc<FP16>();
         const int s0 = (q <= 0 ? kq.x : q == 1 ? kq.y : kq.z) / 16;
@@ -397,6 +421,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                     bulk_g2s(sC(s) + NXP, clo + oc, NXP * 4, &full[s]);
                 }
             }
+            __syncwarp();
             issued = b + 1;
         };
         if (producer)
@@ -411,10 +436,9 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
         } else {
             for (int b = 0; b < n_bins && ok; ++b) {
                 const int s = b % NST, t = b & 1;
-                const unsigned ps = (unsigned)(b / NST) & 1u;
-                ok = wait(&full[s], ps) && wait(&aready[s], ps);
-                if (ok && b >= 2) ok = wait(&tfree[t], (unsigned)((b - 2) >> 1) & 1u);
-                ok = __all_sync(0xffffffffu, ok);
+                // go[t]: the blocks of bin b are built (which the build warps did after
+                // its copy landed) and accumulator set t was read out for bin b - 2
+                ok = __all_sync(0xffffffffu, wait(&go[t], (unsigned)(b >> 1) & 1u));
                 if (!ok) break;
                 tc_fence_after();
                 const uint64_t da0 = umma_desc(smem_u32(sA(s)), BLK_BYTES, 128);
@@ -431,11 +455,8 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                     }
                 }
                 any = true;
-                __syncwarp();
-                if (lane == 0) {
-                    umma_commit(&sfree[s]);
-                    umma_commit(&afull[t]);
-                }
+                umma_commit_elect(&sfree[s]);
+                umma_commit_elect(&afull[t]);
             }
         }
         if (!ok && lane == 0) {
@@ -448,8 +469,8 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                 mbar_wait(&full[b % NST], (unsigned)(b / NST) & 1u);
         }
     } else {
-        // ---------------- build + fold (warps 0-7) ----------------
-        const int quarter = warp & 3, fh = warp >> 2;
+        // ---------------- build + fold (warps 4-11) ----------------
+        const int quarter = warp & 3, fh = (warp - 4) >> 2, ctid = tid - 128;
         const int i_epi = 32 * quarter + lane;
         float acc[FW][NACC];
 #pragma unroll
@@ -465,7 +486,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
             if (!wait(&full[s], (unsigned)(b / NST) & 1u)) return false;
 #pragma unroll
             for (int pidx = 0; pidx < NPART; ++pidx) {
-                const int n = tid >> 3, r = tid & 7;
+                const int n = ctid >> 3, r = ctid & 7;
                 const uint32_t *cw = sC(s) + pidx * NXP;
                 const int m0 = 8 * (n & 15) + r;
                 unsigned w[8];
@@ -481,7 +502,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&aready[s]);
+            if (lane == 0) mbar_arrive(&go[b & 1]);
             return true;
         };
         auto fold = [&](int b) -> bool {
@@ -499,7 +520,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                 if (h == 1) {
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&tfree[t]);
+                    if (lane == 0) mbar_arrive(&go[t]);   // set t is free for bin b + 2
                 }
 #pragma unroll
                 for (int ff = 0; ff < 8; ++ff) {
@@ -522,10 +543,19 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
             return true;
         };
 
+        if (lane == 0) {   // accumulator sets 0 and 1 start free (bins -2 and -1)
+            mbar_arrive(&go[0]);
+            mbar_arrive(&go[1]);
+        }
+        // Blocks are built two bins ahead, so that MMA(b+1) only waits for the
+        // fold of bin b-1 to release its accumulator set. Building bin b+2 reuses
+        // the stage of bin b+2-NST (NST >= 2), whose MMAs are done once fold(b)
+        // has seen bin b's accumulators.
         bool ok = n_bins == 0 || build(0);
+        if (ok && n_bins > 1) ok = build(1);
         for (int b = 0; b < n_bins && ok; ++b) {
-            if (b + 1 < n_bins && !build(b + 1)) ok = false;   // tensor core: MMA(b)
-            if (ok && !fold(b)) ok = false;                     // tensor core: MMA(b+1)
+            if (!fold(b)) ok = false;                            // tensor core: MMA(b+1)
+            if (ok && b + 2 < n_bins && !build(b + 2)) ok = false;
         }
         const size_t npix = (size_t)nz * NXP;
 #pragma unroll
