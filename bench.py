@@ -218,6 +218,56 @@ def run_reference(args):
     return 0
 
 
+def run_forms(args, w, pool, stream, dev):
+    """Frames/s of the batched forms (args.batch frames per call) on the frame pool;
+    each tensor-core form's image is compared with the plain FP32 form's."""
+    import torch
+    from paper_2412_02413_gb300 import pam
+    P = pool.shape[0]
+    forms = {}
+    ref_img = None
+    names = [f for f in args.forms.split(",") if f]
+    if names and names[0] != "fp32" and "fp32" in names:
+        names.remove("fp32")
+        names.insert(0, "fp32")
+    for form in names:
+        fp = pam.Plan.from_workload(w, max_frames=args.batch, form=form)
+        fo = {"image": torch.empty(args.batch, w.nz, w.nx, device=dev),
+              "rho_n": torch.empty(args.batch, w.nz, w.nx, device=dev)}
+        nb = max(1, P // args.batch)
+
+        def bstep(i):
+            s0 = (i % nb) * args.batch
+            fp.as_tax(pool[s0:s0 + args.batch], outs=fo, stream=stream)
+
+        for i in range(3):
+            bstep(i)
+        torch.cuda.synchronize()
+        fp.profile_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.batch_steps):
+            bstep(i)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms, kn, kl = fp.profile_read()
+        fms = e0.elapsed_time(e1)
+        bstep(0)
+        torch.cuda.synchronize()
+        img = fo["image"].double()
+        entry = {"frames_per_call": args.batch, "value": args.batch * args.batch_steps / (fms / 1000.0),
+                 "unit": "frames/s", "ms_per_frame": fms / (args.batch * args.batch_steps),
+                 "main_kernel_us_per_frame": 1000.0 * kms / max(kn, 1) / args.batch}
+        if form == "fp32":
+            ref_img = img
+        elif ref_img is not None:
+            entry["rel_l2_vs_fp32"] = float(torch.linalg.norm(img - ref_img) / torch.linalg.norm(ref_img))
+        forms[form] = entry
+        fp.close()
+    return forms
+
+
 # -------------------------------------------------------------- our arm --
 def run_ours(args):
     import numpy as np
@@ -238,6 +288,12 @@ def run_ours(args):
     P = pool.shape[0]
     outs = {"image": torch.empty(F, w.nz, w.nx, device=dev), "rho_n": torch.empty(F, w.nz, w.nx, device=dev)}
     stream = torch.cuda.current_stream()
+    if args.forms_only:
+        # profiling aid: only the batched forms, one JSON line
+        print(json.dumps({"forms": run_forms(args, w, pool, stream, dev), "config": {"workload": w.name}}),
+              flush=True)
+        dist.finalize()
+        return 0
 
     def step(i):
         s = (i * F) % (P - F + 1)
@@ -287,44 +343,7 @@ def run_ours(args):
     e2e_value = dist.sum_over_ranks(e2e_steps * F, device=dev) / t_e2e
 
     # Batched forms: 64 frames per call, the plain FP32 path and the tensor-core forms.
-    forms = {}
-    if not args.no_forms:
-        ref_img = None
-        for form in ("fp32", "bf16", "fp16", "bf16split"):
-            fp = pam.Plan.from_workload(w, max_frames=args.batch, form=form)
-            fo = {"image": torch.empty(args.batch, w.nz, w.nx, device=dev),
-                  "rho_n": torch.empty(args.batch, w.nz, w.nx, device=dev)}
-            nb = max(1, P // args.batch)
-
-            def bstep(i):
-                s0 = (i % nb) * args.batch
-                fp.as_tax(pool[s0:s0 + args.batch], outs=fo, stream=stream)
-
-            for i in range(3):
-                bstep(i)
-            torch.cuda.synchronize()
-            fp.profile_enable(True)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for i in range(args.batch_steps):
-                bstep(i)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            kms, kn, kl = fp.profile_read()
-            fms = e0.elapsed_time(e1)
-            bstep(0)
-            torch.cuda.synchronize()
-            img = fo["image"].double()
-            entry = {"frames_per_call": args.batch, "value": args.batch * args.batch_steps / (fms / 1000.0),
-                     "unit": "frames/s", "ms_per_frame": fms / (args.batch * args.batch_steps),
-                     "main_kernel_us_per_frame": 1000.0 * kms / max(kn, 1) / args.batch}
-            if form == "fp32":
-                ref_img = img
-            else:
-                entry["rel_l2_vs_fp32"] = float(torch.linalg.norm(img - ref_img) / torch.linalg.norm(ref_img))
-            forms[form] = entry
-            fp.close()
+    forms = {} if args.no_forms else run_forms(args, w, pool, stream, dev)
 
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -382,6 +401,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched plain / tensor-core forms")
     ap.add_argument("--batch", type=int, default=64, help="frames per call of the batched forms")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--forms", default="fp32,bf16,fp16,bf16split", help="comma list of batched forms to time")
+    ap.add_argument("--forms-only", action="store_true", help="time only the batched forms (profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -212,7 +212,7 @@ prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, 
     uint8_t *dl = SPLIT ? Blo + ((size_t)g * n_bins + b) * tile : nullptr;
     for (int idx = threadIdx.x; idx < K * NG; idx += blockDim.x) {
         const int k = idx / NG, n = idx % NG;
-        const int f = g * FG + n / 2, kind = n & 1;
+        const int f = g * FG + n % FG, kind = n / FG;   // columns: Re of the 32 frames, then Im
         float v = 0.f;
         const short kt = ktab[k];
         if (f < F && kt >= 0) {
@@ -294,6 +294,16 @@ __device__ __forceinline__ void umma_commit_elect(uint64_t *bar)
                  " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
                      smem_u32(bar))
                  : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float *v)
+{
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int t = 0; t < 8; ++t) v[t] = __uint_as_float(r[t]);
 }
 
 __device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v)
@@ -472,11 +482,13 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
         // ---------------- build + fold (warps 4-11) ----------------
         const int quarter = warp & 3, fh = (warp - 4) >> 2, ctid = tid - 128;
         const int i_epi = 32 * quarter + lane;
-        float acc[FW][NACC];
+        // Sums of frame pairs (2p, 2p+1) as float2, so that one packed FMA
+        // (fma.rn.f32x2) serves two frames.
+        float2 acc[FW / 2][NACC];
 #pragma unroll
-        for (int f = 0; f < FW; ++f)
+        for (int f = 0; f < FW / 2; ++f)
 #pragma unroll
-            for (int a = 0; a < NACC; ++a) acc[f][a] = 0.f;
+            for (int a = 0; a < NACC; ++a) acc[f][a] = make_float2(0.f, 0.f);
 
         // Thread (part, n, r) writes row r of block n: the 8 entries
         // c[(8 (n mod 16) + r - t) mod 128], t = 0..7, as one 16-byte row of
@@ -509,13 +521,16 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
             const int t = b & 1;
             if (!wait(&afull[t], (unsigned)(b >> 1) & 1u)) return false;
             tc_fence_after();
-            const unsigned base =
-                tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(t * ACC_COLS + fh * 2 * FW);
+            // columns of aperture q: Re of frames 0..31, then Im of frames 0..31
+            const unsigned base = tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(t * ACC_COLS + fh * FW);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                float r[NAP][16];
+                float re[NAP][8], im[NAP][8];
 #pragma unroll
-                for (int q = 0; q < NAP; ++q) tmem_ld16(base + (unsigned)(q * NG + 16 * h), r[q]);
+                for (int q = 0; q < NAP; ++q) {
+                    tmem_ld8(base + (unsigned)(q * NG + 8 * h), re[q]);
+                    tmem_ld8(base + (unsigned)(q * NG + FG + 8 * h), im[q]);
+                }
                 tmem_wait_ld();
                 if (h == 1) {
                     tc_fence_before();
@@ -523,20 +538,23 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                     if (lane == 0) mbar_arrive(&go[t]);   // set t is free for bin b + 2
                 }
 #pragma unroll
-                for (int ff = 0; ff < 8; ++ff) {
-                    const int f = 8 * h + ff;
-                    const float ar = r[0][2 * ff], ai = r[0][2 * ff + 1];
-                    const float br = r[1][2 * ff], bi = r[1][2 * ff + 1];
-                    acc[f][0] = fmaf(ar, ar, fmaf(ai, ai, acc[f][0]));
-                    acc[f][1] = fmaf(br, br, fmaf(bi, bi, acc[f][1]));
+                for (int pp = 0; pp < 4; ++pp) {
+                    float2 *A = acc[4 * h + pp];
+                    const float2 ar = make_float2(re[0][2 * pp], re[0][2 * pp + 1]);
+                    const float2 ai = make_float2(im[0][2 * pp], im[0][2 * pp + 1]);
+                    const float2 br = make_float2(re[1][2 * pp], re[1][2 * pp + 1]);
+                    const float2 bi = make_float2(im[1][2 * pp], im[1][2 * pp + 1]);
+                    A[0] = __ffma2_rn(ar, ar, __ffma2_rn(ai, ai, A[0]));
+                    A[1] = __ffma2_rn(br, br, __ffma2_rn(bi, bi, A[1]));
                     if constexpr (NAP == 2) {
-                        acc[f][2] = fmaf(ar, br, fmaf(ai, bi, acc[f][2]));
+                        A[2] = __ffma2_rn(ar, br, __ffma2_rn(ai, bi, A[2]));
                     } else {
-                        const float cr = r[2][2 * ff], ci = r[2][2 * ff + 1];
-                        acc[f][2] = fmaf(cr, cr, fmaf(ci, ci, acc[f][2]));
-                        acc[f][3] = fmaf(ar, br, fmaf(ai, bi, acc[f][3]));
-                        acc[f][4] = fmaf(br, cr, fmaf(bi, ci, acc[f][4]));
-                        acc[f][5] = fmaf(cr, ar, fmaf(ci, ai, acc[f][5]));
+                        const float2 cr = make_float2(re[2][2 * pp], re[2][2 * pp + 1]);
+                        const float2 ci = make_float2(im[2][2 * pp], im[2][2 * pp + 1]);
+                        A[2] = __ffma2_rn(cr, cr, __ffma2_rn(ci, ci, A[2]));
+                        A[3] = __ffma2_rn(ar, br, __ffma2_rn(ai, bi, A[3]));
+                        A[4] = __ffma2_rn(br, cr, __ffma2_rn(bi, ci, A[4]));
+                        A[5] = __ffma2_rn(cr, ar, __ffma2_rn(ci, ai, A[5]));
                     }
                 }
             }
@@ -564,8 +582,10 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
             if (fr < F && ok) {
                 const float s2 = ldexpf(1.0f, 2 * frame_exp(smax[fr]));
 #pragma unroll
-                for (int a = 0; a < NACC; ++a)
-                    part[((size_t)fr * NACC + a) * npix + (size_t)j * NXP + i_epi] = acc[f][a] * s2;
+                for (int a = 0; a < NACC; ++a) {
+                    const float v = (f & 1) ? acc[f >> 1][a].y : acc[f >> 1][a].x;
+                    part[((size_t)fr * NACC + a) * npix + (size_t)j * NXP + i_epi] = v * s2;
+                }
             }
         }
     }
