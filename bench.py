@@ -268,6 +268,74 @@ def run_forms(args, w, pool, stream, dev):
     return forms
 
 
+def run_batch(args, dev, stream):
+    """Uneven batch (workload 3): args.batch_frames frames with their own
+    sample counts and depth ranges in one graph-launched call, against a loop
+    of one-frame calls of the same frames."""
+    import numpy as np
+    import torch
+    from paper_2412_02413_gb300 import pam, synth
+    ws = synth.batch_workload(args.batch_frames)
+    frames = [(w.nt, w.nz) for w in ws]
+    common = dict(n_elem=128, pitch=0.3e-3, fs=40e6, c=1540.0, z0=5e-3, dz=synth.BATCH_DZ, n_bins=300,
+                  f_lo=0.5e6, f_hi=8e6, n_apod=3, pattern_m=16)
+    b = pam.Batch(frames=frames, **common)
+    rng = np.random.default_rng(20241203 + 3000 + 7)
+    rf = torch.from_numpy(rng.standard_normal(b.rf_total, dtype=np.float32)).to(dev)
+    img = torch.empty(b.map_total, device=dev)
+    rn = torch.empty(b.map_total, device=dev)
+    for _ in range(3):
+        b.as_tax(rf, image=img, rho_n=rn, stream=stream)
+    torch.cuda.synchronize()
+    k0 = b.info()[2]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.batch_calls):
+        b.as_tax(rf, image=img, rho_n=rn, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    b.sync(stream)
+    ms = e0.elapsed_time(e1) / args.batch_calls
+    kernels = (b.info()[2] - k0) // args.batch_calls
+    n_items, grid, _ = b.info()
+    # loop of one-frame calls (direct launches, no graph) over the first frames
+    nl = min(len(frames), args.batch_loop_frames)
+    singles = []
+    for i in range(nl):
+        s1 = pam.Batch(frames=[frames[i]], **common)
+        s1.configure(use_graph=False)
+        r1 = rf[b.rf_offsets[i]:b.rf_offsets[i] + s1.rf_total].contiguous()
+        singles.append((s1, r1, torch.empty(s1.map_total, device=dev), torch.empty(s1.map_total, device=dev)))
+    for s1, r1, i1, n1 in singles:
+        s1.as_tax(r1, image=i1, rho_n=n1, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s1, r1, i1, n1 in singles:
+        s1.as_tax(r1, image=i1, rho_n=n1, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = e0.elapsed_time(e1)
+    for s1, *_ in singles:
+        s1.close()
+    # algorithmic FP32 work: the fused path per frame plus the direct time DFT (4 flops per sample, bin, channel)
+    flops = sum(fused_flops_per_frame(len(b.bins[i]), nz, 128, 3) + 4.0 * len(b.bins[i]) * 128 * nt
+                for i, (nt, nz) in enumerate(frames))
+    peaks, _ = measured_peaks()
+    peak_tf = fp32_peak_tflops(float(peaks.get("sm_max_mhz", 2070.0)))
+    out = {"workload": "uneven_batch_128el_nt1024-8192_nz128-512_300bins", "frames_per_call": len(frames),
+           "value": len(frames) / (ms / 1000.0), "unit": "frames/s", "ms_per_call": ms,
+           "us_per_frame": 1000.0 * ms / len(frames), "kernels_per_call": kernels, "graph": True,
+           "work_items": n_items, "persistent_ctas": grid,
+           "loop_frames": nl, "loop_value": nl / (loop_ms / 1000.0), "loop_us_per_frame": 1000.0 * loop_ms / nl,
+           "achieved_tflops": flops / (ms / 1000.0) / 1e12, "fp32_peak_tflops": peak_tf,
+           "frac_fp32_peak": flops / (ms / 1000.0) / 1e12 / peak_tf,
+           "data": "synthetic Gaussian channel data of the workload's shapes"}
+    out["speedup_vs_loop"] = out["value"] / out["loop_value"]
+    b.close()
+    return out
+
+
 # -------------------------------------------------------------- our arm --
 def run_ours(args):
     import numpy as np
@@ -288,6 +356,10 @@ def run_ours(args):
     P = pool.shape[0]
     outs = {"image": torch.empty(F, w.nz, w.nx, device=dev), "rho_n": torch.empty(F, w.nz, w.nx, device=dev)}
     stream = torch.cuda.current_stream()
+    if args.batch_only:
+        print(json.dumps({"batch": run_batch(args, dev, stream)}), flush=True)
+        dist.finalize()
+        return 0
     if args.forms_only:
         # profiling aid: only the batched forms, one JSON line
         print(json.dumps({"forms": run_forms(args, w, pool, stream, dev), "config": {"workload": w.name}}),
@@ -344,6 +416,7 @@ def run_ours(args):
 
     # Batched forms: 64 frames per call, the plain FP32 path and the tensor-core forms.
     forms = {} if args.no_forms else run_forms(args, w, pool, stream, dev)
+    batch = run_batch(args, dev, stream) if args.batch_frames > 0 and rank == 0 else {}
 
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -379,6 +452,7 @@ def run_ours(args):
                          "share_of_step": (prop_ms / ms) if ms > 0 else None},
             "clocks": ck,
             "forms": forms,
+            "batch": batch,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -403,6 +477,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--forms", default="fp32,bf16,fp16,bf16split", help="comma list of batched forms to time")
     ap.add_argument("--forms-only", action="store_true", help="time only the batched forms (profiling aid)")
+    ap.add_argument("--batch-frames", type=int, default=256, help="frames of the uneven batch (0: skip)")
+    ap.add_argument("--batch-calls", type=int, default=10)
+    ap.add_argument("--batch-loop-frames", type=int, default=32, help="frames of the one-frame-call loop")
+    ap.add_argument("--batch-only", action="store_true", help="time only the uneven batch (profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -214,6 +214,74 @@ pam_status pam_profile_enable(pam_plan_t p, int on);
 pam_status pam_profile_read(pam_plan_t p, double *prop_ms, long long *prop_launches,
                             long long *kernel_launches);
 
+/* ------------------------------------------------------------------------
+ * Batches: many frames in one call, each with its own sample count, depth
+ * range and bins (Eq. 1-5, 10-11 applied to each frame on its own geometry).
+ * The time transform of a frame is the direct DFT of its selected bins, so
+ * n_samples may be any integer (no power-of-2 requirement). One call runs a
+ * fixed sequence of 4 kernels (time DFT, lateral FFT, a persistent
+ * propagate-and-correlate kernel over (frame, row tile) work items, and the
+ * per-frame normalisation), replayed as a CUDA graph that the batch captures
+ * on its first call and again whenever the buffers change.
+ * ------------------------------------------------------------------------ */
+typedef struct pam_batch_s *pam_batch_t;
+
+/* One frame of a batch. */
+typedef struct {
+    int n_samples;     /* nt of this frame, 32..16384, any integer */
+    int nz;            /* depth rows: z_j = z0_m + j dz_m (z0_m, dz_m from the common descriptor) */
+    const int *bins;   /* n_bins (common) DFT bins, 0 < k < nt/2, strictly increasing; or NULL:
+                          n_bins of the band's bins spread evenly from its first to its last
+                          (bin index floor(i (K-1)/(n_bins-1) + 1/2) of the K in-band bins),
+                          or all K when the band holds fewer than n_bins (short frames) */
+} pam_frame_desc;
+
+/* Creates a batch. `common` is a plan descriptor whose n_elem, pitch_m, fs_hz,
+ * c_mps, nx, z0_m, dz_m, f_lo_hz, f_hi_hz, n_bins (bins per frame, required),
+ * n_apod (2 or 3), apod / pattern_m, eps and flags (PAM_EVANESCENT_ZERO only)
+ * apply to every frame; its bins must be NULL and its n_samples, nz and
+ * max_frames are ignored. The batch copies everything it needs. Inputs and
+ * outputs are packed: frame f's rf [n_elem][nt_f] starts at rf_offsets[f]
+ * floats, its maps [nz_f][nx] at map_offsets[f] floats (pam_batch_layout; every
+ * offset is a multiple of 4). Errors: PAM_ERR_INVALID_ARG (descriptor),
+ * PAM_ERR_UNSUPPORTED (a tensor-core form flag), PAM_ERR_OOM, PAM_ERR_CUDA. */
+pam_status pam_batch_create(const pam_plan_desc *common, const pam_frame_desc *frames, int n_frames,
+                            pam_batch_t *out);
+
+/* Packing of a batch's buffers. rf_offsets and map_offsets (n_frames entries
+ * each) and the totals (floats) may each be NULL. */
+pam_status pam_batch_layout(pam_batch_t b, size_t *rf_offsets, size_t *map_offsets, size_t *rf_total,
+                            size_t *map_total);
+
+/* The bins of frame `frame` into bins_out (up to n_bins ints, may be NULL).
+ * Returns the frame's bin count, or 0 for a bad handle or frame index. */
+int pam_batch_bins(pam_batch_t b, int frame, int *bins_out);
+
+/* AS-TAX (n_apod 3) or AS-DAX (n_apod 2) of every frame of the batch.
+ *   rf      device float32, packed as pam_batch_layout says (16-byte aligned)
+ *   image   device float32 maps, packed; rho_n the same or NULL
+ * Asynchronous on `stream`. The first call, and a call whose buffers differ
+ * from the previous call's, captures the launch sequence into a CUDA graph on
+ * a private stream; every call then launches that graph on `stream`. Calls on
+ * one batch must not overlap on the GPU (they share its workspace). */
+pam_status pam_batch_as_tax(pam_batch_t b, const float *rf, float *image, float *rho_n, void *stream);
+
+/* Waits for `stream` and reads the batch's device status word, as pam_sync. */
+pam_status pam_batch_sync(pam_batch_t b, void *stream);
+
+/* Tuning knobs. use_graph 0 launches the kernels directly (no graph);
+ * persistent_ctas > 0 sets the grid of the persistent kernel (0: two per SM,
+ * at most one per work item). */
+pam_status pam_batch_configure(pam_batch_t b, int use_graph, int persistent_ctas);
+
+/* Work items (frame, row tile), the persistent grid in use, and the libpam
+ * kernels launched so far (a graph launch counts its 4 kernels). Any output
+ * pointer may be NULL. */
+pam_status pam_batch_info(pam_batch_t b, int *n_items, int *persistent_ctas, long long *kernel_launches);
+
+/* Frees the batch (NULL-safe). Waits for the device first. */
+void pam_batch_destroy(pam_batch_t b);
+
 /* Static description of a status code. */
 const char *pam_status_string(pam_status s);
 

@@ -1,0 +1,139 @@
+"""Measured choice of launch parameters, cached as JSON.
+
+Two knobs have no closed-form best value on a given GPU: the bin split of
+the single-frame fused kernel (how many CTAs share a row tile's bins; set by
+``Plan.set_split``) and the persistent grid of a batch
+(``Batch.configure(persistent_ctas=...)``). The tuner times each candidate
+through the library's own calls, keeps the fastest, and caches it under a key
+made of the problem's shape: (kind, n_elem, nt bucket, nz bucket, frames). nt
+and nz are bucketed to the next power of 2 so that frames of similar size
+share an entry.
+
+The selection and caching logic is plain Python and takes any timing
+function, so it is tested without a GPU.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+from typing import Callable, Dict, Iterable, Optional
+
+
+def bucket(v: int) -> int:
+    """Next power of 2 >= v (v >= 1)."""
+    v = max(1, int(v))
+    return 1 << (v - 1).bit_length()
+
+
+def make_key(kind: str, n_elem: int, nt: int, nz: int, frames: int) -> str:
+    return f"{kind}:ne{int(n_elem)}:nt{bucket(nt)}:nz{bucket(nz)}:F{int(frames)}"
+
+
+def default_cache_path() -> str:
+    p = os.environ.get("PAM_AUTOTUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "pam_gb300_autotune.json")
+
+
+class Autotuner:
+    """Keeps {key: {"best": value, "seconds": {str(value): s}}} in a JSON file."""
+
+    def __init__(self, path: Optional[str] = None):
+        self.path = path or default_cache_path()
+        self._lock = threading.Lock()
+        self._db: Dict[str, dict] = {}
+        if os.path.exists(self.path):
+            try:
+                with open(self.path) as fh:
+                    db = json.load(fh)
+                if isinstance(db, dict):
+                    self._db = {k: v for k, v in db.items() if isinstance(v, dict) and "best" in v}
+            except (OSError, ValueError):
+                self._db = {}
+
+    def lookup(self, key: str):
+        e = self._db.get(key)
+        return None if e is None else e["best"]
+
+    def entries(self) -> Dict[str, dict]:
+        return dict(self._db)
+
+    def tune(self, key: str, candidates: Iterable, run: Callable[[object], float], repeats: int = 3,
+             force: bool = False):
+        """Times ``run(c)`` (seconds per call) ``repeats`` times per candidate and
+        keeps the candidate with the smallest median. Cached unless ``force``."""
+        if not force:
+            hit = self.lookup(key)
+            if hit is not None:
+                return hit
+        cands = list(candidates)
+        if not cands:
+            raise ValueError("no candidates")
+        times = {}
+        for c in cands:
+            ts = sorted(float(run(c)) for _ in range(max(1, repeats)))
+            times[c] = ts[len(ts) // 2]
+        best = min(cands, key=lambda c: (times[c], cands.index(c)))
+        with self._lock:
+            self._db[key] = {"best": best, "seconds": {str(c): times[c] for c in cands}}
+            self._save()
+        return best
+
+    def _save(self):
+        d = os.path.dirname(self.path)
+        if d:
+            os.makedirs(d, exist_ok=True)
+        tmp = f"{self.path}.tmp{os.getpid()}"
+        with open(tmp, "w") as fh:
+            json.dump(self._db, fh, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+
+def _event_timer(call, warmup: int = 1, iters: int = 3) -> float:
+    """Seconds per call of ``call()`` from CUDA events on the current stream."""
+    import torch
+    for _ in range(warmup):
+        call()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(iters):
+        call()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / iters
+
+
+def tune_plan_split(tuner: Autotuner, plan, rf, candidates=(0, 1, 2, 4, 8, 9, 12, 16), force: bool = False):
+    """Best bin split for ``plan.as_tax(rf)`` (0 is the built-in heuristic); applied to the plan."""
+    F = rf.shape[0] if rf.dim() == 3 else 1
+    key = make_key("split", plan.n_elem, plan.n_samples, plan.nz, F)
+    outs = {}
+
+    def run(c):
+        plan.set_split(int(c))
+        return _event_timer(lambda: plan.as_tax(rf, outs=outs))
+
+    best = tuner.tune(key, candidates, run, force=force)
+    plan.set_split(int(best))
+    return best
+
+
+def tune_batch_grid(tuner: Autotuner, batch, rf, num_sms: int, force: bool = False):
+    """Best persistent grid for ``batch.as_tax(rf)``; applied to the batch."""
+    n_items, _, _ = batch.info()
+    cands = sorted({min(n_items, c) for c in (num_sms, (3 * num_sms) // 2, 2 * num_sms)})
+    key = make_key("batch_grid", batch.n_elem, max(batch.n_samples), max(batch.nz), batch.n_frames)
+    img = None
+
+    def run(c):
+        nonlocal img
+        batch.configure(use_graph=True, persistent_ctas=int(c))
+        return _event_timer(lambda: batch.as_tax(rf))
+
+    best = tuner.tune(key, cands, run, force=force)
+    batch.configure(use_graph=True, persistent_ctas=int(best))
+    return best

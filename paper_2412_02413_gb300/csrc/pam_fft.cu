@@ -166,6 +166,7 @@ time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const 
 
 // -------------------------------------------------------- lateral FFT ----
 // Q[f][b][q][u] = live[b][u] / nx * sum_e apod_q[e] S[f][b][e] exp(-2 pi i u e / nx).
+// live_fs is the frame stride of the mask (0: one mask for all frames).
 // One CTA per (bin, frame): the napq apodized rows are transformed together
 // by the shared-memory FFT. The 1/nx of the inverse lateral transform is
 // applied here.
@@ -174,7 +175,7 @@ constexpr int LAT_THREADS = 128;
 __global__ void __launch_bounds__(LAT_THREADS)
 lateral_kernel(const float2 *__restrict__ S, int ne, int nx, int log2nx, int n_bins, int napq,
                const float *__restrict__ apod, const float2 *__restrict__ twx, const float *__restrict__ live,
-               float2 *__restrict__ Q)
+               size_t live_fs, float2 *__restrict__ Q)
 {
     extern __shared__ __align__(16) float2 lbuf[];
     float2 *x = lbuf, *y = lbuf + napq * nx, *tws = lbuf + 2 * napq * nx;
@@ -193,7 +194,7 @@ lateral_kernel(const float2 *__restrict__ S, int ne, int nx, int log2nx, int n_b
     float2 *dst = Q + ((size_t)f * n_bins + b) * napq * nx;
     for (int i = threadIdx.x; i < napq * nx; i += LAT_THREADS) {
         const int u = i & (nx - 1);
-        const float l = live[(size_t)b * nx + u] * inv_nx;
+        const float l = live[(size_t)f * live_fs + (size_t)b * nx + u] * inv_nx;
         dst[i] = make_float2(X[i].x * l, X[i].y * l);
     }
 }
@@ -236,7 +237,29 @@ cudaError_t launch_lateral(const pam_plan_s &p, int n_frames, int napq, const fl
 {
     dim3 grid(p.n_bins, n_frames);
     lateral_kernel<<<grid, LAT_THREADS, lateral_smem(p.nx, napq), st>>>(p.w.S, p.ne, p.nx, ilog2i(p.nx), p.n_bins,
-                                                                        napq, apod, p.t.tw_x, p.t.live, p.w.Q);
+                                                                        napq, apod, p.t.tw_x, p.t.live, 0, p.w.Q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lateral_frames(const pam_plan_s &p, int n_frames, int napq, const float *apod,
+                                  const float *live, size_t live_fs, cudaStream_t st)
+{
+    dim3 grid(p.n_bins, n_frames);
+    lateral_kernel<<<grid, LAT_THREADS, lateral_smem(p.nx, napq), st>>>(p.w.S, p.ne, p.nx, ilog2i(p.nx), p.n_bins,
+                                                                        napq, apod, p.t.tw_x, live, live_fs, p.w.Q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tables_frame(const pam_plan_s &p, const int *bins, int n_bins, int nt, uint4 *phase, float *live,
+                                int *bin_evan, float2 *tw_t, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(bin_evan, 0, sizeof(int) * n_bins, st);
+    if (e != cudaSuccess) return e;
+    int n = n_bins * p.nx;
+    if (nt > n) n = nt;
+    tables_kernel<<<(n + 255) / 256, 256, 0, st>>>(bins, n_bins, p.nx, nt, p.d.fs_hz, p.d.c_mps, p.d.pitch_m,
+                                                    p.d.z0_m, p.d.dz_m, (p.d.flags & PAM_EVANESCENT_ZERO) ? 1 : 0,
+                                                    phase, live, bin_evan, tw_t, p.t.tw_x);
     return cudaGetLastError();
 }
 

@@ -41,6 +41,17 @@ struct EpiOut {
 // + |p3|^2, Re p2*p3, Re p3*p1 (TAX).
 inline int n_acc(int n_apod) { return n_apod == 1 ? 1 : (n_apod == 2 ? 3 : 6); }
 
+// One frame of a batch (pam_batch_*): its spectra, phase table and geometry,
+// and the offset of its [nz][nx] maps in the packed outputs.
+struct BatchFrame {
+    const float2 *Q;        // [n_bins][napq][nx]
+    const uint4 *phase;     // [n_bins][nx]
+    const int *bin_evan;    // [n_bins]
+    int n_bins, nz, nx, nt;
+    float z0f, dzf;
+    size_t out_off;         // pixel offset of the frame's maps
+};
+
 struct Workspace {
     float2 *S = nullptr;        // [max_frames][n_bins][n_elem]      selected time bins
     float2 *Q = nullptr;        // [max_frames][n_bins][napq][nx]    apodized lateral spectra / nx
@@ -108,6 +119,11 @@ namespace pam {
 cudaError_t launch_tables(const pam_plan_s &p, cudaStream_t st);
 cudaError_t launch_time_fft(const pam_plan_s &p, const float *rf, int n_frames, cudaStream_t st);
 cudaError_t launch_lateral(const pam_plan_s &p, int n_frames, int napq, const float *apod, cudaStream_t st);
+// Per-frame masks (live + f * live_fs) and per-frame plan tables for batches.
+cudaError_t launch_lateral_frames(const pam_plan_s &p, int n_frames, int napq, const float *apod,
+                                  const float *live, size_t live_fs, cudaStream_t st);
+cudaError_t launch_tables_frame(const pam_plan_s &p, const int *bins, int n_bins, int nt, uint4 *phase, float *live,
+                                int *bin_evan, float2 *tw_t, cudaStream_t st);
 // The fused propagate-and-correlate kernel. With n_split <= kMaxClusterSplit
 // it runs as clusters and also writes the per-pixel epilogue into `out`.
 cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields,
@@ -117,6 +133,12 @@ cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split
 cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, const EpiOut &out,
                             cudaStream_t st, bool from_partials = false);
 int epilogue_kernels(int napq, int n_split);   // kernels launch_epilogue launches
+// Batch (pam_batch.cu): the persistent propagate-and-correlate kernel over
+// (frame, row tile) items and the per-frame normalisation.
+cudaError_t launch_prop_batch(int nx, int napq, int grid, const BatchFrame *frames, const int2 *items, int n_items,
+                              int *counter, const EpiOut &out, cudaStream_t st);
+cudaError_t launch_normalize_batch(int n_frames, int max_npix, const BatchFrame *frames, const EpiOut &out,
+                                   cudaStream_t st);
 bool prop_uses_cluster(int n_split);
 cudaError_t prepare_kernels(const pam_plan_s &p);
 

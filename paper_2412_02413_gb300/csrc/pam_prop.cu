@@ -242,61 +242,71 @@ __device__ __forceinline__ void block_max_to(float v, unsigned *dst, float *scra
     }
 }
 
-// CLUSTER: the n_split CTAs of a row tile form one thread-block cluster. After
-// the bin loop they add their accumulators through distributed shared memory
-// (in rank order, so the sum is deterministic) and finish the per-pixel
-// epilogue themselves. Otherwise each CTA writes its partial sums to `part`
-// for epi_reduce_kernel.
-template <int NAP, int NX, bool FIELDS, bool CLUSTER>
-__global__ void __launch_bounds__(PROP_THREADS, 2)
-prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
-                 const int *__restrict__ bin_evan, int n_bins, int nz,
-                 float z0f, float dzf, int n_split, float *__restrict__ part, float2 *__restrict__ fields,
-                 EpiOut out)
+// Shared-memory regions of the fused kernel (layout of prop_smem_bytes).
+template <int NAP, int NX>
+struct PropSmem {
+    uint64_t *full;   // [NSTAGE] data of a stage has landed
+    uint64_t *empty;  // [NSTAGE] all warps are done with a stage
+    float2 *sQ;       // [NSTAGE][NAP][NX] spectra
+    uint4 *sD;        // [NSTAGE][NX] phase words
+    float2 *sW;       // [NX/2] exp(+2 pi i m / (nx/2))
+    float2 *sT;       // per-warp transpose regions
+    __device__ explicit PropSmem(unsigned char *raw)
+    {
+        full = reinterpret_cast<uint64_t *>(raw);
+        empty = full + NSTAGE;
+        sQ = reinterpret_cast<float2 *>(raw + 128);
+        sD = reinterpret_cast<uint4 *>(sQ + NSTAGE * NAP * NX);
+        sW = reinterpret_cast<float2 *>(sD + NSTAGE * NX);
+        sT = sW + NX / 2;
+    }
+    // second-factor twiddles and the staging barriers; every thread calls this once
+    __device__ void init() const
+    {
+        for (int m = threadIdx.x; m < NX / 2; m += PROP_THREADS) {
+            float s, c;
+            sincospif(2.0f * (float)m / (float)(NX / 2), &s, &c);
+            sW[m] = make_float2(c, s);
+        }
+        if (threadIdx.x == 0) {
+            for (int st = 0; st < NSTAGE; ++st) {
+                mbar_init(&full[st], 1);
+                mbar_init(&empty[st], PROP_WARPS);
+            }
+            mbar_fence_init();
+        }
+        __syncthreads();
+    }
+};
+
+// The bin loop of one row tile: Eq. 2 phasors, the inverse lateral DFT and
+// the per-pixel sums over bins [b_begin, b_begin + nb) of one frame. Qf is the
+// frame's [n_bins][NAP][NX] spectra; row jj (clamped into the frame) at depth
+// zj. `seq` counts the bins this CTA staged before this call: the staging
+// ring's stage and phase continue from it. With FIELDS, lanes of valid rows
+// also write bin b's fields to fields_row + b * bin_stride. Returns false if a
+// bounded wait expired; the copies still in flight have landed by then.
+template <int NAP, int NX, bool FIELDS>
+__device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const float2 *__restrict__ Qf,
+                                          const uint4 *__restrict__ phase, const int *__restrict__ bin_evan,
+                                          int b_begin, int nb, int jj, float zj, unsigned seq,
+                                          float (&acc)[8][Acc<NAP>::N], float2 *__restrict__ fields_row,
+                                          bool row_ok, size_t bin_stride)
 {
     using S = Shape<NX>;
-    constexpr int H = S::H, L2 = S::L2, LPR = S::LPR, RPW = S::RPW, RPC = S::RPC, KPL = S::KPL;
+    constexpr int H = S::H, L2 = S::L2, LPR = S::LPR, RPW = S::RPW, KPL = S::KPL;
     constexpr int TS = S::TS, RS = S::RS;
-    constexpr int NACC = Acc<NAP>::N;
     constexpr int NOUT = KPL * L2;  // 8 pixels per lane
-
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);   // [NSTAGE] data of a stage has landed
-    uint64_t *empty = full + NSTAGE;                            // [NSTAGE] all warps are done with a stage
-    float2 *sQ = reinterpret_cast<float2 *>(smem_raw + 128);
-    uint4 *sD = reinterpret_cast<uint4 *>(sQ + NSTAGE * NAP * NX);
-    float2 *sW = reinterpret_cast<float2 *>(sD + NSTAGE * NX);
-    float2 *sT = sW + H;
-
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
-    const int f = blockIdx.z, split = blockIdx.y;
-    const int j = blockIdx.x * RPC + warp * RPW + r;
-    const bool row_ok = j < nz;
-    const int jj = row_ok ? j : nz - 1;
-    const int b_begin = (int)(((long long)n_bins * split) / n_split);
-    const int b_end = (int)(((long long)n_bins * (split + 1)) / n_split);
+    float2 *myT = sm.sT + (size_t)warp * (NAP * RPW * 2 * RS);
+    const float2 *sW = sm.sW;
 
-    float2 *myT = sT + (size_t)warp * (NAP * RPW * 2 * RS);
-
-    // second-factor twiddles exp(+2 pi i m / H), m < H
-    for (int m = tid; m < H; m += PROP_THREADS) {
-        float s, c;
-        sincospif(2.0f * (float)m / (float)H, &s, &c);
-        sW[m] = make_float2(c, s);
-    }
     // Radix-2 DIF split folded into the phase: lanes of half g take
     // x_g[n'] = exp(2 pi i g n'/nx) (P[n'] + (-1)^g P[n'+H]).
     const unsigned g_unit = g ? (1u << (32 - S::LOG2NX)) : 0u;
     const unsigned g_half = g ? 0x80000000u : 0u;
     const unsigned jw = (unsigned)jj;
-    const float zj = z0f + (float)jj * dzf;
-
-    float acc[NOUT][NACC];
-#pragma unroll
-    for (int o = 0; o < NOUT; ++o)
-#pragma unroll
-        for (int a = 0; a < NACC; ++a) acc[o][a] = 0.0f;
 
     // Staging pipeline: thread 0 keeps NSTAGE-1 bins in flight with TMA bulk
     // copies (spectra + phase words), each completing on the stage's `full`
@@ -304,24 +314,16 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
     // finished with the stage. Warps can therefore run up to NSTAGE-1 bins
     // apart, with no CTA-wide barrier per bin.
     constexpr unsigned BYTES_Q = NAP * NX * sizeof(float2), BYTES_D = NX * sizeof(uint4);
-    if (tid == 0) {
-        for (int st = 0; st < NSTAGE; ++st) {
-            mbar_init(&full[st], 1);
-            mbar_init(&empty[st], PROP_WARPS);
-        }
-        mbar_fence_init();
-    }
-    __syncthreads();
-    const int nb = b_end - b_begin;
     int issued = 0;    // producer (thread 0): bins whose copies have been issued
     bool ok = true;    // false once a bounded wait expired
     auto issue_next = [&]() -> bool {
-        const int st = issued % NSTAGE;
-        if (issued >= NSTAGE && !mbar_wait(&empty[st], ((issued / NSTAGE) - 1) & 1)) return false;
+        const unsigned n = seq + (unsigned)issued;
+        const int st = (int)(n % NSTAGE);
+        if (n >= NSTAGE && !mbar_wait(&sm.empty[st], ((n / NSTAGE) - 1) & 1)) return false;
         const int b = b_begin + issued;
-        mbar_expect_tx(&full[st], BYTES_Q + BYTES_D);
-        bulk_g2s(sQ + st * NAP * NX, Q + ((size_t)f * n_bins + b) * NAP * NX, BYTES_Q, &full[st]);
-        bulk_g2s(sD + st * NX, phase + (size_t)b * NX, BYTES_D, &full[st]);
+        mbar_expect_tx(&sm.full[st], BYTES_Q + BYTES_D);
+        bulk_g2s(sm.sQ + st * NAP * NX, Qf + (size_t)b * NAP * NX, BYTES_Q, &sm.full[st]);
+        bulk_g2s(sm.sD + st * NX, phase + (size_t)b * NX, BYTES_D, &sm.full[st]);
         ++issued;
         return true;
     };
@@ -331,15 +333,16 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
     int done = 0;      // bins this warp has finished
     for (int i = 0; i < nb; ++i) {
         if (tid == 0 && issued < nb) ok = issue_next();
-        const int stage = i % NSTAGE;
-        if (ok) ok = mbar_wait(&full[stage], (i / NSTAGE) & 1);
+        const unsigned n = seq + (unsigned)i;
+        const int stage = (int)(n % NSTAGE);
+        if (ok) ok = mbar_wait(&sm.full[stage], (n / NSTAGE) & 1);
         if (!__all_sync(0xffffffffu, ok)) {
             ok = false;
             break;
         }
         const int b = b_begin + i;
-        const float2 *cQ = sQ + stage * NAP * NX;
-        const uint4 *cD = sD + stage * NX;
+        const float2 *cQ = sm.sQ + stage * NAP * NX;
+        const uint4 *cD = sm.sD + stage * NX;
         const bool evan = bin_evan[b] != 0;
 
         // Eq. 2 phasors of this lane's 16 lateral bins at depth z_j. The row's
@@ -415,7 +418,7 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
         }
         if constexpr (FIELDS) {
             if (row_ok) {  // fields of bin b
-                float2 *dst = fields + (((size_t)f * n_bins + b) * nz + j) * NX;
+                float2 *dst = fields_row + (size_t)b * bin_stride;
 #pragma unroll
                 for (int o = 0; o < NOUT; ++o) {
                     const int k1 = n2 * KPL + o / L2, k2 = o % L2;
@@ -424,15 +427,60 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
             }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[stage]);
+        if (lane == 0) mbar_arrive(&sm.empty[stage]);
         done = i + 1;
     }
-    if (!ok) {
-        if (lane == 0) atomicOr(out.status, 1);
-        // let copies still in flight land before the CTA's shared memory goes away
-        if (tid == 0)
-            for (int k = done; k < issued; ++k) mbar_wait(&full[k % NSTAGE], (k / NSTAGE) & 1);
+    if (!ok && tid == 0) {
+        // let copies still in flight land before the stages are reused or the CTA exits
+        for (int k = done; k < issued; ++k) {
+            const unsigned n = seq + (unsigned)k;
+            mbar_wait(&sm.full[n % NSTAGE], (n / NSTAGE) & 1);
+        }
     }
+    return ok;
+}
+
+// CLUSTER: the n_split CTAs of a row tile form one thread-block cluster. After
+// the bin loop they add their accumulators through distributed shared memory
+// (in rank order, so the sum is deterministic) and finish the per-pixel
+// epilogue themselves. Otherwise each CTA writes its partial sums to `part`
+// for epi_reduce_kernel.
+template <int NAP, int NX, bool FIELDS, bool CLUSTER>
+__global__ void __launch_bounds__(PROP_THREADS, 2)
+prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
+                 const int *__restrict__ bin_evan, int n_bins, int nz,
+                 float z0f, float dzf, int n_split, float *__restrict__ part, float2 *__restrict__ fields,
+                 EpiOut out)
+{
+    using S = Shape<NX>;
+    constexpr int L2 = S::L2, LPR = S::LPR, RPW = S::RPW, RPC = S::RPC, KPL = S::KPL;
+    constexpr int NACC = Acc<NAP>::N;
+    constexpr int NOUT = KPL * L2;  // 8 pixels per lane
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const PropSmem<NAP, NX> sm(smem_raw);
+    float2 *sT = sm.sT;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
+    const int f = blockIdx.z, split = blockIdx.y;
+    const int j = blockIdx.x * RPC + warp * RPW + r;
+    const bool row_ok = j < nz;
+    const int jj = row_ok ? j : nz - 1;
+    const int b_begin = (int)(((long long)n_bins * split) / n_split);
+    const int b_end = (int)(((long long)n_bins * (split + 1)) / n_split);
+
+    sm.init();
+    float acc[NOUT][NACC];
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[o][a] = 0.0f;
+    const bool ok = prop_bins<NAP, NX, FIELDS>(
+        sm, Q + (size_t)f * n_bins * NAP * NX, phase, bin_evan, b_begin, b_end - b_begin, jj,
+        z0f + (float)jj * dzf, 0u, acc, FIELDS ? fields + ((size_t)f * n_bins * nz + j) * NX : nullptr, row_ok,
+        (size_t)nz * NX);
+    if (!ok && lane == 0) atomicOr(out.status, 1);
     const bool aborted = __syncthreads_or(!ok) != 0;
 
     if constexpr (CLUSTER) {
@@ -548,6 +596,80 @@ epi_normalize_kernel(const float4 *__restrict__ rho_tmp, const float4 *__restric
     if (rho_n) rho_n[o] = rn;
 }
 
+// Persistent form for a batch of frames with their own bins and depth grids
+// (uneven sample counts and depth ranges). Work items are (frame, row tile)
+// pairs taken from a global counter; an item runs every bin of its frame, so
+// its per-pixel epilogue follows directly from the registers. The staging
+// ring's position carries over from item to item.
+template <int NAP, int NX>
+__global__ void __launch_bounds__(PROP_THREADS, 2)
+prop_batch_kernel(const BatchFrame *__restrict__ frames, const int2 *__restrict__ items, int n_items,
+                  int *__restrict__ counter, EpiOut out)
+{
+    using S = Shape<NX>;
+    constexpr int L2 = S::L2, LPR = S::LPR, RPW = S::RPW, RPC = S::RPC, KPL = S::KPL;
+    constexpr int NACC = Acc<NAP>::N;
+    constexpr int NOUT = KPL * L2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const PropSmem<NAP, NX> sm(smem_raw);
+    __shared__ int s_item;
+    __shared__ float wmax[PROP_THREADS / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
+    sm.init();
+    unsigned seq = 0;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const int2 w = items[it];
+        const BatchFrame fr = frames[w.x];
+        const int j = w.y * RPC + warp * RPW + r;
+        const bool row_ok = j < fr.nz;
+        const int jj = row_ok ? j : fr.nz - 1;
+        float acc[NOUT][NACC];
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o)
+#pragma unroll
+            for (int a = 0; a < NACC; ++a) acc[o][a] = 0.0f;
+        const bool ok = prop_bins<NAP, NX, false>(sm, fr.Q, fr.phase, fr.bin_evan, 0, fr.n_bins, jj,
+                                                  fr.z0f + (float)jj * fr.dzf, seq, acc, nullptr, row_ok, 0);
+        seq += (unsigned)fr.n_bins;
+        if (!ok && lane == 0) atomicOr(out.status, 1);
+        if (__syncthreads_or(!ok)) break;
+        float rmax = 0.0f;
+        if (row_ok) {
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) {
+                const int k1 = n2 * KPL + o / L2, k2 = o % L2;
+                const int i = 2 * (k1 + 8 * k2) + g;
+                rmax = fmaxf(rmax, pixel_epilogue<NAP>(acc[o], out, 0, fr.out_off + (size_t)j * NX + i));
+            }
+        }
+        block_max_to(rmax, out.fmax + w.x, wmax, PROP_THREADS);
+    }
+}
+
+// Per-frame rho_n and image for a batch packed by per-frame pixel offsets.
+__global__ void __launch_bounds__(EPI_THREADS)
+epi_normalize_batch_kernel(const BatchFrame *__restrict__ frames, const float *__restrict__ rho_tmp,
+                           const float *__restrict__ e_tmp, const unsigned *__restrict__ fmax,
+                           float *__restrict__ image, float *__restrict__ rho_n)
+{
+    const int f = blockIdx.y;
+    const BatchFrame fr = frames[f];
+    const size_t npix = (size_t)fr.nz * fr.nx;
+    const float m = __uint_as_float(fmax[f]);
+    for (size_t x = (size_t)blockIdx.x * EPI_THREADS + threadIdx.x; x < npix; x += (size_t)gridDim.x * EPI_THREADS) {
+        const size_t o = fr.out_off + x;
+        const float rn = rho_tmp[o] / m;
+        image[o] = rn * rn * e_tmp[o];
+        if (rho_n) rho_n[o] = rn;
+    }
+}
+
 template <int NAP, int NX, bool FIELDS, bool CLUSTER>
 cudaError_t launch_prop_t(const pam_plan_s &p, int n_frames, int n_split, float *fields, const EpiOut &out,
                           cudaStream_t st)
@@ -614,7 +736,27 @@ template <int NX>
 cudaError_t prepare_nx()
 {
     cudaError_t e = prepare_nc<NX, true>();
-    return e != cudaSuccess ? e : prepare_nc<NX, false>();
+    if (e == cudaSuccess) e = prepare_nc<NX, false>();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(prop_batch_kernel<2, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)prop_smem_bytes<2, NX>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(prop_batch_kernel<3, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)prop_smem_bytes<3, NX>());
+    return e;
+}
+
+template <int NX>
+cudaError_t launch_batch_nx(int napq, int grid, const BatchFrame *frames, const int2 *items, int n_items,
+                            int *counter, const EpiOut &out, cudaStream_t st)
+{
+    if (napq == 2)
+        prop_batch_kernel<2, NX><<<grid, PROP_THREADS, prop_smem_bytes<2, NX>(), st>>>(frames, items, n_items,
+                                                                                      counter, out);
+    else
+        prop_batch_kernel<3, NX><<<grid, PROP_THREADS, prop_smem_bytes<3, NX>(), st>>>(frames, items, n_items,
+                                                                                      counter, out);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -680,6 +822,28 @@ cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_s
     if (napq == 1) return cudaSuccess;
     epi_normalize_kernel<<<grid, EPI_THREADS, 0, st>>>(v4(out.rho_tmp), v4(out.e_tmp), out.fmax, npix4,
                                                        v4(out.out_main), v4(out.rho_n));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prop_batch(int nx, int napq, int grid, const BatchFrame *frames, const int2 *items, int n_items,
+                              int *counter, const EpiOut &out, cudaStream_t st)
+{
+    if (napq != 2 && napq != 3) return cudaErrorInvalidValue;
+    switch (nx) {
+    case 16: return launch_batch_nx<16>(napq, grid, frames, items, n_items, counter, out, st);
+    case 32: return launch_batch_nx<32>(napq, grid, frames, items, n_items, counter, out, st);
+    case 64: return launch_batch_nx<64>(napq, grid, frames, items, n_items, counter, out, st);
+    case 128: return launch_batch_nx<128>(napq, grid, frames, items, n_items, counter, out, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_normalize_batch(int n_frames, int max_npix, const BatchFrame *frames, const EpiOut &out,
+                                   cudaStream_t st)
+{
+    dim3 grid((unsigned)((max_npix + EPI_THREADS - 1) / EPI_THREADS), (unsigned)n_frames);
+    epi_normalize_batch_kernel<<<grid, EPI_THREADS, 0, st>>>(frames, out.rho_tmp, out.e_tmp, out.fmax,
+                                                             out.out_main, out.rho_n);
     return cudaGetLastError();
 }
 

@@ -44,6 +44,11 @@ class PlanDesc(ctypes.Structure):
     ]
 
 
+class FrameDesc(ctypes.Structure):
+    """Mirror of ``pam_frame_desc``."""
+    _fields_ = [("n_samples", ctypes.c_int), ("nz", ctypes.c_int), ("bins", ctypes.POINTER(ctypes.c_int))]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -65,6 +70,17 @@ _SIGS = {
     "pam_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_longlong)]),
+    "pam_batch_create": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(FrameDesc), ctypes.c_int,
+                                        ctypes.POINTER(_VP)]),
+    "pam_batch_layout": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "pam_batch_bins": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "pam_batch_as_tax": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "pam_batch_sync": (ctypes.c_int, [_VP, _VP]),
+    "pam_batch_configure": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    "pam_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_longlong)]),
+    "pam_batch_destroy": (None, [_VP]),
     "pam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pam_last_error": (ctypes.c_char_p, []),
 }
@@ -290,6 +306,114 @@ class Plan:
 
     def sync(self, stream=None):
         _check(load().pam_sync(self._h, _stream_ptr(stream)))
+
+
+class Batch:
+    """Frames with their own sample counts, depth ranges and bins, run in one
+    call (``pam_batch_*``): a time DFT of the selected bins (any nt), the
+    lateral FFTs, the persistent propagate-and-correlate kernel and the
+    per-frame normalisation, replayed as a CUDA graph.
+
+    ``frames`` is a list of ``(n_samples, nz)`` or ``(n_samples, nz, bins)``.
+    Without explicit bins each frame takes ``n_bins`` of its band's bins spread
+    evenly. Inputs and outputs are packed 1-D float32 tensors; ``rf_offsets``
+    and ``map_offsets`` give each frame's start."""
+
+    def __init__(self, n_elem: int, pitch: float, fs: float, c: float, frames, z0: float, dz: float,
+                 n_bins: int, f_lo: float, f_hi: float, n_apod: int = 3, apod=None, pattern_m: int = 16,
+                 eps: float = 1e-3, evanescent_zero: bool = False, nx: int = 0):
+        _require_cuda()
+        L = load()
+        d = PlanDesc()
+        L.pam_plan_desc_init(ctypes.byref(d))
+        d.n_elem, d.pitch_m, d.fs_hz, d.c_mps = int(n_elem), float(pitch), float(fs), float(c)
+        d.nx, d.z0_m, d.dz_m = int(nx), float(z0), float(dz)
+        d.f_lo_hz, d.f_hi_hz, d.n_bins, d.n_apod = float(f_lo), float(f_hi), int(n_bins), int(n_apod)
+        self._apod_keep = None
+        if apod is not None:
+            self._apod_keep = np.ascontiguousarray(np.asarray(apod, dtype=np.float32))
+            d.apod = self._apod_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        d.pattern_m, d.eps = int(pattern_m), float(eps)
+        d.flags = PAM_EVANESCENT_ZERO if evanescent_zero else 0
+        F = len(frames)
+        fd = (FrameDesc * F)()
+        self._keep = []
+        for i, fr in enumerate(frames):
+            fd[i].n_samples, fd[i].nz = int(fr[0]), int(fr[1])
+            if len(fr) > 2 and fr[2] is not None:
+                b = np.ascontiguousarray(np.asarray(fr[2], dtype=np.int32))
+                self._keep.append(b)
+                fd[i].bins = b.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        h = _VP()
+        _check(L.pam_batch_create(ctypes.byref(d), fd, F, ctypes.byref(h)))
+        self._h = h
+        self.n_frames, self.n_elem, self.n_apod, self.n_bins = F, int(n_elem), int(n_apod), int(n_bins)
+        self.nx = self.n_elem if not nx else int(nx)
+        self.n_samples = [int(fr[0]) for fr in frames]
+        self.nz = [int(fr[1]) for fr in frames]
+        ro = (ctypes.c_size_t * F)()
+        mo = (ctypes.c_size_t * F)()
+        rt, mt = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(L.pam_batch_layout(h, ro, mo, ctypes.byref(rt), ctypes.byref(mt)))
+        self.rf_offsets = [int(v) for v in ro]
+        self.map_offsets = [int(v) for v in mo]
+        self.rf_total, self.map_total = int(rt.value), int(mt.value)
+        self.bins = []
+        for i in range(F):
+            out = np.zeros(self.n_bins, dtype=np.int32)
+            n = L.pam_batch_bins(h, i, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+            self.bins.append(out[:n].copy())
+
+    def pack_rf(self, frames_rf) -> "object":
+        """Packs per-frame [n_elem][n_samples] arrays into the batch's rf layout (device tensor)."""
+        torch = _require_cuda()
+        buf = torch.zeros(self.rf_total, dtype=torch.float32)
+        for i, a in enumerate(frames_rf):
+            t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).reshape(-1)
+            buf[self.rf_offsets[i]:self.rf_offsets[i] + t.numel()] = t
+        return buf.cuda()
+
+    def unpack(self, maps, i: int):
+        """Frame i's [nz][nx] view of a packed map tensor."""
+        n = self.nz[i] * self.nx
+        return maps[self.map_offsets[i]:self.map_offsets[i] + n].view(self.nz[i], self.nx)
+
+    def as_tax(self, rf, image=None, rho_n=None, want_rho_n: bool = True, stream=None):
+        """AS-TAX / AS-DAX of every frame. Returns (image, rho_n) packed tensors."""
+        torch = _require_cuda()
+        if not isinstance(rf, torch.Tensor) or not rf.is_cuda or rf.dtype != torch.float32:
+            raise TypeError("rf must be a float32 CUDA tensor")
+        if rf.numel() < self.rf_total:
+            raise ValueError(f"rf must hold {self.rf_total} floats")
+        if image is None:
+            image = torch.empty(self.map_total, dtype=torch.float32, device="cuda")
+        if rho_n is None and want_rho_n:
+            rho_n = torch.empty(self.map_total, dtype=torch.float32, device="cuda")
+        _check(load().pam_batch_as_tax(self._h, _dptr(rf), _dptr(image), _dptr(rho_n), _stream_ptr(stream)))
+        return image, rho_n
+
+    def configure(self, use_graph: bool = True, persistent_ctas: int = 0):
+        _check(load().pam_batch_configure(self._h, int(bool(use_graph)), int(persistent_ctas)))
+
+    def info(self):
+        """(work items, persistent grid, libpam kernel launches so far)."""
+        n, g, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        _check(load().pam_batch_info(self._h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(k)))
+        return n.value, g.value, k.value
+
+    def sync(self, stream=None):
+        _check(load().pam_batch_sync(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pam_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def status_string(s: int) -> str:

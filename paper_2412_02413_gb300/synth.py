@@ -73,7 +73,11 @@ class Workload:
         if self.n_bins is None or self.n_bins >= allk.size:
             return allk.astype(np.int32)
         K = allk.size
-        idx = np.floor(np.arange(self.n_bins) * (K - 1) / (self.n_bins - 1) + 0.5).astype(np.int64)
+        n = self.n_bins
+        if n == 1:
+            return allk[:1].astype(np.int32)
+        # floor(i (K-1)/(n-1) + 1/2) in integers (the rule libpam's batches use)
+        idx = (2 * np.arange(n, dtype=np.int64) * (K - 1) + (n - 1)) // (2 * (n - 1))
         return allk[idx].astype(np.int32)
 
     def pixel_x(self) -> np.ndarray:
@@ -99,6 +103,28 @@ def workload(wid: int) -> Workload:
                         n_bins=300, pattern_m=16, n_sources=(1, 6), snr_db=20.0,
                         source_z=(10e-3, 55e-3), harmonic_f0=(1.0e6, 1.5e6), workload_id=2)
     raise ValueError(f"unknown workload {wid}")
+
+
+BATCH_DZ = 55e-3 / 511      # the 0.1076 mm depth step of the 128 x 512 workload
+
+
+def batch_workload(n_frames: int = 256, seed_offset: int = 0) -> List[Workload]:
+    """Workload 3 (uneven batch): frames of a 128-element array at 40 MHz.
+    Each frame draws its sample count uniformly in [1024, 8192] (not a power
+    of 2 in general) and its depth rows uniformly in [128, 512] from 5 mm at
+    0.1076 mm, 1-8 sources, and uses 300 bins spread over 0.5-8 MHz at its own
+    bin spacing fs / nt. Frame f's sources use seed 20241203 + 3000 + f."""
+    rng = np.random.default_rng(SEED_BASE + 3000 + 999_983 + seed_offset)
+    out = []
+    for f in range(n_frames):
+        nt = int(rng.integers(1024, 8193))
+        nz = int(rng.integers(128, 513))
+        z_last = 5e-3 + (nz - 1) * BATCH_DZ
+        out.append(Workload(name=f"batch_frame{f}", n_elem=128, pitch=0.3e-3, fs=40e6, nt=nt, c=1540.0, nz=nz,
+                            z_first=5e-3, z_last=z_last, f_lo=0.5e6, f_hi=8e6, n_bins=300, pattern_m=16,
+                            n_sources=(1, 8), snr_db=20.0, source_z=(10e-3, min(55e-3, z_last)),
+                            harmonic_f0=(1.0e6, 1.5e6), workload_id=3))
+    return out
 
 
 def tiny_workload(n_elem=16, nt=128, nz=8, n_bins=None, fs=20e6, pattern_m=2) -> Workload:

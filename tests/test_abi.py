@@ -110,3 +110,60 @@ def test_null_arguments(lib):
     assert lib.pam_as_backprop(None, None, 1, -1, None, None, None) == 1
     assert lib.pam_sync(None, None) == 1
     assert lib.pam_plan_bins(None, None) == 0
+
+
+def _batch_desc(lib, **kw):
+    return _desc(lib, **{"n_bins": 8, **kw})
+
+
+def _frames(specs):
+    arr = (pam.FrameDesc * max(1, len(specs)))()
+    for i, (nt, nz) in enumerate(specs):
+        arr[i].n_samples, arr[i].nz = nt, nz
+    return arr
+
+
+@pytest.mark.parametrize("kw,specs,status", [
+    ({}, [], 1),                                  # no frames
+    ({"n_apod": 1}, [(512, 16)], 1),              # batches are AS-DAX / AS-TAX
+    ({"n_bins": 0}, [(512, 16)], 1),              # bins per frame are required
+    ({"flags": 0x10}, [(512, 16)], 2),            # tensor-core forms are not batched
+    ({}, [(512, 16), (31, 16)], 1),               # frame n_samples below 32
+    ({}, [(512, 16), (20000, 16)], 1),            # frame n_samples above 16384
+    ({}, [(512, 0)], 1),                          # frame with no depth rows
+    ({"f_lo_hz": 5.01e6, "f_hi_hz": 5.02e6}, [(512, 16)], 1),   # band holds no bin
+])
+def test_bad_batch_is_rejected(lib, kw, specs, status):
+    d = _batch_desc(lib, **kw)
+    fr = _frames(specs)
+    h = ctypes.c_void_p(123)
+    s = lib.pam_batch_create(ctypes.byref(d), fr, len(specs), ctypes.byref(h))
+    assert s == status, (kw, specs, s, lib.pam_last_error())
+    assert h.value is None
+
+
+def test_batch_rejects_common_bins(lib):
+    arr = (ctypes.c_int * 2)(3, 4)
+    d = _batch_desc(lib, bins=ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)))
+    h = ctypes.c_void_p()
+    assert lib.pam_batch_create(ctypes.byref(d), _frames([(512, 16)]), 1, ctypes.byref(h)) == 1
+
+
+def test_batch_rejects_bad_frame_bins(lib):
+    for bins in ([0, 5], [5, 5], [9, 4], [10, 256]):
+        arr = (ctypes.c_int * len(bins))(*bins)
+        d = _batch_desc(lib, n_bins=len(bins))
+        fr = _frames([(512, 16)])
+        fr[0].bins = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int))
+        h = ctypes.c_void_p()
+        assert lib.pam_batch_create(ctypes.byref(d), fr, 1, ctypes.byref(h)) == 1, bins
+
+
+def test_batch_null_handles(lib):
+    assert lib.pam_batch_as_tax(None, None, None, None, None) == 1
+    assert lib.pam_batch_sync(None, None) == 1
+    assert lib.pam_batch_configure(None, 1, 0) == 1
+    assert lib.pam_batch_info(None, None, None, None) == 1
+    assert lib.pam_batch_layout(None, None, None, None, None) == 1
+    assert lib.pam_batch_bins(None, 0, None) == 0
+    lib.pam_batch_destroy(None)

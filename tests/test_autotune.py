@@ -1,0 +1,44 @@
+"""Autotuner selection and cache logic, with a fake timer (no GPU)."""
+import json
+
+from paper_2412_02413_gb300 import autotune
+
+
+def test_bucket_and_key():
+    assert [autotune.bucket(v) for v in (1, 2, 3, 1024, 1025, 8192)] == [1, 2, 4, 1024, 2048, 8192]
+    assert autotune.make_key("split", 128, 4096, 512, 1) == "split:ne128:nt4096:nz512:F1"
+    assert autotune.make_key("split", 128, 4000, 300, 1) == "split:ne128:nt4096:nz512:F1"
+
+
+def test_picks_the_fastest_median_and_caches(tmp_path):
+    path = str(tmp_path / "db.json")
+    t = autotune.Autotuner(path)
+    calls = []
+    cost = {1: [3.0, 1.0, 3.0], 2: [2.0, 2.0, 2.0], 4: [5.0, 0.1, 5.0]}   # medians 3, 2, 5
+
+    def run(c):
+        calls.append(c)
+        return cost[c][sum(1 for x in calls if x == c) - 1]
+
+    assert t.tune("k", [1, 2, 4], run) == 2
+    assert len(calls) == 9
+    # cached: no more timing, and a fresh tuner reads the file
+    assert t.tune("k", [1, 2, 4], run) == 2 and len(calls) == 9
+    t2 = autotune.Autotuner(path)
+    assert t2.lookup("k") == 2
+    db = json.load(open(path))
+    assert db["k"]["seconds"] == {"1": 3.0, "2": 2.0, "4": 5.0}
+
+
+def test_ties_keep_the_first_candidate_and_force_retunes(tmp_path):
+    t = autotune.Autotuner(str(tmp_path / "db.json"))
+    assert t.tune("k", [8, 4, 2], lambda c: 1.0) == 8
+    assert t.tune("k", [8, 4, 2], lambda c: float(c), force=True) == 2
+
+
+def test_corrupt_cache_is_ignored(tmp_path):
+    p = tmp_path / "db.json"
+    p.write_text("{not json")
+    t = autotune.Autotuner(str(p))
+    assert t.lookup("k") is None
+    assert t.tune("k", [1], lambda c: 1.0) == 1

@@ -1,0 +1,197 @@
+"""Batches (pam_batch_*): frames with their own sample counts (not powers of
+2), depth ranges and bins in one call, against the FP64 oracle frame by frame.
+Each frame of a batch is the plain AS-TAX / AS-DAX problem of its own
+geometry, so the oracle needs nothing new: it runs each frame on its own.
+
+Tolerances are the plain path's: relative L2 <= 1e-5 on energy maps, max
+|d rho_n| <= 1e-5. Random channel data have no dominant pixel, so the peak
+is compared on the synthetic-source frames only."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import NCC_TOL, REL_L2_TOL, peak, rel_l2
+from paper_2412_02413_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+C = 1540.0
+PITCH = 0.3e-3
+
+
+def _pam():
+    from paper_2412_02413_gb300 import pam
+    return pam
+
+
+def _batch(ne, frames, n_bins, fs=20e6, f_lo=1e6, f_hi=8e6, n_apod=3, pattern_m=2, z0=4e-3, dz=0.45e-3, **kw):
+    return _pam().Batch(n_elem=ne, pitch=PITCH, fs=fs, c=C, frames=frames, z0=z0, dz=dz, n_bins=n_bins,
+                        f_lo=f_lo, f_hi=f_hi, n_apod=n_apod, pattern_m=pattern_m, **kw)
+
+
+def _oracle_frame(b, i, rf_i, apod, fs, z0, dz, evanescent_zero=False):
+    g = oracle.Geometry(b.n_elem, b.n_samples[i], fs, C, PITCH, b.nz[i], z0, dz, b.bins[i],
+                        evanescent_zero=evanescent_zero)
+    return oracle.as_xcorr(g, rf_i, apod)
+
+
+def _compare(b, img, rn, i, orc, check_peak=False):
+    gi = b.unpack(img, i).cpu().numpy()
+    gr = b.unpack(rn, i).cpu().numpy()
+    e_img = rel_l2(gi, orc["image"])
+    e_rn = float(np.max(np.abs(gr - orc["rho_n"])))
+    assert e_img <= REL_L2_TOL, (i, e_img)
+    assert e_rn <= NCC_TOL, (i, e_rn)
+    if check_peak:
+        assert peak(gi) == peak(orc["image"]), i
+    return e_img, e_rn
+
+
+# uneven sample counts (primes, odd, even non-powers of 2) and depth ranges
+# that end in ragged row tiles
+UNEVEN = [(250, 9), (509, 40), (640, 23), (1000, 17), (333, 33), (32, 5)]
+
+
+def test_batch_uneven_tax():
+    ne, nb, fs = 32, 10, 20e6
+    frames = [(nt, nz) for nt, nz in UNEVEN[:-1]]
+    b = _batch(ne, frames, nb, fs=fs)
+    rfs = [synth.random_rf(ne, nt, seed=300 + i) for i, (nt, _) in enumerate(frames)]
+    img, rn = b.as_tax(b.pack_rf(rfs))
+    torch.cuda.synchronize()
+    b.sync()
+    apod = oracle.pattern(ne, 3, 2)
+    worst = [0.0, 0.0]
+    for i in range(len(frames)):
+        e = _compare(b, img, rn, i, _oracle_frame(b, i, rfs[i], apod, fs, 4e-3, 0.45e-3))
+        worst = [max(worst[0], e[0]), max(worst[1], e[1])]
+    print(f"\nbatch uneven: worst rel L2 image {worst[0]:.2e}, max |d rho_n| {worst[1]:.2e}")
+
+
+def test_batch_short_frames_use_every_bin_of_their_band():
+    """A frame whose band holds fewer than n_bins bins takes all of them; the
+    other frames take n_bins spread evenly (the workload's rule)."""
+    ne, fs = 16, 20e6
+    frames = [(64, 6), (1000, 5)]       # 64 samples: bins 4..22 of 1-7 MHz (19 bins)
+    b = _batch(ne, frames, 24, fs=fs, f_lo=1e6, f_hi=7e6)
+    assert list(b.bins[0]) == list(range(4, 23))
+    w = synth.Workload(name="t", n_elem=ne, pitch=PITCH, fs=fs, nt=1000, c=C, nz=5, z_first=4e-3, z_last=6e-3,
+                       f_lo=1e6, f_hi=7e6, n_bins=24, pattern_m=2)
+    assert list(b.bins[1]) == list(w.bins())
+    rfs = [synth.random_rf(ne, nt, seed=305 + i) for i, (nt, _) in enumerate(frames)]
+    img, rn = b.as_tax(b.pack_rf(rfs))
+    apod = oracle.pattern(ne, 3, 2)
+    for i in range(len(frames)):
+        _compare(b, img, rn, i, _oracle_frame(b, i, rfs[i], apod, fs, 4e-3, 0.45e-3))
+
+
+def test_batch_dax_explicit_bins_and_shortest_frame():
+    ne, fs = 16, 20e6
+    bins = [[3, 5, 7, 11], [9, 10, 40, 61], [2, 3, 4, 15]]
+    frames = [(64, 12, bins[0]), (130, 3, bins[1]), (32, 7, bins[2])]
+    b = _batch(ne, frames, 4, fs=fs, n_apod=2)
+    assert [list(x) for x in b.bins] == bins
+    rfs = [synth.random_rf(ne, nt, seed=310 + i) for i, (nt, _, _) in enumerate(frames)]
+    img, rn = b.as_tax(b.pack_rf(rfs))
+    apod = oracle.pattern(ne, 2, 2)
+    for i in range(len(frames)):
+        _compare(b, img, rn, i, _oracle_frame(b, i, rfs[i], apod, fs, 4e-3, 0.45e-3))
+
+
+def test_batch_evanescent_zero():
+    ne, fs = 32, 20e6
+    frames = [(300, 11), (517, 20)]
+    b = _batch(ne, frames, 8, fs=fs, f_lo=0.3e6, f_hi=4e6, evanescent_zero=True)
+    rfs = [synth.random_rf(ne, nt, seed=320 + i) for i, (nt, _) in enumerate(frames)]
+    img, rn = b.as_tax(b.pack_rf(rfs))
+    apod = oracle.pattern(ne, 3, 2)
+    for i in range(len(frames)):
+        _compare(b, img, rn, i, _oracle_frame(b, i, rfs[i], apod, fs, 4e-3, 0.45e-3, evanescent_zero=True))
+
+
+def test_batch_graph_replay_direct_launch_and_grid_agree():
+    """Graph replay, a re-capture on new buffers, direct launches and a
+    one-CTA persistent grid all give bit-identical maps (every work item sums
+    its bins in the same order)."""
+    ne = 32
+    frames = [(nt, nz) for nt, nz in UNEVEN]
+    b = _batch(ne, frames, 10)
+    rf = b.pack_rf([synth.random_rf(ne, nt, seed=330 + i) for i, (nt, _) in enumerate(frames)])
+    img1, rn1 = b.as_tax(rf)
+    img1, rn1 = img1.clone(), rn1.clone()
+    img2, rn2 = b.as_tax(rf)                 # replay
+    assert torch.equal(img1, img2) and torch.equal(rn1, rn2)
+    img3 = torch.empty_like(img1)
+    rn3 = torch.empty_like(rn1)
+    b.as_tax(rf, image=img3, rho_n=rn3)     # new buffers: captured again
+    assert torch.equal(img1, img3) and torch.equal(rn1, rn3)
+    b.configure(use_graph=False, persistent_ctas=1)
+    img4, rn4 = b.as_tax(rf)
+    assert torch.equal(img1, img4) and torch.equal(rn1, rn4)
+    n_items, grid, k = b.info()
+    rows = 8 * (32 // (ne // 8))        # rows per work item: 8 warps, 2 nx/16 lanes per row
+    assert grid == 1 and n_items == sum((nz + rows - 1) // rows for _, nz in frames) and k >= 16
+    b.sync()
+
+
+def test_batch_matches_the_plan_path_on_power_of_two_frames():
+    """For power-of-2 sample counts the plain plan (real FFT over time) and the
+    batch (direct DFT of the bins) compute the same maps."""
+    ne, nb, fs = 32, 10, 20e6
+    frames = [(256, 37), (512, 16)]
+    b = _batch(ne, frames, nb, fs=fs)
+    rfs = [synth.random_rf(ne, nt, seed=340 + i) for i, (nt, _) in enumerate(frames)]
+    img, rn = b.as_tax(b.pack_rf(rfs))
+    pam = _pam()
+    for i, (nt, nz) in enumerate(frames):
+        p = pam.Plan(n_elem=ne, pitch=PITCH, fs=fs, c=C, n_samples=nt, nz=nz, z0=4e-3, dz=0.45e-3,
+                     bins=b.bins[i], n_apod=3, pattern_m=2)
+        o = p.as_tax(torch.from_numpy(rfs[i]).cuda())
+        assert rel_l2(b.unpack(img, i).cpu().numpy(), o["image"][0].cpu().numpy()) <= 2e-6
+        assert float(torch.max(torch.abs(b.unpack(rn, i) - o["rho_n"][0]))) <= 2e-6
+
+
+def test_batch_workload3_sampled_rows():
+    """Frames of the uneven-batch workload at full size (128 elements, 300 bins,
+    nt in [1024, 8192], nz in [128, 512]) in the configuration the bench runs.
+    The oracle evaluates single depth rows (a one-row geometry at that depth):
+    the coherent energy E = image / rho_n^2 must match its Eq. 3 energy, and
+    rho_n along the row must match up to the frame's normalisation."""
+    ws = synth.batch_workload(6)
+    pick = [0, 2, 5]
+    frames = [(w.nt, w.nz) for w in ws]
+    b = _pam().Batch(n_elem=128, pitch=PITCH, fs=40e6, c=C, frames=frames, z0=5e-3, dz=synth.BATCH_DZ,
+                     n_bins=300, f_lo=0.5e6, f_hi=8e6, n_apod=3, pattern_m=16)
+    rfs = [synth.make_frame(w, i)[0] for i, w in enumerate(ws)]
+    img, rn = b.as_tax(b.pack_rf(rfs))
+    apod = oracle.pattern(128, 3, 16)
+    for i in pick:
+        assert list(b.bins[i]) == list(ws[i].bins())
+        gi = b.unpack(img, i).cpu().numpy().astype(np.float64)
+        gr = b.unpack(rn, i).cpu().numpy().astype(np.float64)
+        for j in (0, ws[i].nz // 2, ws[i].nz - 1):
+            g = oracle.Geometry(128, ws[i].nt, 40e6, C, PITCH, 1, 5e-3 + j * synth.BATCH_DZ, 1e-4, b.bins[i])
+            orc = oracle.as_xcorr(g, rfs[i], apod)
+            e_gpu = gi[j] / gr[j] ** 2
+            assert rel_l2(e_gpu, orc["image_as"][0]) <= 2e-5, (i, j)
+            ratio = gr[j] / gr[j].max()
+            assert np.max(np.abs(ratio - orc["rho_n"][0])) <= 2e-5, (i, j)
+
+
+def test_autotuned_batch_grid_keeps_results(tmp_path):
+    from paper_2412_02413_gb300 import autotune
+    ne = 32
+    frames = [(nt, nz) for nt, nz in UNEVEN]
+    b = _batch(ne, frames, 10)
+    rf = b.pack_rf([synth.random_rf(ne, nt, seed=350 + i) for i, (nt, _) in enumerate(frames)])
+    ref, _ = b.as_tax(rf)
+    ref = ref.clone()
+    t = autotune.Autotuner(str(tmp_path / "tune.json"))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    best = autotune.tune_batch_grid(t, b, rf, sms)
+    n_items, grid, _ = b.info()
+    assert grid == min(best, n_items)
+    img, _ = b.as_tax(rf)
+    assert torch.equal(ref, img)
+    assert t.lookup(autotune.make_key("batch_grid", ne, 1000, 40, len(frames))) == best
