@@ -39,73 +39,126 @@ constexpr int DFT_MAX_NT = 16384;
 // S[f][b][e] = sum_t rf[e][t] exp(-2 pi i k_b t / nt)   (Eq. 1, selected bins)
 // by direct summation with the exact index reduction m = k t mod nt into the
 // frame's twiddle table exp(-2 pi i m / nt) (built in FP64). One CTA per
-// (32 bins, frame): warp w owns bins 4w..4w+3 (twiddle reads are warp-uniform
-// broadcasts), lane l owns channels l + 32 c, c < CPL. 64-sample tiles of all
-// channels are staged transposed in shared memory (row stride 32 CPL + 1,
-// conflict-free both ways). The sum of each tile is formed on its own and
-// then added to the total, so the rounding error grows like 64 + nt/64 ulp
-// rather than nt ulp. One packed FMA (fma.rn.f32x2) updates Re and Im.
+// (32 bins, frame): warp w owns bins 4w..4w+3, lane l channels l + 32 c,
+// c < CPL. Per 64-sample tile the CTA stages the channels' samples (rows of
+// 64 + 4 floats) and the 32 bins' twiddles for those samples (rows of 64 + 4
+// float2, gathered from the table, which stays in L1/L2, with the index
+// stepped by k per sample), with cp.async into two buffers: tile i+1 is in
+// flight while tile i is summed. Two CTAs share an SM.
+// The inner loop then reads 4 samples of a channel and 4 twiddles of a bin as
+// 16-byte loads (twiddle reads are warp-uniform broadcasts) and updates Re
+// and Im with one packed FMA (fma.rn.f32x2). The sum of each tile is formed on
+// its own and then added to the total, so the rounding error grows like
+// 64 + nt/64 ulp rather than nt ulp.
+constexpr int XROW = DFT_T + 4;     // floats per staged channel row
+constexpr int WROW = DFT_T + 4;     // float2 per staged twiddle row
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+// 4- and 8-byte asynchronous copies global -> shared (cp.async); `valid` false
+// writes zeros without reading.
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
 template <int CPL>
-__global__ void __launch_bounds__(DFT_THREADS)
+__global__ void __launch_bounds__(DFT_THREADS, CPL >= 8 ? 1 : 2)
 time_dft_kernel(const float *__restrict__ rf, const DftFrame *__restrict__ frames, const int *__restrict__ bins,
                 int n_bins, int ne, const float2 *__restrict__ tw_all, float2 *__restrict__ S)
 {
-    constexpr int XS = 32 * CPL + 1;
     extern __shared__ __align__(16) float2 dsm[];
+    constexpr int WBUF = DFT_BINS * WROW;               // float2 per twiddle buffer
+    constexpr int XBUF = 32 * CPL * XROW;               // floats per sample buffer
     const int f = blockIdx.y;
     const DftFrame fr = frames[f];
     const int nt = fr.nt;
-    float2 *tw = dsm;                                       // [nt]
-    float *xs = reinterpret_cast<float *>(dsm + nt);        // [DFT_T][XS]
+    float2 *wt = dsm;                                                  // [2][DFT_BINS][WROW]
+    float *xs = reinterpret_cast<float *>(wt + 2 * WBUF);             // [2][32 CPL][XROW]
+    const float2 *tw = tw_all + fr.tw_off;                             // [nt]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int m = tid; m < nt; m += DFT_THREADS) tw[m] = tw_all[fr.tw_off + m];
-    const int b0 = blockIdx.x * DFT_BINS + warp * DFT_BPW;
-    int k[DFT_BPW], idx[DFT_BPW];
+    // twiddle staging role: bin bb of the CTA, samples s + 8 j of each tile
+    const int bb = tid >> 3, sg = tid & 7;
+    const int bglob = blockIdx.x * DFT_BINS + bb;
+    const int kb = bglob < fr.n_bins ? bins[(size_t)f * n_bins + bglob] : 0;
+    const int kstep8 = (int)((8LL * kb) % nt);
+    const float *x = rf + fr.rf_off;
+    // Copies of tile t0 into buffer `buf` (all threads; one commit group).
+    auto stage = [&](int t0, int buf) {
+        const int tn = min(DFT_T, nt - t0);
+        float *xb = xs + buf * XBUF;
+        for (int e = warp; e < 32 * CPL; e += DFT_WARPS) {
+            const bool erow = e < ne;
+            const float *row = x + (size_t)(erow ? e : 0) * nt + t0;
+            for (int t = lane; t < DFT_T; t += 32)
+                cp_async4(xb + e * XROW + t, row + (t < tn ? t : 0), erow && t < tn);
+        }
+        float2 *wb = wt + buf * WBUF + bb * WROW;
+        int idx = (int)(((long long)kb * (t0 + sg)) % nt);
 #pragma unroll
-    for (int i = 0; i < DFT_BPW; ++i) {
-        k[i] = b0 + i < fr.n_bins ? bins[(size_t)f * n_bins + b0 + i] : 0;
-        idx[i] = 0;
-    }
+        for (int j = 0; j < DFT_T / 8; ++j) {
+            cp_async8(wb + sg + 8 * j, tw + idx);
+            idx += kstep8;
+            if (idx >= nt) idx -= nt;
+        }
+        cp_async_commit();
+    };
     float2 tot[DFT_BPW][CPL];
 #pragma unroll
     for (int i = 0; i < DFT_BPW; ++i)
 #pragma unroll
         for (int c = 0; c < CPL; ++c) tot[i][c] = make_float2(0.f, 0.f);
-    const float *x = rf + fr.rf_off;
-    for (int t0 = 0; t0 < nt; t0 += DFT_T) {
-        const int tn = min(DFT_T, nt - t0);
-        __syncthreads();  // the previous tile is consumed (first pass: nothing to wait for)
-        for (int e = warp; e < 32 * CPL; e += DFT_WARPS) {
-            const float *row = x + (size_t)e * nt + t0;
-            for (int t = lane; t < DFT_T; t += 32) xs[t * XS + e] = (e < ne && t < tn) ? row[t] : 0.f;
-        }
-        __syncthreads();
+    const int ntiles = (nt + DFT_T - 1) / DFT_T;
+    stage(0, 0);
+    for (int it = 0; it < ntiles; ++it) {
+        const int buf = it & 1, t0 = it * DFT_T, tn = min(DFT_T, nt - t0);
+        if (it + 1 < ntiles) stage(t0 + DFT_T, buf ^ 1);
+        else cp_async_commit();                 // empty group keeps the wait count uniform
+        cp_async_wait1();                       // this thread's copies of tile `it` have landed
+        __syncthreads();                        // ... and everyone else's
+        const float *xb = xs + buf * XBUF;
+        const float2 *wb = wt + buf * WBUF;
         float2 part[DFT_BPW][CPL];
 #pragma unroll
         for (int i = 0; i < DFT_BPW; ++i)
 #pragma unroll
             for (int c = 0; c < CPL; ++c) part[i][c] = make_float2(0.f, 0.f);
-        for (int t = 0; t < tn; ++t) {
-            float2 xv[CPL];
+        // samples past tn are zero in xs, so whole groups of 4 are summed
+        for (int t = 0; t < tn; t += 4) {
+            float4 xv[CPL];
 #pragma unroll
-            for (int c = 0; c < CPL; ++c) {
-                const float v = xs[t * XS + lane + 32 * c];
-                xv[c] = make_float2(v, v);
-            }
+            for (int c = 0; c < CPL; ++c) xv[c] = *reinterpret_cast<const float4 *>(xb + (lane + 32 * c) * XROW + t);
 #pragma unroll
             for (int i = 0; i < DFT_BPW; ++i) {
-                const float2 w = tw[idx[i]];
+                const float4 *wp = reinterpret_cast<const float4 *>(wb + (warp * DFT_BPW + i) * WROW + t);
+                const float4 w01 = wp[0], w23 = wp[1];
+                const float2 w0 = make_float2(w01.x, w01.y), w1 = make_float2(w01.z, w01.w);
+                const float2 w2 = make_float2(w23.x, w23.y), w3 = make_float2(w23.z, w23.w);
 #pragma unroll
-                for (int c = 0; c < CPL; ++c) part[i][c] = __ffma2_rn(xv[c], w, part[i][c]);
-                idx[i] += k[i];
-                if (idx[i] >= nt) idx[i] -= nt;
+                for (int c = 0; c < CPL; ++c) {
+                    float2 a = part[i][c];
+                    a = __ffma2_rn(make_float2(xv[c].x, xv[c].x), w0, a);
+                    a = __ffma2_rn(make_float2(xv[c].y, xv[c].y), w1, a);
+                    a = __ffma2_rn(make_float2(xv[c].z, xv[c].z), w2, a);
+                    a = __ffma2_rn(make_float2(xv[c].w, xv[c].w), w3, a);
+                    part[i][c] = a;
+                }
             }
         }
 #pragma unroll
         for (int i = 0; i < DFT_BPW; ++i)
 #pragma unroll
             for (int c = 0; c < CPL; ++c) tot[i][c] = __fadd2_rn(tot[i][c], part[i][c]);
+        __syncthreads();                        // buffer `buf` is free for tile it + 2
     }
+    const int b0 = blockIdx.x * DFT_BINS + warp * DFT_BPW;
 #pragma unroll
     for (int i = 0; i < DFT_BPW; ++i) {
         if (b0 + i >= n_bins) continue;
@@ -118,7 +171,10 @@ time_dft_kernel(const float *__restrict__ rf, const DftFrame *__restrict__ frame
     }
 }
 
-size_t dft_smem(int nt, int cpl) { return (size_t)nt * sizeof(float2) + (size_t)DFT_T * (32 * cpl + 1) * 4; }
+size_t dft_smem(int, int cpl)
+{
+    return 2 * ((size_t)DFT_BINS * WROW * sizeof(float2) + (size_t)32 * cpl * XROW * sizeof(float));
+}
 
 template <int CPL>
 cudaError_t launch_dft_t(const float *rf, const DftFrame *frames, const int *bins, int n_bins, int ne, int F,
