@@ -282,6 +282,106 @@ pam_status pam_batch_info(pam_batch_t b, int *n_items, int *persistent_ctas, lon
 /* Frees the batch (NULL-safe). Waits for the device first. */
 void pam_batch_destroy(pam_batch_t b);
 
+/* ------------------------------------------------------------------------
+ * Learned form (AS-TAX with a predicted NCC weight). A 5-layer convolutional
+ * network predicts rho_TAX (Eq. 10, before the max normalisation) from the
+ * full-aperture AS energy (Eq. 3) and the energies of the four contiguous
+ * quarters of Omega, so that a frame needs one back-propagation instead of
+ * three apodized ones. Layers: conv3x3 (zero padding 1) 5 -> 32 -> 32 -> 32
+ * -> 32 -> 1, ReLU after the first four, head rho = eps + (1 - eps)
+ * sigmoid(z). Inputs: channel 0 = log10(E / max E + 1e-4) / 4, channels 1..4
+ * the same for each quarter's energy (max over the frame's pixels of E). The
+ * image is I = rho_n^2 E (Eq. 11 with the full-aperture energy, which equals
+ * sum_k |p~_1 + p~_2 + p~_3|^2 when the apodizations sum to one).
+ * Operands of every convolution (activations, weights, gradients) are BF16;
+ * every sum is FP32. Training minimises the mean squared error against the
+ * exact rho_TAX with Adam (Kingma and Ba 2015: beta1 0.9, beta2 0.999,
+ * eps 1e-8), all on the GPU.
+ *
+ * Error gate: per frame, the exact method runs on the tile of 16 depth rows
+ * (nx = 128; 2048 / nx rows otherwise) that holds the brightest pixel of the
+ * predicted image. If the relative L2 distance there between rho_pred^2 E and
+ * rho^2 E exceeds gate_tol, the frame is recomputed by the plain AS-TAX path,
+ * on the GPU, within the same call.
+ *
+ * Parameters are a flat FP32 vector: for each layer, w[out][in][3][3] then
+ * b[out] (pam_learn_n_params() = 29505 values).
+ *
+ * Feature tensors ("packed features") are BF16 [n_frames][nz+2][nx+2][8]:
+ * the five input channels and three zeros per pixel, with a one-pixel zero
+ * border (pam_learn_feature_bytes() bytes per frame).
+ * ------------------------------------------------------------------------ */
+typedef struct pam_learn_s *pam_learn_t;
+
+/* Number of network parameters (29505). */
+size_t pam_learn_n_params(void);
+
+/* Creates the learned form for the geometry `d` (as pam_plan_create; n_apod
+ * must be 3, no tensor-core form flag). d->max_frames is the batch size of
+ * every call (pam_learn_tax runs larger calls in batches). Parameters start at
+ * zero: set them with pam_learn_set_params. Errors: PAM_ERR_INVALID_ARG,
+ * PAM_ERR_UNSUPPORTED, PAM_ERR_OOM, PAM_ERR_CUDA; *out is NULL on failure. */
+pam_status pam_learn_create(const pam_plan_desc *d, pam_learn_t *out);
+
+/* Frees everything (NULL-safe); waits for the device first. */
+void pam_learn_destroy(pam_learn_t l);
+
+/* Copies n = pam_learn_n_params() host floats into the network and resets the
+ * Adam state. Blocks. PAM_ERR_NUMERIC for a non-finite value. */
+pam_status pam_learn_set_params(pam_learn_t l, const float *params, size_t n);
+
+/* Copies the current parameters to host memory. Blocks. */
+pam_status pam_learn_get_params(pam_learn_t l, float *params, size_t n);
+
+/* gate_tol: relative L2 bound of the gate (default 0.05; < 0 sends every
+ * frame through the exact path, +inf accepts every frame). use_tensor_cores: 1
+ * runs the 32 -> 32 layers' forward on tcgen05 (nx == 128 only, else
+ * PAM_ERR_UNSUPPORTED), 0 on CUDA cores (default). */
+pam_status pam_learn_configure(pam_learn_t l, float gate_tol, int use_tensor_cores);
+
+/* Bytes of one frame of packed features. */
+size_t pam_learn_feature_bytes(pam_learn_t l);
+
+/* A training example of each frame, made by the method itself:
+ *   rf        device float32 [n_frames][n_elem][n_samples], n_frames <= max_frames
+ *   features  device packed features (written in full, border included)
+ *   target    device [n_frames][nz][nx] exact rho_TAX (Eq. 4, 10, clamped
+ *             pairs, before normalisation), or NULL
+ *   energy    device [n_frames][nz][nx] full-aperture energy E, or NULL */
+pam_status pam_learn_example(pam_learn_t l, const float *rf, int n_frames, void *features, float *target,
+                             float *energy, void *stream);
+
+/* Network output rho (in [eps, 1)) for packed features: device [n_frames][nz][nx]. */
+pam_status pam_learn_forward(pam_learn_t l, const void *features, int n_frames, float *rho, void *stream);
+
+/* Mean squared error against target ([n_frames][nz][nx]) and its gradient
+ * with respect to every parameter, without an update: grads device
+ * [pam_learn_n_params()] or NULL, loss device [1] or NULL. */
+pam_status pam_learn_grads(pam_learn_t l, const void *features, const float *target, int n_frames, float *grads,
+                           float *loss, void *stream);
+
+/* One Adam step (learning rate lr) on the batch; loss (before the step) to
+ * device [1] or NULL. */
+pam_status pam_learn_train_step(pam_learn_t l, const void *features, const float *target, int n_frames, float lr,
+                                float *loss, void *stream);
+
+/* Learned AS-TAX with the error gate:
+ *   rf         device float32 [n_frames][n_elem][n_samples]
+ *   image      device [n_frames][nz][nx]: rho_n^2 E (gate passed) or the
+ *              plain AS-TAX image (gate missed)
+ *   rho_n      device [n_frames][nz][nx] or NULL
+ *   gate_err   device [n_frames] relative L2 distance on the gate tile, or NULL
+ *   gate_pass  device int [n_frames]: 1 if the network's map was used, or NULL */
+pam_status pam_learn_tax(pam_learn_t l, const float *rf, int n_frames, float *image, float *rho_n, float *gate_err,
+                         int *gate_pass, void *stream);
+
+/* As pam_sync, for the learned form's work on `stream`. */
+pam_status pam_learn_sync(pam_learn_t l, void *stream);
+
+/* Kernels launched since the last read (then cleared), the batch size and the
+ * Adam steps taken. Any pointer may be NULL. */
+pam_status pam_learn_info(pam_learn_t l, long long *kernel_launches, int *max_frames, long long *adam_steps);
+
 /* Static description of a status code. */
 const char *pam_status_string(pam_status s);
 

@@ -1,0 +1,293 @@
+// pam_conv_tc.cu -- tensor-core (tcgen05) forward of a 32 -> 32 channel 3x3
+// convolution with bias and ReLU, for rows of nx = 128 pixels: the hidden
+// layers of the learned NCC-weight network.
+//
+// One output row is a GEMM with M = 128 pixels, N = 32 output channels and
+// K = 9 taps x 32 input channels:
+//   y[j][o] = b[o] + sum_{u,v,c} x[i+u-1][j+v-1][c] w[o][c][u][v].
+// Activations are stored chunked and padded, [C/8][nz+2][nx+2][8] BF16 per
+// frame, so one padded input row of one chunk of 8 channels is 130 pixels x
+// 16 bytes, contiguous. Copied as it is into shared memory, 8 consecutive
+// pixels of it form one 8-row x 16-byte core matrix of the canonical K-major
+// layout (no swizzle): the A operand of tap (u, v) for channel chunks (c, c+1)
+// is the staged row i+u-1 starting at pixel v, i.e. a descriptor whose start
+// address moves by 16 bytes per pixel, with SBO = 128 bytes (next 8 pixels)
+// and LBO = 2080 bytes (next chunk of channels). No im2col is materialised.
+// The B operand (weights) is resident: [tap][chunk][out channel][8] BF16, 18 KB.
+// Each row accumulates 18 MMAs (M = 128, N = 32, K = 16) into one of two
+// tensor-memory accumulator sets.
+//
+// One CTA per (16-row strip, frame), 6 warps:
+//   warp 0: bulk copies of the strip's 18 input rows through a ring of 6 slots;
+//   warp 1: the MMA chain of each output row (one elected lane issues);
+//   warps 2-5: the epilogue, each reading its quarter of the 128 TMEM lanes
+//     (pixels), adding the bias, ReLU, and storing BF16 to the output tensor.
+// All waits are bounded; on expiry the CTA sets the status word and drains.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pam_internal.h"
+
+namespace pam {
+namespace {
+
+constexpr int W = 128, WP = W + 2;
+constexpr int ROWS = 16;                       // output rows per CTA
+constexpr int NSLOT = 6;                       // staged input rows
+constexpr int CH_BYTES = WP * 16;              // one padded row of one chunk: 2080 B
+constexpr int ROW_BYTES = 4 * CH_BYTES;        // 8320 B
+constexpr int WT_BYTES = 9 * 4 * 32 * 16;      // 18432 B
+constexpr int THREADS = 192;
+constexpr size_t SMEM = (size_t)WT_BYTES + (size_t)NSLOT * ROW_BYTES + 256;
+
+__device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t *b, unsigned n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity), "r"(10000u)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *b)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor: canonical K-major, no swizzle, version 1.
+__device__ __forceinline__ uint64_t sdesc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// kind::f16, FP32 accumulate, A = B = BF16, both K-major, N = 32, M = 128.
+constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_elect(unsigned d, uint64_t a, uint64_t b, unsigned acc)
+{
+    asm volatile(
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void commit_elect(uint64_t *b)
+{
+    asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+                 " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(su32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned pack2(float a, float b)
+{
+    unsigned r;
+    asm("cvt.rn.bf16x2.f32 %0, %2, %1;\n" : "=r"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__global__ void __launch_bounds__(THREADS)
+conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const float *__restrict__ bias,
+               uint4 *__restrict__ out, int H, int *__restrict__ status)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t *sW = sm;                                  // [9][4][32][8] BF16
+    uint8_t *sRow = sm + WT_BYTES;                     // [NSLOT][4][130][8] BF16
+    uint64_t *full = reinterpret_cast<uint64_t *>(sRow + NSLOT * ROW_BYTES);   // [NSLOT]
+    uint64_t *sfree = full + NSLOT;                    // [NSLOT]
+    uint64_t *afull = sfree + NSLOT;                   // [2]
+    uint64_t *aempty = afull + 2;                      // [2]
+    uint64_t *wbar = aempty + 2;                       // [1]
+    uint64_t *dbar = wbar + 1;                         // [1] drain
+    unsigned *tslot = reinterpret_cast<unsigned *>(dbar + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int strip = blockIdx.x, f = blockIdx.y;
+    const int HP = H + 2;
+    const int r_first = strip * ROWS;
+    const int nr = min(ROWS, H - r_first);   // output rows of this CTA
+    const int nin = nr + 2;                  // input rows (padded rows r_first .. r_first + nr + 1)
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)),
+                     "r"(64u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 32) {
+        for (int s = 0; s < NSLOT; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&sfree[s], 1);
+        }
+        for (int t = 0; t < 2; ++t) {
+            bar_init(&afull[t], 1);
+            bar_init(&aempty[t], 4);
+        }
+        bar_init(wbar, 1);
+        bar_init(dbar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = *tslot;
+
+    auto wait = [&](uint64_t *b, unsigned parity) -> bool {
+        if (bar_try(b, parity)) return true;
+        const long long t0 = clock64();
+        while (!bar_try(b, parity)) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > (1ll << 31)) {
+                *abort_flag = 1;
+                atomicOr(status, 1);
+                return false;
+            }
+        }
+        return true;
+    };
+
+    if (warp == 0) {
+        // ---------------- producer: weights, then the input rows ----------------
+        int issued = 0;
+        bool ok = true;
+        if (lane == 0) {
+            bar_expect(wbar, WT_BYTES);
+            bulk_load(sW, wt, WT_BYTES, wbar);
+            for (int k = 0; k < nin && ok; ++k) {
+                const int s = k % NSLOT;
+                if (k >= NSLOT) ok = wait(&sfree[s], (unsigned)(k / NSLOT - 1) & 1u);
+                if (!ok) break;
+                bar_expect(&full[s], ROW_BYTES);
+                const int prow = r_first + k;
+                for (int c = 0; c < 4; ++c)
+                    bulk_load(sRow + s * ROW_BYTES + c * CH_BYTES, in + (((size_t)f * 4 + c) * HP + prow) * WP,
+                              CH_BYTES, &full[s]);
+                issued = k + 1;
+            }
+            if (!ok) {
+                // let the copies in flight land before the CTA exits
+                wait(wbar, 0);
+                for (int k = issued - NSLOT < 0 ? 0 : issued - NSLOT; k < issued; ++k)
+                    wait(&full[k % NSLOT], (unsigned)(k / NSLOT) & 1u);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issue ----------------
+        bool ok = __all_sync(0xffffffffu, wait(wbar, 0));
+        bool any = false;
+        const unsigned wbase = su32(sW), rbase = su32(sRow);
+        for (int r = 0; r < nr && ok; ++r) {
+            // input rows r, r+1, r+2 (the first two were waited for by earlier rows)
+            for (int k = (r == 0 ? 0 : r + 2); k <= r + 2 && ok; ++k)
+                ok = __all_sync(0xffffffffu, wait(&full[k % NSLOT], (unsigned)(k / NSLOT) & 1u));
+            const int t = r & 1;
+            if (ok && r >= 2) ok = __all_sync(0xffffffffu, wait(&aempty[t], (unsigned)((r >> 1) - 1) & 1u));
+            if (!ok) break;
+            fence_after();
+            const unsigned d = tmem + (unsigned)(t * 32);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int u = tap / 3, v = tap % 3;
+                const unsigned arow = rbase + (unsigned)(((r + u) % NSLOT) * ROW_BYTES + v * 16);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint64_t a = sdesc(arow + (unsigned)(2 * h * CH_BYTES), CH_BYTES, 128);
+                    const uint64_t b = sdesc(wbase + (unsigned)(tap * 2048 + h * 1024), 512, 128);
+                    mma_elect(d, a, b, (tap | h) ? 1u : 0u);
+                }
+            }
+            any = true;
+            commit_elect(&afull[t]);
+            commit_elect(&sfree[r % NSLOT]);
+        }
+        if (!ok && any && lane == 0) {
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             su32(dbar))
+                         : "memory");
+            wait(dbar, 0);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: TMEM -> bias + ReLU -> BF16 ----------------
+        const int quarter = warp & 3;
+        const int j = 32 * quarter + lane;   // pixel = TMEM lane
+        float b[32];
+#pragma unroll
+        for (int o = 0; o < 32; ++o) b[o] = bias[o];
+        for (int r = 0; r < nr; ++r) {
+            const int t = r & 1;
+            if (!__all_sync(0xffffffffu, wait(&afull[t], (unsigned)(r >> 1) & 1u))) break;
+            fence_after();
+            unsigned acc[32];
+            tmem_ld32(tmem + (unsigned)(t * 32) + ((unsigned)(32 * quarter) << 16), acc);
+            fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(&aempty[t]);
+            const int prow = r_first + r + 1;
+            uint4 *dst = out + (((size_t)f * 4) * HP + prow) * WP + (j + 1);
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch) {
+                float y[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) y[k] = fmaxf(__uint_as_float(acc[ch * 8 + k]) + b[ch * 8 + k], 0.0f);
+                dst[(size_t)ch * HP * WP] =
+                    make_uint4(pack2(y[0], y[1]), pack2(y[2], y[3]), pack2(y[4], y[5]), pack2(y[6], y[7]));
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(64u) : "memory");
+}
+
+}  // namespace
+
+cudaError_t prepare_conv_tc()
+{
+    return cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+}
+
+cudaError_t launch_conv_tc(const uint4 *in, const uint4 *wt, const float *bias, uint4 *out, int F, int H,
+                           int *status, cudaStream_t st)
+{
+    dim3 grid((H + ROWS - 1) / ROWS, F);
+    conv_tc_kernel<<<grid, THREADS, SMEM, st>>>(in, wt, bias, out, H, status);
+    return cudaGetLastError();
+}
+
+}  // namespace pam

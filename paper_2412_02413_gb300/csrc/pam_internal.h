@@ -135,8 +135,14 @@ cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_s
 int epilogue_kernels(int napq, int n_split);   // kernels launch_epilogue launches
 // Batch (pam_batch.cu): the persistent propagate-and-correlate kernel over
 // (frame, row tile) items and the per-frame normalisation.
+// n_items_dev (optional): a device int that caps n_items when the kernel starts.
 cudaError_t launch_prop_batch(int nx, int napq, int grid, const BatchFrame *frames, const int2 *items, int n_items,
-                              int *counter, const EpiOut &out, cudaStream_t st);
+                              int *counter, const EpiOut &out, cudaStream_t st, const int *n_items_dev = nullptr);
+// Full-aperture energy split by bins: the fused kernel (one aperture, whatever
+// Q holds) over n_bands contiguous chunks of Omega, chunk b = bins
+// [floor(n_bins b / n_bands), floor(n_bins (b+1) / n_bands)), each chunk's
+// per-pixel sum written to bands[f][b][nz][nx] (no reduction).
+cudaError_t launch_prop_bands(const pam_plan_s &p, int n_frames, int n_bands, float *bands, cudaStream_t st);
 cudaError_t launch_normalize_batch(int n_frames, int max_npix, const BatchFrame *frames, const EpiOut &out,
                                    cudaStream_t st);
 bool prop_uses_cluster(int n_split);

@@ -604,8 +604,9 @@ epi_normalize_kernel(const float4 *__restrict__ rho_tmp, const float4 *__restric
 template <int NAP, int NX>
 __global__ void __launch_bounds__(PROP_THREADS, 2)
 prop_batch_kernel(const BatchFrame *__restrict__ frames, const int2 *__restrict__ items, int n_items,
-                  int *__restrict__ counter, EpiOut out)
+                  const int *__restrict__ n_items_dev, int *__restrict__ counter, EpiOut out)
 {
+    if (n_items_dev) n_items = min(n_items, *n_items_dev);
     using S = Shape<NX>;
     constexpr int L2 = S::L2, LPR = S::LPR, RPW = S::RPW, RPC = S::RPC, KPL = S::KPL;
     constexpr int NACC = Acc<NAP>::N;
@@ -672,7 +673,7 @@ epi_normalize_batch_kernel(const BatchFrame *__restrict__ frames, const float *_
 
 template <int NAP, int NX, bool FIELDS, bool CLUSTER>
 cudaError_t launch_prop_t(const pam_plan_s &p, int n_frames, int n_split, float *fields, const EpiOut &out,
-                          cudaStream_t st)
+                          cudaStream_t st, float *part = nullptr)
 {
     using S = Shape<NX>;
     cudaLaunchConfig_t cfg = {};
@@ -691,7 +692,7 @@ cudaError_t launch_prop_t(const pam_plan_s &p, int n_frames, int n_split, float 
     }
     cudaError_t e = cudaLaunchKernelEx(&cfg, prop_corr_kernel<NAP, NX, FIELDS, CLUSTER>, p.w.Q, p.t.phase,
                                        p.t.bin_evan, p.n_bins, p.nz, (float)p.d.z0_m, (float)p.d.dz_m, n_split,
-                                       p.w.part, reinterpret_cast<float2 *>(fields), out);
+                                       part ? part : p.w.part, reinterpret_cast<float2 *>(fields), out);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -748,15 +749,23 @@ cudaError_t prepare_nx()
 
 template <int NX>
 cudaError_t launch_batch_nx(int napq, int grid, const BatchFrame *frames, const int2 *items, int n_items,
-                            int *counter, const EpiOut &out, cudaStream_t st)
+                            const int *n_items_dev, int *counter, const EpiOut &out, cudaStream_t st)
 {
     if (napq == 2)
         prop_batch_kernel<2, NX><<<grid, PROP_THREADS, prop_smem_bytes<2, NX>(), st>>>(frames, items, n_items,
-                                                                                      counter, out);
+                                                                                      n_items_dev, counter, out);
     else
         prop_batch_kernel<3, NX><<<grid, PROP_THREADS, prop_smem_bytes<3, NX>(), st>>>(frames, items, n_items,
-                                                                                      counter, out);
+                                                                                      n_items_dev, counter, out);
     return cudaGetLastError();
+}
+
+template <int NX>
+cudaError_t launch_bands_nx(const pam_plan_s &p, int n_frames, int n_bands, float *bands, cudaStream_t st)
+{
+    EpiOut out;
+    out.status = p.w.status;
+    return launch_prop_t<1, NX, false, false>(p, n_frames, n_bands, nullptr, out, st, bands);
 }
 
 }  // namespace
@@ -826,14 +835,26 @@ cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_s
 }
 
 cudaError_t launch_prop_batch(int nx, int napq, int grid, const BatchFrame *frames, const int2 *items, int n_items,
-                              int *counter, const EpiOut &out, cudaStream_t st)
+                              int *counter, const EpiOut &out, cudaStream_t st, const int *n_items_dev)
 {
     if (napq != 2 && napq != 3) return cudaErrorInvalidValue;
     switch (nx) {
-    case 16: return launch_batch_nx<16>(napq, grid, frames, items, n_items, counter, out, st);
-    case 32: return launch_batch_nx<32>(napq, grid, frames, items, n_items, counter, out, st);
-    case 64: return launch_batch_nx<64>(napq, grid, frames, items, n_items, counter, out, st);
-    case 128: return launch_batch_nx<128>(napq, grid, frames, items, n_items, counter, out, st);
+    case 16: return launch_batch_nx<16>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st);
+    case 32: return launch_batch_nx<32>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st);
+    case 64: return launch_batch_nx<64>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st);
+    case 128: return launch_batch_nx<128>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_prop_bands(const pam_plan_s &p, int n_frames, int n_bands, float *bands, cudaStream_t st)
+{
+    if (n_bands < 1 || n_bands > p.n_bins) return cudaErrorInvalidValue;
+    switch (p.nx) {
+    case 16: return launch_bands_nx<16>(p, n_frames, n_bands, bands, st);
+    case 32: return launch_bands_nx<32>(p, n_frames, n_bands, bands, st);
+    case 64: return launch_bands_nx<64>(p, n_frames, n_bands, bands, st);
+    case 128: return launch_bands_nx<128>(p, n_frames, n_bands, bands, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -81,6 +81,21 @@ _SIGS = {
     "pam_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "pam_batch_destroy": (None, [_VP]),
+    "pam_learn_n_params": (ctypes.c_size_t, []),
+    "pam_learn_create": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(_VP)]),
+    "pam_learn_destroy": (None, [_VP]),
+    "pam_learn_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+    "pam_learn_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
+    "pam_learn_configure": (ctypes.c_int, [_VP, ctypes.c_float, ctypes.c_int]),
+    "pam_learn_feature_bytes": (ctypes.c_size_t, [_VP]),
+    "pam_learn_example": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
+    "pam_learn_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
+    "pam_learn_grads": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
+    "pam_learn_train_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_float, _VP, _VP]),
+    "pam_learn_tax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
+    "pam_learn_sync": (ctypes.c_int, [_VP, _VP]),
+    "pam_learn_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_longlong)]),
     "pam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pam_last_error": (ctypes.c_char_p, []),
 }
@@ -130,6 +145,32 @@ def _dptr(t) -> Optional[int]:
     return None if t is None else int(t.data_ptr())
 
 
+def _make_desc(n_elem, pitch, fs, c, n_samples, nz, z0, dz, bins=None, f_lo=0.0, f_hi=0.0, n_apod=3, apod=None,
+               pattern_m=16, eps=1e-3, evanescent_zero=False, max_frames=1, nx=0, form="fp32"):
+    """A filled ``pam_plan_desc`` and the host arrays it points to (keep them alive)."""
+    L = load()
+    d = PlanDesc()
+    L.pam_plan_desc_init(ctypes.byref(d))
+    d.n_elem, d.pitch_m, d.fs_hz, d.c_mps = int(n_elem), float(pitch), float(fs), float(c)
+    d.n_samples, d.nx, d.nz = int(n_samples), int(nx), int(nz)
+    d.z0_m, d.dz_m, d.f_lo_hz, d.f_hi_hz = float(z0), float(dz), float(f_lo), float(f_hi)
+    bins_keep = apod_keep = None
+    if bins is not None:
+        bins_keep = np.ascontiguousarray(np.asarray(bins, dtype=np.int32))
+        d.bins = bins_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        d.n_bins = int(bins_keep.size)
+    d.n_apod = int(n_apod)
+    if apod is not None:
+        apod_keep = np.ascontiguousarray(np.asarray(apod, dtype=np.float32))
+        d.apod = apod_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    d.pattern_m, d.eps = int(pattern_m), float(eps)
+    if form not in FORMS:
+        raise ValueError(f"form must be one of {sorted(FORMS)}")
+    d.flags = (PAM_EVANESCENT_ZERO if evanescent_zero else 0) | FORMS[form]
+    d.max_frames = int(max_frames)
+    return d, bins_keep, apod_keep
+
+
 class Plan:
     """An AS / AS-DAX / AS-TAX plan on the current CUDA device.
 
@@ -143,26 +184,9 @@ class Plan:
                  evanescent_zero: bool = False, max_frames: int = 1, nx: int = 0, form: str = "fp32"):
         _require_cuda()
         L = load()
-        d = PlanDesc()
-        L.pam_plan_desc_init(ctypes.byref(d))
-        d.n_elem, d.pitch_m, d.fs_hz, d.c_mps = int(n_elem), float(pitch), float(fs), float(c)
-        d.n_samples, d.nx, d.nz = int(n_samples), int(nx), int(nz)
-        d.z0_m, d.dz_m, d.f_lo_hz, d.f_hi_hz = float(z0), float(dz), float(f_lo), float(f_hi)
-        self._bins_keep = None
-        self._apod_keep = None
-        if bins is not None:
-            self._bins_keep = np.ascontiguousarray(np.asarray(bins, dtype=np.int32))
-            d.bins = self._bins_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
-            d.n_bins = int(self._bins_keep.size)
-        d.n_apod = int(n_apod)
-        if apod is not None:
-            self._apod_keep = np.ascontiguousarray(np.asarray(apod, dtype=np.float32))
-            d.apod = self._apod_keep.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
-        d.pattern_m, d.eps = int(pattern_m), float(eps)
-        if form not in FORMS:
-            raise ValueError(f"form must be one of {sorted(FORMS)}")
-        d.flags = (PAM_EVANESCENT_ZERO if evanescent_zero else 0) | FORMS[form]
-        d.max_frames = int(max_frames)
+        d, self._bins_keep, self._apod_keep = _make_desc(
+            n_elem, pitch, fs, c, n_samples, nz, z0, dz, bins, f_lo, f_hi, n_apod, apod, pattern_m, eps,
+            evanescent_zero, max_frames, nx, form)
         h = _VP()
         _check(L.pam_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -414,6 +438,156 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Learned:
+    """Learned AS-TAX (``pam_learn_*``): a 5-layer BF16 network predicts the
+    TAX weight from band energies of the full-aperture AS map, with a per-frame
+    error gate and the plain method as fallback. Training runs on the GPU in
+    the library's kernels. ``max_frames`` is the batch size of every call."""
+
+    def __init__(self, n_elem: int, pitch: float, fs: float, c: float, n_samples: int, nz: int,
+                 z0: float, dz: float, bins: Optional[Sequence[int]] = None, f_lo: float = 0.0,
+                 f_hi: float = 0.0, pattern_m: int = 16, eps: float = 1e-3, max_frames: int = 1, nx: int = 0,
+                 apod=None):
+        _require_cuda()
+        L = load()
+        d, self._bins_keep, self._apod_keep = _make_desc(
+            n_elem, pitch, fs, c, n_samples, nz, z0, dz, bins, f_lo, f_hi, 3, apod, pattern_m, eps, False,
+            max_frames, nx)
+        h = _VP()
+        _check(L.pam_learn_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.n_elem, self.n_samples, self.nz = int(n_elem), int(n_samples), int(nz)
+        self.nx = self.n_elem if not nx else int(nx)
+        self.max_frames = int(max_frames)
+        self.n_params = int(L.pam_learn_n_params())
+        self.feature_bytes = int(L.pam_learn_feature_bytes(h))
+
+    @classmethod
+    def from_workload(cls, w, max_frames: int = 1, **kw) -> "Learned":
+        return cls(n_elem=w.n_elem, pitch=w.pitch, fs=w.fs, c=w.c, n_samples=w.nt, nz=w.nz, z0=w.z0, dz=w.dz,
+                   bins=w.bins(), pattern_m=w.pattern_m, max_frames=max_frames, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pam_learn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # parameters: flat float32, per layer w[out][in][3][3] then b[out]
+    def set_params(self, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+        _check(load().pam_learn_set_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().pam_learn_get_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
+        return p
+
+    def configure(self, gate_tol: float = 0.05, tensor_cores: bool = False):
+        _check(load().pam_learn_configure(self._h, float(gate_tol), int(bool(tensor_cores))))
+
+    def empty_features(self, n: int):
+        """Uninitialised packed-feature tensor of n frames (uint8 view of BF16 [n][nz+2][nx+2][8])."""
+        torch = _require_cuda()
+        return torch.empty((n, self.feature_bytes), dtype=torch.uint8, device="cuda")
+
+    def _rf(self, rf):
+        torch = _require_cuda()
+        if not isinstance(rf, torch.Tensor) or not rf.is_cuda or rf.dtype != torch.float32:
+            raise TypeError("rf must be a float32 CUDA tensor")
+        if rf.dim() == 2:
+            rf = rf.unsqueeze(0)
+        if tuple(rf.shape[1:]) != (self.n_elem, self.n_samples):
+            raise ValueError(f"rf must be [F][{self.n_elem}][{self.n_samples}], got {tuple(rf.shape)}")
+        return rf.contiguous()
+
+    def _maps(self, n):
+        torch = _require_cuda()
+        return torch.empty((n, self.nz, self.nx), dtype=torch.float32, device="cuda")
+
+    def example(self, rf, features=None, target=True, energy=False, stream=None):
+        """Packed features and, optionally, the exact rho_TAX and energy E of each frame."""
+        rf = self._rf(rf)
+        n = rf.shape[0]
+        feats = self.empty_features(n) if features is None else features
+        tgt = self._maps(n) if target is True else (target if target is not False else None)
+        en = self._maps(n) if energy is True else (energy if energy is not False else None)
+        _check(load().pam_learn_example(self._h, _dptr(rf), n, _dptr(feats), _dptr(tgt), _dptr(en),
+                                        _stream_ptr(stream)))
+        return feats, tgt, en
+
+    def forward(self, features, n: Optional[int] = None, out=None, stream=None):
+        n = features.shape[0] if n is None else int(n)
+        rho = self._maps(n) if out is None else out
+        _check(load().pam_learn_forward(self._h, _dptr(features), n, _dptr(rho), _stream_ptr(stream)))
+        return rho
+
+    def grads(self, features, target, n: Optional[int] = None, stream=None):
+        torch = _require_cuda()
+        n = features.shape[0] if n is None else int(n)
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        loss = torch.empty(4, dtype=torch.float32, device="cuda")
+        _check(load().pam_learn_grads(self._h, _dptr(features), _dptr(target), n, _dptr(g), _dptr(loss),
+                                      _stream_ptr(stream)))
+        return g, loss[:1]
+
+    def train_step(self, features, target, lr: float, n: Optional[int] = None, loss=None, stream=None):
+        n = features.shape[0] if n is None else int(n)
+        _check(load().pam_learn_train_step(self._h, _dptr(features), _dptr(target), n, float(lr), _dptr(loss),
+                                           _stream_ptr(stream)))
+        return loss
+
+    def as_tax(self, rf, image=None, rho_n=None, want_rho_n: bool = True, stream=None):
+        """Learned AS-TAX: dict of image, rho_n, gate_err [F] and gate_pass [F] (int32)."""
+        torch = _require_cuda()
+        rf = self._rf(rf)
+        n = rf.shape[0]
+        image = self._maps(n) if image is None else image
+        if rho_n is None and want_rho_n:
+            rho_n = self._maps(n)
+        gerr = torch.empty(max(n, 4), dtype=torch.float32, device="cuda")
+        gpass = torch.empty(max(n, 4), dtype=torch.int32, device="cuda")
+        _check(load().pam_learn_tax(self._h, _dptr(rf), n, _dptr(image), _dptr(rho_n), _dptr(gerr), _dptr(gpass),
+                                    _stream_ptr(stream)))
+        return {"image": image, "rho_n": rho_n, "gate_err": gerr[:n], "gate_pass": gpass[:n]}
+
+    def sync(self, stream=None):
+        _check(load().pam_learn_sync(self._h, _stream_ptr(stream)))
+
+    def info(self):
+        k = ctypes.c_longlong()
+        mf = ctypes.c_int()
+        t = ctypes.c_longlong()
+        _check(load().pam_learn_info(self._h, ctypes.byref(k), ctypes.byref(mf), ctypes.byref(t)))
+        return {"kernel_launches": k.value, "max_frames": mf.value, "adam_steps": t.value}
+
+
+def unpack_features(features, nz: int, nx: int):
+    """Packed features (uint8 tensor or array) -> float32 numpy [n][5][nz][nx]."""
+    a = features.detach().cpu().numpy() if hasattr(features, "detach") else np.asarray(features)
+    u16 = a.view(np.uint16).reshape(a.shape[0], nz + 2, nx + 2, 8)
+    f32 = (u16.astype(np.uint32) << 16).view(np.float32)
+    return np.ascontiguousarray(f32[:, 1:nz + 1, 1:nx + 1, :5].transpose(0, 3, 1, 2))
+
+
+def pack_features(x):
+    """float numpy [n][5][nz][nx] -> packed BF16 features as uint8 numpy [n][bytes] (round to nearest even)."""
+    x = np.asarray(x, dtype=np.float32)
+    n, c, nz, nx = x.shape
+    if c != 5:
+        raise ValueError("features have 5 channels")
+    bits = x.view(np.uint32).astype(np.uint64)
+    rounded = ((bits + 0x7FFF + ((bits >> 16) & 1)) >> 16).astype(np.uint16)
+    out = np.zeros((n, nz + 2, nx + 2, 8), dtype=np.uint16)
+    out[:, 1:nz + 1, 1:nx + 1, :5] = rounded.transpose(0, 2, 3, 1)
+    return out.reshape(n, -1).view(np.uint8)
 
 
 def status_string(s: int) -> str:
