@@ -336,6 +336,73 @@ def run_batch(args, dev, stream):
     return out
 
 
+def run_learned(args, w, pool, stream, dev):
+    """Learned AS-TAX (trained checkpoint, tensor-core network, error gate) on
+    args.learned_batch frames per call, against the plain FP32 path on the
+    same batch; accuracy of the learned image against the plain one on the
+    pool's distinct frames."""
+    import numpy as np
+    import torch
+    from paper_2412_02413_gb300 import learn, pam
+    if not os.path.exists(learn.CHECKPOINT):
+        return {"unavailable": "no trained checkpoint (python -m paper_2412_02413_gb300.learn)"}
+    params, meta = learn.load_checkpoint()
+    B = args.learned_batch
+    P = pool.shape[0]
+    rf = pool[torch.arange(B, device=dev) % P].contiguous()
+    L = pam.Learned.from_workload(w, max_frames=B)
+    L.set_params(params)
+    L.configure(gate_tol=args.gate_tol, tensor_cores=True)
+    plan = pam.Plan.from_workload(w, max_frames=B)
+    img = torch.empty(B, w.nz, w.nx, device=dev)
+    rn = torch.empty(B, w.nz, w.nx, device=dev)
+    outs = {"image": torch.empty(B, w.nz, w.nx, device=dev), "rho_n": torch.empty(B, w.nz, w.nx, device=dev),
+            "image_as": torch.empty(B, w.nz, w.nx, device=dev)}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.learned_calls):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.learned_calls
+
+    L.info()
+    ms_l = timed(lambda: L.as_tax(rf, image=img, rho_n=rn, stream=stream))
+    kernels = L.info()["kernel_launches"] // (args.learned_calls + 2)
+    ms_p = timed(lambda: plan.as_tax(rf, outs=outs, image_as=True, stream=stream))
+    res = L.as_tax(rf, image=img, rho_n=rn, stream=stream)
+    plan.as_tax(rf, outs=outs, image_as=True, stream=stream)
+    torch.cuda.synchronize()
+    n = min(B, P)
+    pix = w.pitch * w.dz * 1e6
+    rows = []
+    for f in range(n):
+        il = img[f].double().cpu().numpy()
+        it = outs["image"][f].double().cpu().numpy()
+        ia = outs["image_as"][f].double().cpu().numpy()
+        rows.append({"gate_err": float(res["gate_err"][f].item()), "gate_pass": int(res["gate_pass"][f].item()),
+                     "rel_l2": float(np.linalg.norm(il / il.max() - it / it.max()) / np.linalg.norm(it / it.max())),
+                     "peak_match": bool(np.argmax(il) == np.argmax(it)),
+                     "isnr_learned": learn.isnr_esa(il, pix)[0], "isnr_tax": learn.isnr_esa(it, pix)[0],
+                     "isnr_as": learn.isnr_esa(ia, pix)[0], "esa_learned": learn.isnr_esa(il, pix)[1],
+                     "esa_tax": learn.isnr_esa(it, pix)[1], "esa_as": learn.isnr_esa(ia, pix)[1]})
+    acc = learn.summarize(rows)
+    L.close()
+    plan.close()
+    return {"workload": w.name, "frames_per_call": B, "value": B / (ms_l / 1000.0), "unit": "frames/s",
+            "us_per_frame": 1000.0 * ms_l / B, "plain_value": B / (ms_p / 1000.0),
+            "plain_us_per_frame": 1000.0 * ms_p / B, "speedup_vs_plain": ms_p / ms_l, "kernels_per_call": kernels,
+            "gate_tol": args.gate_tol, "accuracy_vs_plain": acc,
+            "checkpoint": {"frames": meta.get("frames"), "epochs": meta.get("epochs"),
+                           "held_out": meta.get("held_out")}}
+
+
 # -------------------------------------------------------------- our arm --
 def run_ours(args):
     import numpy as np
@@ -358,6 +425,11 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     if args.batch_only:
         print(json.dumps({"batch": run_batch(args, dev, stream)}), flush=True)
+        dist.finalize()
+        return 0
+    if args.learned_only:
+        print(json.dumps({"learned": run_learned(args, w, pool, stream, dev), "config": {"workload": w.name}}),
+              flush=True)
         dist.finalize()
         return 0
     if args.forms_only:
@@ -417,6 +489,7 @@ def run_ours(args):
     # Batched forms: 64 frames per call, the plain FP32 path and the tensor-core forms.
     forms = {} if args.no_forms else run_forms(args, w, pool, stream, dev)
     batch = run_batch(args, dev, stream) if args.batch_frames > 0 and rank == 0 else {}
+    learned = run_learned(args, w, pool, stream, dev) if args.learned_batch > 0 and rank == 0 else {}
 
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -453,6 +526,7 @@ def run_ours(args):
             "clocks": ck,
             "forms": forms,
             "batch": batch,
+            "learned": learned,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -481,6 +555,10 @@ def main():
     ap.add_argument("--batch-calls", type=int, default=10)
     ap.add_argument("--batch-loop-frames", type=int, default=32, help="frames of the one-frame-call loop")
     ap.add_argument("--batch-only", action="store_true", help="time only the uneven batch (profiling aid)")
+    ap.add_argument("--learned-batch", type=int, default=256, help="frames per learned-form call (0: skip)")
+    ap.add_argument("--learned-calls", type=int, default=5)
+    ap.add_argument("--gate-tol", type=float, default=0.25, help="error-gate bound of the learned form")
+    ap.add_argument("--learned-only", action="store_true", help="time only the learned form (profiling aid)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

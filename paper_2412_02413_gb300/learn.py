@@ -1,0 +1,232 @@
+"""Training and evaluation of the learned NCC-weight network (pam_learn_*).
+
+The network is trained on frames the method itself turns into examples:
+synthetic channel data of the 128-element workload go through
+``pam_learn_example``, which returns the network input (band energies of the
+full-aperture AS map, Eq. 3) and the target (the exact rho_TAX of Eq. 4 and
+Eq. 10). Forward, backward and Adam run in libpam's kernels
+(``pam_learn_train_step``).
+
+Training frames: the receive model is linear in the sources, so frames are
+made as sums of 1-6 single-source responses drawn from a seeded bank
+(``synth.source_response``), each with a seeded gain, plus white channel noise
+at 20 dB SNR. Superposition and noise are input synthesis; they are done on
+the GPU with torch so that 20k frames take seconds. Held-out frames come from
+``synth.make_frame`` (independent sources and seeds).
+
+  python -m paper_2412_02413_gb300.learn [--frames 20000] [--epochs 3] [--out PATH]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import time
+
+import numpy as np
+
+from . import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CHECKPOINT = os.path.join(HERE, "weights", "ncc_cnn_astax_128el_128x512.npz")
+BANK_SEED = 1_000_000        # sources of the training bank
+HELD_OUT_FIRST = 500_000     # frame indices of the held-out synth.make_frame frames
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-normal weights and zero biases, flat in the library's order
+    (per layer w[out][in][3][3] then b[out])."""
+    rng = np.random.default_rng(seed)
+    chans = (5, 32, 32, 32, 32, 1)
+    parts = []
+    for cin, cout in zip(chans[:-1], chans[1:]):
+        parts.append((rng.standard_normal((cout, cin, 3, 3)) * math.sqrt(2.0 / (9 * cin))).ravel())
+        parts.append(np.zeros(cout))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def _response(args):
+    w, src, seed = args
+    return synth.source_response(w, src, seed)
+
+
+def make_bank(w, n: int, seed: int = BANK_SEED, workers: int = 0) -> np.ndarray:
+    """[n][n_elem][nt] float32 single-source responses (spawned worker pool)."""
+    srcs = synth.bank_sources(w, n, seed)
+    jobs = [(w, s, seed + 7 + i) for i, s in enumerate(srcs)]
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    if workers == 1:
+        return np.stack([_response(j) for j in jobs])
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return np.stack(pool.map(_response, jobs, chunksize=8))
+
+
+def mix_frames(bank, n: int, gen, max_sources: int = 6, snr_db: float = 20.0):
+    """n frames [n][n_elem][nt] on the bank's device: sums of 1..max_sources
+    bank responses with gains in [0.6, 1.4], plus white noise at snr_db
+    relative to each frame's mean channel power."""
+    import torch
+    dev = bank.device
+    K = bank.shape[0]
+    count = torch.randint(1, max_sources + 1, (n,), generator=gen, device=dev)
+    idx = torch.randint(0, K, (n, max_sources), generator=gen, device=dev)
+    gain = 0.6 + 0.8 * torch.rand((n, max_sources), generator=gen, device=dev)
+    rf = torch.zeros((n,) + tuple(bank.shape[1:]), dtype=torch.float32, device=dev)
+    for j in range(max_sources):
+        g = gain[:, j] * (count > j).float()
+        rf += g[:, None, None] * bank.index_select(0, idx[:, j])
+    p = rf.pow(2).mean(dim=(1, 2))
+    sigma = torch.sqrt(p / 10.0 ** (snr_db / 10.0))
+    rf += torch.randn(rf.shape, generator=gen, device=dev) * sigma[:, None, None]
+    return rf
+
+
+def isnr_esa(img: np.ndarray, pix_area_mm2: float):
+    """Eq. 12 ISNR (dB) and the energy spread area A_0.5 (mm^2)."""
+    m = img > 0.5 * img.max()
+    inside, outside = img[m].mean(), img[~m].mean()
+    return 10.0 * math.log10(inside / outside), float(m.sum() * pix_area_mm2)
+
+
+def save_checkpoint(path: str, params: np.ndarray, meta: dict):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez(path, params=np.asarray(params, np.float32), meta=np.array(json.dumps(meta)))
+
+
+def load_checkpoint(path: str = CHECKPOINT):
+    d = np.load(path)
+    return d["params"], json.loads(str(d["meta"]))
+
+
+def held_out_frames(w, n: int, first: int = HELD_OUT_FIRST, workers: int = 0) -> np.ndarray:
+    jobs = [(w, first + i) for i in range(n)]
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return np.stack(pool.map(_frame, jobs))
+
+
+def _frame(args):
+    w, f = args
+    return synth.make_frame(w, f)[0]
+
+
+def evaluate(learned, plan, rf_t, w, gate_tol: float):
+    """Learned vs plain AS-TAX on frames rf_t: per-frame gate error and pass,
+    relative L2 of the normalised images, peak match, ISNR of learned, exact
+    and plain AS images."""
+    import torch
+    learned.configure(gate_tol=gate_tol, tensor_cores=True)
+    out = learned.as_tax(rf_t)
+    ref = plan.as_tax(rf_t, rho_n=True, image_as=True)
+    torch.cuda.synchronize()
+    pix = w.pitch * w.dz * 1e6
+    rows = []
+    for f in range(rf_t.shape[0]):
+        il = out["image"][f].cpu().numpy().astype(np.float64)
+        it = ref["image"][f].cpu().numpy().astype(np.float64)
+        ia = ref["image_as"][f].cpu().numpy().astype(np.float64)
+        rows.append({
+            "gate_err": float(out["gate_err"][f].item()),
+            "gate_pass": int(out["gate_pass"][f].item()),
+            "rel_l2": float(np.linalg.norm(il / il.max() - it / it.max()) / np.linalg.norm(it / it.max())),
+            "peak_match": bool(np.argmax(il) == np.argmax(it)),
+            "isnr_learned": isnr_esa(il, pix)[0], "isnr_tax": isnr_esa(it, pix)[0], "isnr_as": isnr_esa(ia, pix)[0],
+            "esa_learned": isnr_esa(il, pix)[1], "esa_tax": isnr_esa(it, pix)[1], "esa_as": isnr_esa(ia, pix)[1],
+        })
+    return rows
+
+
+def summarize(rows):
+    a = lambda k: float(np.mean([r[k] for r in rows]))
+    return {"frames": len(rows), "gate_pass_rate": a("gate_pass"), "gate_err_median": float(np.median(
+        [r["gate_err"] for r in rows])), "rel_l2_mean": a("rel_l2"), "peak_match_rate": a("peak_match"),
+        "isnr_learned_db": a("isnr_learned"), "isnr_tax_db": a("isnr_tax"), "isnr_as_db": a("isnr_as"),
+        "esa_learned_mm2": a("esa_learned"), "esa_tax_mm2": a("esa_tax"), "esa_as_mm2": a("esa_as")}
+
+
+def train(args):
+    import torch
+    from . import pam
+    torch.cuda.set_device(0)
+    w = synth.workload(2)
+    t0 = time.time()
+    bank_np = make_bank(w, args.bank, workers=args.workers)
+    bank = torch.from_numpy(bank_np).cuda()
+    del bank_np
+    t_bank = time.time() - t0
+    G = args.gen_batch
+    L = pam.Learned.from_workload(w, max_frames=G)
+    L.set_params(init_params(args.seed))
+    N = args.frames
+    feats = L.empty_features(N)
+    target = torch.empty((N, w.nz, w.n_elem), dtype=torch.float32, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(args.seed + 17)
+    t1 = time.time()
+    for s in range(0, N, G):
+        n = min(G, N - s)
+        rf = mix_frames(bank, n, gen)
+        L.example(rf, features=feats[s:s + n], target=target[s:s + n])
+    L.sync()
+    t_data = time.time() - t1
+    del bank
+    B = args.batch
+    nb = N // B
+    steps = args.epochs * nb
+    loss = torch.zeros(4, dtype=torch.float32, device="cuda")
+    order_gen = torch.Generator().manual_seed(args.seed + 29)
+    log = []
+    t2 = time.time()
+    step = 0
+    for ep in range(args.epochs):
+        for bi in torch.randperm(nb, generator=order_gen).tolist():
+            lr = args.lr_min + 0.5 * (args.lr - args.lr_min) * (1.0 + math.cos(math.pi * step / steps))
+            L.train_step(feats[bi * B:(bi + 1) * B], target[bi * B:(bi + 1) * B], lr, loss=loss)
+            if step % args.log_every == 0 or step == steps - 1:
+                log.append((step, float(loss[0].item())))
+            step += 1
+    L.sync()
+    t_train = time.time() - t2
+    params = L.get_params()
+    del feats, target
+    # held-out evaluation on independent frames
+    rf_ho = torch.from_numpy(held_out_frames(w, args.held_out, workers=args.workers)).cuda()
+    L.close()
+    Le = pam.Learned.from_workload(w, max_frames=args.held_out)
+    Le.set_params(params)
+    plan = pam.Plan.from_workload(w, max_frames=args.held_out)
+    rows = evaluate(Le, plan, rf_ho, w, args.gate_tol)
+    meta = {
+        "workload": w.name, "frames": N, "epochs": args.epochs, "batch": B, "steps": steps, "lr": args.lr,
+        "lr_min": args.lr_min, "bank_sources": args.bank, "seed": args.seed,
+        "seconds": {"bank": round(t_bank, 1), "examples": round(t_data, 1), "train": round(t_train, 1)},
+        "loss_log": log[:: max(1, len(log) // 40)] + [log[-1]],
+        "held_out": summarize(rows), "gate_tol": args.gate_tol,
+    }
+    save_checkpoint(args.out, params, meta)
+    print(json.dumps(meta))
+    plan.close()
+    Le.close()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--frames", type=int, default=20000)
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--lr-min", type=float, default=5e-5)
+    ap.add_argument("--bank", type=int, default=1024, help="single-source responses in the bank")
+    ap.add_argument("--gen-batch", type=int, default=256, help="frames per example call")
+    ap.add_argument("--held-out", type=int, default=64)
+    ap.add_argument("--gate-tol", type=float, default=0.25)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--log-every", type=int, default=100)
+    ap.add_argument("--workers", type=int, default=0)
+    ap.add_argument("--out", default=CHECKPOINT)
+    train(ap.parse_args())
+
+
+if __name__ == "__main__":
+    main()

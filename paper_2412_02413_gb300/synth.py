@@ -201,16 +201,10 @@ def source_signal_spectrum(src: Source, w: Workload, rng, n: int):
     return np.array(freqs), np.array(amps), np.array(phases), noise
 
 
-def make_frame(w: Workload, frame: int = 0, sources: Optional[List[Source]] = None):
-    """One frame of channel-major float32 RF [n_elem][nt] plus its sources.
-
-    The harmonic emission delays are analytic. The broadband emission is
-    periodic over a record of 2*nt samples and delayed exactly in the
-    frequency domain. Amplitude falls off as 10 mm / r."""
-    seed = SEED_BASE + 1000 * w.workload_id + frame
-    if sources is None:
-        sources = make_sources(w, seed)
-    rng = np.random.default_rng(seed + 7)
+def _propagated_sources(w: Workload, sources: List[Source], rng):
+    """Harmonic part of the channel signals [n_elem][nt] (analytic delays) and
+    the summed, delayed spectra of the broadband parts [n_elem][nt + 1] on a
+    periodic record of 2*nt samples (exact fractional delays)."""
     ne, nt = w.n_elem, w.nt
     t = np.arange(nt) / w.fs
     xe = w.pixel_x()
@@ -231,7 +225,43 @@ def make_frame(w: Workload, frame: int = 0, sources: Optional[List[Source]] = No
         nspec = np.fft.rfft(noise)
         band = np.nonzero(nspec)[0]
         spec[:, band] += (gain[:, None] * nspec[band][None, :]) * np.exp(-2j * np.pi * fL[band][None, :] * tau[:, None])
-    rf += np.fft.irfft(spec, L, axis=1)[:, :nt]
+    return rf, spec
+
+
+def source_response(w: Workload, src: Source, seed: int) -> np.ndarray:
+    """Noise-free channel signals [n_elem][nt] (float32) of one source alone.
+    The receive model is linear in the sources, so a frame of several sources
+    is the sum of their responses plus channel noise."""
+    rf, spec = _propagated_sources(w, [src], np.random.default_rng(seed))
+    rf += np.fft.irfft(spec, 2 * w.nt, axis=1)[:, :w.nt]
+    return rf.astype(np.float32)
+
+
+def bank_sources(w: Workload, n: int, seed: int) -> List[Source]:
+    """n single sources on seeded pixels of the workload's grid (kinds
+    alternate stable / inertial), as make_sources draws them."""
+    one = dataclasses.replace(w, n_sources=(1, 1))
+    out = []
+    for i in range(n):
+        src = make_sources(one, seed + i)[0]
+        if i % 2:
+            src = dataclasses.replace(src, kind="inertial")
+        out.append(src)
+    return out
+
+
+def make_frame(w: Workload, frame: int = 0, sources: Optional[List[Source]] = None):
+    """One frame of channel-major float32 RF [n_elem][nt] plus its sources.
+
+    The harmonic emission delays are analytic. The broadband emission is
+    periodic over a record of 2*nt samples and delayed exactly in the
+    frequency domain. Amplitude falls off as 10 mm / r."""
+    seed = SEED_BASE + 1000 * w.workload_id + frame
+    if sources is None:
+        sources = make_sources(w, seed)
+    rng = np.random.default_rng(seed + 7)
+    rf, spec = _propagated_sources(w, sources, rng)
+    rf += np.fft.irfft(spec, 2 * w.nt, axis=1)[:, :w.nt]
     p = float(np.mean(rf ** 2))
     nrng = np.random.default_rng(seed + 1)
     if w.snr_db is not None and p > 0:
