@@ -282,6 +282,31 @@ pam_status pam_batch_info(pam_batch_t b, int *n_items, int *persistent_ctas, lon
 /* Frees the batch (NULL-safe). Waits for the device first. */
 void pam_batch_destroy(pam_batch_t b);
 
+/* AS^3 (Eq. 20): I = (I_AS / max I_AS)^2 * I_AS, the full-aperture AS energy
+ * (Eq. 3) weighted by its own squared normalised map instead of rho_n (the
+ * paper's comparison in its appendix). image: device [n_frames][nz][nx]. The
+ * maximum is taken per frame; an all-zero frame stays zero. */
+pam_status pam_as3(pam_plan_t p, const float *rf, int n_frames, float *image, void *stream);
+
+/* Image-quality measures of one map (Sec. II-D, Eq. 12-13). */
+typedef struct {
+    float esa_m2;   /* energy spread area A_0.5: pixels with I > max/2, times the pixel area |dx dz| */
+    float isnr_db;  /* Eq. 12: 10 log10(mean I inside A_0.5 / mean I outside); +inf with nothing
+                       (or only zeros) outside, NaN when max <= 0 */
+    float cx_m;     /* Eq. 13 centroid sum(I_i r_i) / sum(I_i) over pixels with I_i > alpha max: */
+    float cz_m;     /*   lateral and axial coordinates (m); NaN when no pixel qualifies */
+    float max;      /* the map's maximum */
+    int n_inside;   /* pixels in A_0.5 */
+} pam_image_metrics_t;
+
+/* Measures of n_frames maps, device float32 [n_frames][nz][nx], one CTA per
+ * frame. Pixel (j, i) sits at x = x0_m + i dx_m, z = z0_m + j dz_m (for a
+ * plan's grid: x0_m = -(nx-1)/2 pitch, dx_m = pitch). alpha in (0, 1): 0.7 for
+ * images, 0.9 for NCC maps (Sec. II-D). out: device [n_frames]. Sums are FP64.
+ * Asynchronous on `stream`. */
+pam_status pam_image_metrics(const float *maps, int n_frames, int nz, int nx, double x0_m, double dx_m, double z0_m,
+                             double dz_m, float alpha, pam_image_metrics_t *out, void *stream);
+
 /* ------------------------------------------------------------------------
  * Learned form (AS-TAX with a predicted NCC weight). A 5-layer convolutional
  * network predicts rho_TAX (Eq. 10, before the max normalisation) from the

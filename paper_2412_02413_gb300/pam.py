@@ -81,6 +81,9 @@ _SIGS = {
     "pam_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                       ctypes.POINTER(ctypes.c_longlong)]),
     "pam_batch_destroy": (None, [_VP]),
+    "pam_as3": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
+    "pam_image_metrics": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_float, _VP, _VP]),
     "pam_learn_n_params": (ctypes.c_size_t, []),
     "pam_learn_create": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(_VP)]),
     "pam_learn_destroy": (None, [_VP]),
@@ -299,6 +302,14 @@ class Plan:
         _check(fn(self._h, _dptr(rf), F, _dptr(o["image"]), _dptr(o.get("rho_n")), _dptr(o.get("rho_pairs")),
                   _dptr(o.get("image_as")), _stream_ptr(stream)))
         return o
+
+    def as3(self, rf, out=None, stream=None):
+        """AS^3 image (Eq. 20) [F][nz][nx]."""
+        rf = self._check_rf(rf)
+        F = rf.shape[0]
+        img = self._empty(F, self.nz, self.nx) if out is None else out
+        _check(load().pam_as3(self._h, _dptr(rf), F, _dptr(img), _stream_ptr(stream)))
+        return img
 
     def as_xcorr_host(self, rf_host: np.ndarray, image_out: np.ndarray, rho_n_out: Optional[np.ndarray] = None,
                       stream=None):
@@ -567,6 +578,24 @@ class Learned:
         t = ctypes.c_longlong()
         _check(load().pam_learn_info(self._h, ctypes.byref(k), ctypes.byref(mf), ctypes.byref(t)))
         return {"kernel_launches": k.value, "max_frames": mf.value, "adam_steps": t.value}
+
+
+METRIC_FIELDS = ("esa_m2", "isnr_db", "cx_m", "cz_m", "max", "n_inside")
+
+
+def image_metrics(maps, x0: float, dx: float, z0: float, dz: float, alpha: float = 0.7, stream=None):
+    """Eq. 12-13 measures of device maps [F][nz][nx]: a list of dicts (one per frame)."""
+    torch = _require_cuda()
+    if maps.dim() == 2:
+        maps = maps.unsqueeze(0)
+    maps = maps.contiguous()
+    F, nz, nx = maps.shape
+    out = torch.empty((max(F, 1), 6), dtype=torch.float32, device=maps.device)   # 6 x 4-byte fields
+    _check(load().pam_image_metrics(_dptr(maps), F, nz, nx, float(x0), float(dx), float(z0), float(dz),
+                                    float(alpha), _dptr(out), _stream_ptr(stream)))
+    raw = out[:F].cpu().numpy()
+    n_in = raw[:, 5].copy().view(np.int32)
+    return [dict(zip(METRIC_FIELDS, [float(v) for v in r[:5]] + [int(n)])) for r, n in zip(raw, n_in)]
 
 
 def unpack_features(features, nz: int, nx: int):
