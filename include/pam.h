@@ -360,8 +360,11 @@ pam_status pam_learn_get_params(pam_learn_t l, float *params, size_t n);
 
 /* gate_tol: relative L2 bound of the gate (default 0.05; < 0 sends every
  * frame through the exact path, +inf accepts every frame). use_tensor_cores: 1
- * runs the 32 -> 32 layers' forward on tcgen05 (nx == 128 only, else
- * PAM_ERR_UNSUPPORTED), 0 on CUDA cores (default). */
+ * runs every layer's forward on tcgen05 and the band energies in the BF16
+ * tensor-core form (PAM_FORM_GEMM_BF16, relative error about 6e-4, below the
+ * BF16 rounding of the features); nx == 128 with disjoint apertures only, else
+ * PAM_ERR_UNSUPPORTED. The first call with 1 builds that form's tables (blocks).
+ * 0 runs both on the FP32 path and CUDA cores (default). */
 pam_status pam_learn_configure(pam_learn_t l, float gate_tol, int use_tensor_cores);
 
 /* Bytes of one frame of packed features. */

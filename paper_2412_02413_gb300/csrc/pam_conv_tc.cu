@@ -1,9 +1,12 @@
-// pam_conv_tc.cu -- tensor-core (tcgen05) forward of a 32 -> 32 channel 3x3
-// convolution with bias and ReLU, for rows of nx = 128 pixels: the hidden
-// layers of the learned NCC-weight network.
+// pam_conv_tc.cu -- tensor-core (tcgen05) forward of the 3x3 convolutions of
+// the learned NCC-weight network, for rows of nx = 128 pixels: the first layer
+// (5 -> 32, bias, ReLU), the hidden layers (32 -> 32, bias, ReLU) and the last
+// layer (32 -> 1, bias, FP32 output).
 //
-// One output row is a GEMM with M = 128 pixels, N = 32 output channels and
-// K = 9 taps x 32 input channels:
+// One output row is a GEMM with M = 128 pixels, N = 32 output channels (16
+// for the last layer, whose channels 1..15 carry zero weights) and K = 9 taps
+// x the input channels (one chunk of 8 for the first layer, padded in shared
+// memory with a zero chunk to the K step of 16):
 //   y[j][o] = b[o] + sum_{u,v,c} x[i+u-1][j+v-1][c] w[o][c][u][v].
 // Activations are stored chunked and padded, [C/8][nz+2][nx+2][8] BF16 per
 // frame, so one padded input row of one chunk of 8 channels is 130 pixels x
@@ -13,15 +16,15 @@
 // is the staged row i+u-1 starting at pixel v, i.e. a descriptor whose start
 // address moves by 16 bytes per pixel, with SBO = 128 bytes (next 8 pixels)
 // and LBO = 2080 bytes (next chunk of channels). No im2col is materialised.
-// The B operand (weights) is resident: [tap][chunk][out channel][8] BF16, 18 KB.
-// Each row accumulates 18 MMAs (M = 128, N = 32, K = 16) into one of two
+// The B operand (weights) is resident: [tap][chunk][out channel][8] BF16.
+// Each row accumulates 9 x (chunks / 2) MMAs (M = 128, K = 16) into one of two
 // tensor-memory accumulator sets.
 //
 // One CTA per (16-row strip, frame), 6 warps:
 //   warp 0: bulk copies of the strip's 18 input rows through a ring of 6 slots;
 //   warp 1: the MMA chain of each output row (one elected lane issues);
 //   warps 2-5: the epilogue, each reading its quarter of the 128 TMEM lanes
-//     (pixels), adding the bias, ReLU, and storing BF16 to the output tensor.
+//     (pixels), adding the bias, and storing BF16 after ReLU (or FP32 channel 0).
 // All waits are bounded; on expiry the CTA sets the status word and drains.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -35,10 +38,21 @@ constexpr int W = 128, WP = W + 2;
 constexpr int ROWS = 16;                       // output rows per CTA
 constexpr int NSLOT = 6;                       // staged input rows
 constexpr int CH_BYTES = WP * 16;              // one padded row of one chunk: 2080 B
-constexpr int ROW_BYTES = 4 * CH_BYTES;        // 8320 B
-constexpr int WT_BYTES = 9 * 4 * 32 * 16;      // 18432 B
 constexpr int THREADS = 192;
-constexpr size_t SMEM = (size_t)WT_BYTES + (size_t)NSLOT * ROW_BYTES + 256;
+
+// Shape of one layer: NCI input chunks in global memory, KCH staged chunks
+// (at least 2: one K step), NCO GEMM columns.
+template <int NCI, int NCO>
+struct ConvShape {
+    static constexpr int KCH = NCI < 2 ? 2 : NCI;
+    static constexpr int ROW_BYTES = KCH * CH_BYTES;
+    static constexpr int TAP_BYTES = KCH * NCO * 16;
+    static constexpr int WT_BYTES = 9 * TAP_BYTES;
+    static constexpr size_t SMEM = (size_t)WT_BYTES + (size_t)NSLOT * ROW_BYTES + 256;
+    // kind::f16, FP32 accumulate, A = B = BF16, both K-major, N = NCO, M = 128.
+    static constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NCO >> 3) << 17) |
+                                      ((128u >> 4) << 24);
+};
 
 __device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -80,15 +94,12 @@ __device__ __forceinline__ uint64_t sdesc(unsigned addr, unsigned lbo, unsigned 
     return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
-// kind::f16, FP32 accumulate, A = B = BF16, both K-major, N = 32, M = 128.
-constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-
-__device__ __forceinline__ void mma_elect(unsigned d, uint64_t a, uint64_t b, unsigned acc)
+__device__ __forceinline__ void mma_elect(unsigned d, uint64_t a, uint64_t b, unsigned idesc, unsigned acc)
 {
     asm volatile(
         "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
         " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void commit_elect(uint64_t *b)
@@ -116,13 +127,16 @@ __device__ __forceinline__ unsigned pack2(float a, float b)
     return r;
 }
 
+template <int NCI, int NCO, bool F32OUT>
 __global__ void __launch_bounds__(THREADS)
 conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const float *__restrict__ bias,
-               uint4 *__restrict__ out, int H, int *__restrict__ status)
+               void *__restrict__ out, int H, int *__restrict__ status)
 {
+    using CS = ConvShape<NCI, NCO>;
+    constexpr int KCH = CS::KCH, ROW_BYTES = CS::ROW_BYTES, WT_BYTES = CS::WT_BYTES;
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t *sW = sm;                                  // [9][4][32][8] BF16
-    uint8_t *sRow = sm + WT_BYTES;                     // [NSLOT][4][130][8] BF16
+    uint8_t *sW = sm;                                  // [9][KCH][NCO][8] BF16
+    uint8_t *sRow = sm + WT_BYTES;                     // [NSLOT][KCH][130][8] BF16
     uint64_t *full = reinterpret_cast<uint64_t *>(sRow + NSLOT * ROW_BYTES);   // [NSLOT]
     uint64_t *sfree = full + NSLOT;                    // [NSLOT]
     uint64_t *afull = sfree + NSLOT;                   // [2]
@@ -159,6 +173,15 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    if constexpr (NCI < KCH) {
+        // staged chunks NCI..KCH-1 of every slot stay zero (the K padding);
+        // make the generic-proxy stores visible to the tensor core
+        for (int i = tid; i < NSLOT * (KCH - NCI) * CH_BYTES / 16; i += THREADS) {
+            const int slot = i / ((KCH - NCI) * CH_BYTES / 16), r = i % ((KCH - NCI) * CH_BYTES / 16);
+            reinterpret_cast<uint4 *>(sRow + slot * ROW_BYTES + NCI * CH_BYTES)[r] = make_uint4(0u, 0u, 0u, 0u);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
     fence_before();
     __syncthreads();
     fence_after();
@@ -189,10 +212,10 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
                 const int s = k % NSLOT;
                 if (k >= NSLOT) ok = wait(&sfree[s], (unsigned)(k / NSLOT - 1) & 1u);
                 if (!ok) break;
-                bar_expect(&full[s], ROW_BYTES);
+                bar_expect(&full[s], NCI * CH_BYTES);
                 const int prow = r_first + k;
-                for (int c = 0; c < 4; ++c)
-                    bulk_load(sRow + s * ROW_BYTES + c * CH_BYTES, in + (((size_t)f * 4 + c) * HP + prow) * WP,
+                for (int c = 0; c < NCI; ++c)
+                    bulk_load(sRow + s * ROW_BYTES + c * CH_BYTES, in + (((size_t)f * NCI + c) * HP + prow) * WP,
                               CH_BYTES, &full[s]);
                 issued = k + 1;
             }
@@ -223,10 +246,10 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
                 const int u = tap / 3, v = tap % 3;
                 const unsigned arow = rbase + (unsigned)(((r + u) % NSLOT) * ROW_BYTES + v * 16);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
+                for (int h = 0; h < KCH / 2; ++h) {
                     const uint64_t a = sdesc(arow + (unsigned)(2 * h * CH_BYTES), CH_BYTES, 128);
-                    const uint64_t b = sdesc(wbase + (unsigned)(tap * 2048 + h * 1024), 512, 128);
-                    mma_elect(d, a, b, (tap | h) ? 1u : 0u);
+                    const uint64_t b = sdesc(wbase + (unsigned)(tap * CS::TAP_BYTES + h * 2 * NCO * 16), NCO * 16, 128);
+                    mma_elect(d, a, b, CS::IDESC, (tap | h) ? 1u : 0u);
                 }
             }
             any = true;
@@ -244,27 +267,39 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
         // ---------------- epilogue: TMEM -> bias + ReLU -> BF16 ----------------
         const int quarter = warp & 3;
         const int j = 32 * quarter + lane;   // pixel = TMEM lane
-        float b[32];
+        constexpr int NB = F32OUT ? 1 : 32;
+        float b[NB];
 #pragma unroll
-        for (int o = 0; o < 32; ++o) b[o] = bias[o];
+        for (int o = 0; o < NB; ++o) b[o] = bias[o];
         for (int r = 0; r < nr; ++r) {
             const int t = r & 1;
             if (!__all_sync(0xffffffffu, wait(&afull[t], (unsigned)(r >> 1) & 1u))) break;
             fence_after();
-            unsigned acc[32];
-            tmem_ld32(tmem + (unsigned)(t * 32) + ((unsigned)(32 * quarter) << 16), acc);
-            fence_before();
-            __syncwarp();
-            if (lane == 0) bar_arrive(&aempty[t]);
-            const int prow = r_first + r + 1;
-            uint4 *dst = out + (((size_t)f * 4) * HP + prow) * WP + (j + 1);
+            const unsigned taddr = tmem + (unsigned)(t * 32) + ((unsigned)(32 * quarter) << 16);
+            if constexpr (F32OUT) {
+                unsigned a0;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n" : "=r"(a0) : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                fence_before();
+                __syncwarp();
+                if (lane == 0) bar_arrive(&aempty[t]);
+                reinterpret_cast<float *>(out)[((size_t)f * H + r_first + r) * W + j] = __uint_as_float(a0) + b[0];
+            } else {
+                unsigned acc[32];
+                tmem_ld32(taddr, acc);
+                fence_before();
+                __syncwarp();
+                if (lane == 0) bar_arrive(&aempty[t]);
+                const int prow = r_first + r + 1;
+                uint4 *dst = reinterpret_cast<uint4 *>(out) + (((size_t)f * 4) * HP + prow) * WP + (j + 1);
 #pragma unroll
-            for (int ch = 0; ch < 4; ++ch) {
-                float y[8];
+                for (int ch = 0; ch < 4; ++ch) {
+                    float y[8];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) y[k] = fmaxf(__uint_as_float(acc[ch * 8 + k]) + b[ch * 8 + k], 0.0f);
-                dst[(size_t)ch * HP * WP] =
-                    make_uint4(pack2(y[0], y[1]), pack2(y[2], y[3]), pack2(y[4], y[5]), pack2(y[6], y[7]));
+                    for (int k = 0; k < 8; ++k) y[k] = fmaxf(__uint_as_float(acc[ch * 8 + k]) + b[ch * 8 + k], 0.0f);
+                    dst[(size_t)ch * HP * WP] =
+                        make_uint4(pack2(y[0], y[1]), pack2(y[2], y[3]), pack2(y[4], y[5]), pack2(y[6], y[7]));
+                }
             }
         }
     }
@@ -275,19 +310,38 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(64u) : "memory");
 }
 
+template <int NCI, int NCO, bool F32OUT>
+cudaError_t set_tc_smem()
+{
+    return cudaFuncSetAttribute(conv_tc_kernel<NCI, NCO, F32OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ConvShape<NCI, NCO>::SMEM);
+}
+
+template <int NCI, int NCO, bool F32OUT>
+cudaError_t launch_tc(const uint4 *in, const uint4 *wt, const float *bias, void *out, int F, int H, int *status,
+                      cudaStream_t st)
+{
+    dim3 grid((H + ROWS - 1) / ROWS, F);
+    conv_tc_kernel<NCI, NCO, F32OUT><<<grid, THREADS, ConvShape<NCI, NCO>::SMEM, st>>>(in, wt, bias, out, H, status);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t prepare_conv_tc()
 {
-    return cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    cudaError_t e = set_tc_smem<1, 32, false>();
+    if (e == cudaSuccess) e = set_tc_smem<4, 32, false>();
+    if (e == cudaSuccess) e = set_tc_smem<4, 16, true>();
+    return e;
 }
 
-cudaError_t launch_conv_tc(const uint4 *in, const uint4 *wt, const float *bias, uint4 *out, int F, int H,
+cudaError_t launch_conv_tc(int layer, const uint4 *in, const uint4 *wt, const float *bias, void *out, int F, int H,
                            int *status, cudaStream_t st)
 {
-    dim3 grid((H + ROWS - 1) / ROWS, F);
-    conv_tc_kernel<<<grid, THREADS, SMEM, st>>>(in, wt, bias, out, H, status);
-    return cudaGetLastError();
+    if (layer == 0) return launch_tc<1, 32, false>(in, wt, bias, out, F, H, status, st);
+    if (layer == 4) return launch_tc<4, 16, true>(in, wt, bias, out, F, H, status, st);
+    return launch_tc<4, 32, false>(in, wt, bias, out, F, H, status, st);
 }
 
 }  // namespace pam

@@ -154,6 +154,12 @@ cudaError_t launch_prec_tables(const pam_plan_s &p, cudaStream_t st);
 cudaError_t launch_prec(const pam_plan_s &p, int n_frames, cudaStream_t st);
 cudaError_t prepare_prec_kernels();
 int prec_kernels();   // kernels launch_prec launches
+// Tensor-core form, band energies: from spectra S [F][n_bins][n_elem] (any
+// plan's, same bins), the full-aperture energy sum_k |p_1 + p_2 + p_3|^2 of each
+// contiguous chunk of Omega (chunks as launch_prop_bands) into bands[f][b][nz][nx].
+// 3 kernels. The plan must be a BF16 or FP16 form with n_apod 3.
+cudaError_t launch_prec_bands(const pam_plan_s &p, const float2 *S, int n_frames, int n_bands, float *bands,
+                              cudaStream_t st);
 
 // Records `msg` as the calling thread's pam_last_error() text and returns s.
 pam_status set_error(pam_status s, const char *msg);

@@ -15,8 +15,8 @@
 // [F][C/8][nz+2][nx+2][8], eight channels of one pixel in 16 bytes, with a
 // zero border of one pixel so that every 3x3 tap reads memory.
 //
-// Kernels of this file run on CUDA cores; the forward of the 32 -> 32 layers
-// also has a tcgen05 tensor-core version (pam_conv_tc.cu).
+// Kernels of this file run on CUDA cores; the forward of every layer also has
+// a tcgen05 tensor-core version (pam_conv_tc.cu) for nx = 128.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -32,8 +32,9 @@
 
 namespace pam {
 
-// tcgen05 forward of a 32 -> 32 layer (pam_conv_tc.cu); nx == 128 only.
-cudaError_t launch_conv_tc(const uint4 *in, const uint4 *wtc, const float *bias, uint4 *out, int F, int H,
+// tcgen05 forward of layer 0..4 (pam_conv_tc.cu); nx == 128 only. Layers 0-3
+// write BF16 activations after bias and ReLU, layer 4 the FP32 logit z.
+cudaError_t launch_conv_tc(int layer, const uint4 *in, const uint4 *wt, const float *bias, void *out, int F, int H,
                            int *status, cudaStream_t st);
 cudaError_t prepare_conv_tc();
 
@@ -44,6 +45,11 @@ constexpr int NL = 5;                                   // layers
 __host__ __device__ constexpr int CIN(int l) { return l == 0 ? 5 : 32; }
 __host__ __device__ constexpr int COUT(int l) { return l == NL - 1 ? 1 : 32; }
 __host__ __device__ constexpr int CINC(int l) { return l == 0 ? 1 : 4; }
+// tensor-core weight layout of layer l: [9][TC_KCH][TC_NCO][8] BF16
+__host__ __device__ constexpr int TC_KCH(int l) { return l == 0 ? 2 : 4; }
+__host__ __device__ constexpr int TC_NCO(int l) { return l == NL - 1 ? 16 : 32; }
+__host__ __device__ constexpr size_t tc_count(int l) { return (size_t)9 * TC_KCH(l) * TC_NCO(l) * 8; }
+__host__ __device__ constexpr size_t tc_offset(int l) { return l == 0 ? 0 : tc_offset(l - 1) + tc_count(l - 1); }
 constexpr int N_BANDS = 4;
 constexpr float FEATURE_FLOOR = 1e-4f;
 constexpr int CT = 128;        // threads (= pixels along a row) of a CUDA-core conv block
@@ -101,11 +107,13 @@ __global__ void prep_kernel(const float *__restrict__ params, PrepPtrs pp)
             pp.wb[l][i] = o < co ? round_bf(w[((size_t)o * ci + c) * 9 + (8 - t)]) : 0.0f;
         }
     }
-    if (pp.wtc[l]) {   // [tap][chunk of 8 input channels][out channel][8], 32 -> 32 layers
-        const int n_t = 9 * 4 * 32 * 8;
+    {   // tensor-core layout [tap][chunk of 8 input channels][GEMM column][8], zero padded
+        const int kch = TC_KCH(l), nco = TC_NCO(l);
+        const int n_t = (int)tc_count(l);
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_t; i += gridDim.x * blockDim.x) {
-            const int k = i % 8, o = (i / 8) % 32, ch = (i / 256) % 4, t = i / 1024;
-            const float v = w[((size_t)o * ci + ch * 8 + k) * 9 + t];
+            const int k = i % 8, o = (i / 8) % nco, ch = (i / (8 * nco)) % kch, t = i / (8 * nco * kch);
+            const int c = ch * 8 + k;
+            const float v = (o < co && c < ci) ? w[((size_t)o * ci + c) * 9 + t] : 0.0f;
             pp.wtc[l][i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
         }
     }
@@ -499,7 +507,18 @@ head_kernel(const float *__restrict__ z, const float *__restrict__ E, int npix, 
         const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, d);
         key = o > key ? o : key;
     }
+    __shared__ float wm[EPI_THREADS / 32];
+    __shared__ unsigned long long wk[EPI_THREADS / 32];
     if ((threadIdx.x & 31) == 0) {
+        wm[threadIdx.x >> 5] = m;
+        wk[threadIdx.x >> 5] = key;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < EPI_THREADS / 32; ++w) {
+            m = fmaxf(m, wm[w]);
+            key = wk[w] > key ? wk[w] : key;
+        }
         atomicMax(rmax + f, __float_as_uint(m));
         atomicMax(peak + f, key);
     }
@@ -659,6 +678,7 @@ cudaError_t prepare_learn_kernels()
 // ------------------------------------------------------------ object ----
 struct pam_learn_s {
     pam_plan_s *plan = nullptr;   // owned: geometry, tables, time/lateral workspace
+    pam_plan_s *gemm = nullptr;   // owned, with tensor cores on: BF16 form for the band energies
     int F = 0, H = 0, W = 0, HP = 0, WP = 0, tiles = 0, rpt = 0, n_sms = 0;
     size_t npix = 0, ppix = 0;    // nz*nx, (nz+2)*(nx+2)
     float gate_tol = 0.05f;
@@ -728,6 +748,7 @@ void learn_free(pam_learn_s *l)
     fr(l->emax); fr(l->rmax); fr(l->fmax_g); fr(l->fmax_x); fr(l->peak);
     fr(l->frames); fr(l->items_gate); fr(l->items_all); fr(l->items_fb); fr(l->counters);
     fr(l->gate_err); fr(l->gate_pass);
+    if (l->gemm) pam_destroy(l->gemm);
     if (l->plan) pam_destroy(l->plan);
     delete l;
 }
@@ -765,14 +786,19 @@ cudaError_t run_features(pam_learn_s *l, const float *rf, int n, uint4 *feat, cu
     pam::reset_kernel<<<(n + 127) / 128, 128, 0, st>>>(l->emax, l->rmax, l->peak, n);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = pam::launch_time_fft(p, rf, n, st)) != cudaSuccess) return e;
-    if ((e = pam::launch_lateral(p, n, 1, p.t.ones, st)) != cudaSuccess) return e;
-    if ((e = pam::launch_prop_bands(p, n, pam::N_BANDS, l->bands, st)) != cudaSuccess) return e;
+    if (l->use_tc && l->gemm) {
+        // tensor-core form: sum_k |p_1 + p_2 + p_3|^2 per band from the same spectra
+        if ((e = pam::launch_prec_bands(*l->gemm, p.w.S, n, pam::N_BANDS, l->bands, st)) != cudaSuccess) return e;
+    } else {
+        if ((e = pam::launch_lateral(p, n, 1, p.t.ones, st)) != cudaSuccess) return e;
+        if ((e = pam::launch_prop_bands(p, n, pam::N_BANDS, l->bands, st)) != cudaSuccess) return e;
+    }
     dim3 g1(epi_grid(l->npix), n);
     pam::energy_kernel<<<g1, pam::EPI_THREADS, 0, st>>>(l->bands, (int)l->npix, l->E, l->emax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 g2(epi_grid(l->ppix), n);
     pam::features_kernel<<<g2, pam::EPI_THREADS, 0, st>>>(l->bands, l->E, l->emax, l->H, l->W, feat);
-    l->kernels += 6;
+    l->kernels += (l->use_tc && l->gemm) ? 7 : 6;
     return cudaGetLastError();
 }
 
@@ -783,18 +809,25 @@ cudaError_t run_forward(pam_learn_s *l, const uint4 *feat, int n, bool keep, cud
     const int H = l->H, W = l->W;
     cudaError_t e;
     uint4 *a[4] = {l->act[0], l->act[1], keep ? l->act[2] : l->act[0], keep ? l->act[3] : l->act[1]};
+    if (l->use_tc) {
+        auto wt = [&](int k) { return reinterpret_cast<const uint4 *>(l->prep.wtc[k]); };
+        int *status = l->plan->w.status;
+        if ((e = pam::launch_conv_tc(0, feat, wt(0), l->prep.bias[0], a[0], n, H, status, st)) != cudaSuccess)
+            return e;
+        for (int k = 1; k < 4; ++k)
+            if ((e = pam::launch_conv_tc(k, a[k - 1], wt(k), l->prep.bias[k], a[k], n, H, status, st)) != cudaSuccess)
+                return e;
+        e = pam::launch_conv_tc(4, a[3], wt(4), l->prep.bias[4], l->z, n, H, status, st);
+        l->kernels += 5;
+        return e;
+    }
     if ((e = pam::conv_cc<1, 32, pam::EPI_RELU>(feat, l->prep.wf[0], l->prep.bias[0], nullptr, a[0], n, H, W, st)) !=
         cudaSuccess)
         return e;
-    for (int k = 1; k < 4; ++k) {
-        if (l->use_tc)
-            e = pam::launch_conv_tc(a[k - 1], reinterpret_cast<const uint4 *>(l->prep.wtc[k]), l->prep.bias[k], a[k],
-                                    n, H, l->plan->w.status, st);
-        else
-            e = pam::conv_cc<4, 32, pam::EPI_RELU>(a[k - 1], l->prep.wf[k], l->prep.bias[k], nullptr, a[k], n, H, W,
-                                                   st);
-        if (e != cudaSuccess) return e;
-    }
+    for (int k = 1; k < 4; ++k)
+        if ((e = pam::conv_cc<4, 32, pam::EPI_RELU>(a[k - 1], l->prep.wf[k], l->prep.bias[k], nullptr, a[k], n, H, W,
+                                                    st)) != cudaSuccess)
+            return e;
     e = pam::conv_cc<4, 1, pam::EPI_F32>(a[3], l->prep.wf[4], l->prep.bias[4], nullptr, l->z, n, H, W, st);
     l->kernels += 5;
     return e;
@@ -911,7 +944,7 @@ pam_status pam_learn_create(const pam_plan_desc *d, pam_learn_t *out)
     }
     prep_n += 4 * NL;   // float4 alignment slack
     LALLOC(zalloc(&l->prep_mem, prep_n));
-    LALLOC(zalloc(&l->tc_mem, (size_t)3 * 9 * 4 * 32 * 8));
+    LALLOC(zalloc(&l->tc_mem, pam::tc_offset(NL)));
     {
         float *q = l->prep_mem;
         auto take = [&](size_t n) { float *r = q; q += (n + 3) / 4 * 4; return r; };
@@ -919,7 +952,7 @@ pam_status pam_learn_create(const pam_plan_desc *d, pam_learn_t *out)
             l->prep.wf[k] = take((size_t)CINC(k) * 8 * 9 * COUT(k));
             l->prep.wb[k] = k >= 1 ? take((size_t)((COUT(k) + 7) / 8 * 8) * 9 * CIN(k)) : nullptr;
             l->prep.bias[k] = take(COUT(k));
-            l->prep.wtc[k] = (k >= 1 && k <= 3) ? l->tc_mem + (size_t)(k - 1) * 9 * 4 * 32 * 8 : nullptr;
+            l->prep.wtc[k] = l->tc_mem + pam::tc_offset(k);
         }
     }
     LALLOC(zalloc(&l->feat, F * l->ppix));
@@ -1012,6 +1045,16 @@ pam_status pam_learn_configure(pam_learn_t l, float gate_tol, int use_tensor_cor
     if (std::isnan(gate_tol)) return lfail(PAM_ERR_INVALID_ARG, "gate_tol is NaN");
     if (use_tensor_cores && l->W != 128)
         return lfail(PAM_ERR_UNSUPPORTED, "the tensor-core convolution is built for nx == 128");
+    if (use_tensor_cores && !l->gemm) {
+        // the band energies' tensor-core form: a BF16 plan of the same geometry
+        pam_plan_desc d = l->plan->d;
+        d.bins = l->plan->bins.data();
+        d.n_bins = (int)l->plan->bins.size();
+        d.apod = l->plan->apod.data();
+        d.flags = (d.flags & PAM_EVANESCENT_ZERO) | PAM_FORM_GEMM_BF16;
+        pam_status s = pam_plan_create(&d, &l->gemm);
+        if (s != PAM_OK) return s;
+    }
     l->gate_tol = gate_tol;
     l->use_tc = use_tensor_cores != 0;
     return PAM_OK;

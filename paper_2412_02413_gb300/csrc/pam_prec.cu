@@ -336,13 +336,18 @@ size_t gemm_smem(int K, bool split)
 }
 
 // steps: element block of K step st in bits 4 (st % 16) of steps[st / 16].
-template <int NAP, bool FP16, bool SPLIT>
+// BANDS: instead of the per-aperture sums, fold the full-aperture energy
+// |p_1 + p_2 + p_3|^2 (Eq. 3 with apodizations that sum to one) and write it
+// out per band of bins: band k = bins [n_bins k / n_bands, n_bins (k+1) / n_bands),
+// to part[frame][k][nz][nx].
+template <int NAP, bool FP16, bool SPLIT, bool BANDS = false>
 __global__ void __launch_bounds__(gemm_threads<NAP>(), 1)
 prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ clo, const uint8_t *__restrict__ Bhi,
                  const uint8_t *__restrict__ Blo, ulonglong2 steps, int4 kq, int n_bins, int nz, int F, int NST,
-                 const unsigned *__restrict__ smax, float *__restrict__ part, int *__restrict__ status)
+                 const unsigned *__restrict__ smax, float *__restrict__ part, int *__restrict__ status, int n_bands)
 {
-    constexpr int NACC = NAP == 2 ? 3 : 6;
+    static_assert(!BANDS || NAP == 3, "band energies fold three apertures");
+    constexpr int NACC = BANDS ? 1 : (NAP == 2 ? 3 : 6);
     constexpr int NPART = SPLIT ? 2 : 1;
     constexpr int ACC_COLS = NAP * NG;
     constexpr unsigned TMEM_ALLOC = 2 * ACC_COLS <= 256 ? 256u : 512u;
@@ -389,10 +394,13 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
     // copy / MMA warpgroup (warps 0-3) drops to REG_CTRL, the two build/fold warpgroups rise
     // to REG_FOLD (2 x 128 x REG_FOLD + 128 x REG_CTRL <= 64512). The host checks
     // that the kernel was built with 168 registers per thread before launching.
-    if (warp < 4)
-        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(REG_CTRL));
-    else
-        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(REG_FOLD));
+    // The band form keeps one sum per pixel and frame and needs no split.
+    if constexpr (!BANDS) {
+        if (warp < 4)
+            asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(REG_CTRL));
+        else
+            asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(REG_FOLD));
+    }
 
     // Bounded wait that also gives up when another thread has aborted.
     auto wait = [&](uint64_t *bar, unsigned parity) -> bool {
@@ -544,17 +552,25 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                     const float2 ai = make_float2(im[0][2 * pp], im[0][2 * pp + 1]);
                     const float2 br = make_float2(re[1][2 * pp], re[1][2 * pp + 1]);
                     const float2 bi = make_float2(im[1][2 * pp], im[1][2 * pp + 1]);
-                    A[0] = __ffma2_rn(ar, ar, __ffma2_rn(ai, ai, A[0]));
-                    A[1] = __ffma2_rn(br, br, __ffma2_rn(bi, bi, A[1]));
-                    if constexpr (NAP == 2) {
-                        A[2] = __ffma2_rn(ar, br, __ffma2_rn(ai, bi, A[2]));
-                    } else {
+                    if constexpr (BANDS) {
                         const float2 cr = make_float2(re[2][2 * pp], re[2][2 * pp + 1]);
                         const float2 ci = make_float2(im[2][2 * pp], im[2][2 * pp + 1]);
-                        A[2] = __ffma2_rn(cr, cr, __ffma2_rn(ci, ci, A[2]));
-                        A[3] = __ffma2_rn(ar, br, __ffma2_rn(ai, bi, A[3]));
-                        A[4] = __ffma2_rn(br, cr, __ffma2_rn(bi, ci, A[4]));
-                        A[5] = __ffma2_rn(cr, ar, __ffma2_rn(ci, ai, A[5]));
+                        const float2 sr = make_float2(ar.x + br.x + cr.x, ar.y + br.y + cr.y);
+                        const float2 si = make_float2(ai.x + bi.x + ci.x, ai.y + bi.y + ci.y);
+                        A[0] = __ffma2_rn(sr, sr, __ffma2_rn(si, si, A[0]));
+                    } else {
+                        A[0] = __ffma2_rn(ar, ar, __ffma2_rn(ai, ai, A[0]));
+                        A[1] = __ffma2_rn(br, br, __ffma2_rn(bi, bi, A[1]));
+                        if constexpr (NAP == 2) {
+                            A[2] = __ffma2_rn(ar, br, __ffma2_rn(ai, bi, A[2]));
+                        } else {
+                            const float2 cr = make_float2(re[2][2 * pp], re[2][2 * pp + 1]);
+                            const float2 ci = make_float2(im[2][2 * pp], im[2][2 * pp + 1]);
+                            A[2] = __ffma2_rn(cr, cr, __ffma2_rn(ci, ci, A[2]));
+                            A[3] = __ffma2_rn(ar, br, __ffma2_rn(ai, bi, A[3]));
+                            A[4] = __ffma2_rn(br, cr, __ffma2_rn(bi, ci, A[4]));
+                            A[5] = __ffma2_rn(cr, ar, __ffma2_rn(ci, ai, A[5]));
+                        }
                     }
                 }
             }
@@ -569,15 +585,36 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
         // fold of bin b-1 to release its accumulator set. Building bin b+2 reuses
         // the stage of bin b+2-NST (NST >= 2), whose MMAs are done once fold(b)
         // has seen bin b's accumulators.
+        const size_t npix = (size_t)nz * NXP;
+        int band = 0;
+        // write the band sums of this warp's frames and restart them
+        auto flush = [&]() {
+#pragma unroll
+            for (int f = 0; f < FW; ++f) {
+                const int fr = grp * FG + fh * FW + f;
+                if (fr < F) {
+                    const float s2 = ldexpf(1.0f, 2 * frame_exp(smax[fr]));
+                    const float v = (f & 1) ? acc[f >> 1][0].y : acc[f >> 1][0].x;
+                    part[((size_t)fr * n_bands + band) * npix + (size_t)j * NXP + i_epi] = v * s2;
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < FW / 2; ++f) acc[f][0] = make_float2(0.f, 0.f);
+        };
         bool ok = n_bins == 0 || build(0);
         if (ok && n_bins > 1) ok = build(1);
         for (int b = 0; b < n_bins && ok; ++b) {
             if (!fold(b)) ok = false;                            // tensor core: MMA(b+1)
             if (ok && b + 2 < n_bins && !build(b + 2)) ok = false;
+            if constexpr (BANDS) {
+                if (ok && b + 1 == (int)(((long long)n_bins * (band + 1)) / n_bands)) {
+                    flush();
+                    ++band;
+                }
+            }
         }
-        const size_t npix = (size_t)nz * NXP;
 #pragma unroll
-        for (int f = 0; f < FW; ++f) {
+        for (int f = 0; f < (BANDS ? 0 : FW); ++f) {
             const int fr = grp * FG + fh * FW + f;
             if (fr < F && ok) {
                 const float s2 = ldexpf(1.0f, 2 * frame_exp(smax[fr]));
@@ -612,7 +649,36 @@ cudaError_t launch_gemm_t(const pam_plan_s &p, int n_frames, cudaStream_t st)
     }
     prec_gemm_kernel<NAP, FP16, SPLIT><<<grid, gemm_threads<NAP>(), gemm_smem(p.K, SPLIT), st>>>(
         p.t.c_hi, p.t.c_lo, reinterpret_cast<const uint8_t *>(p.w.Bhi), reinterpret_cast<const uint8_t *>(p.w.Blo),
-        steps, kq, p.n_bins, p.nz, n_frames, gemm_stages(p.K, SPLIT), p.w.smax, p.w.part, p.w.status);
+        steps, kq, p.n_bins, p.nz, n_frames, gemm_stages(p.K, SPLIT), p.w.smax, p.w.part, p.w.status, 0);
+    return cudaGetLastError();
+}
+
+// Per-band full-aperture energies of BF16 or FP16 form (no split): operand
+// packing from the spectra S [F][n_bins][n_elem] and the BANDS GEMM.
+template <bool FP16>
+cudaError_t launch_bands_form(const pam_plan_s &p, const float2 *S, int n_frames, int n_bands, float *bands,
+                              cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(p.w.smax, 0, sizeof(unsigned) * n_frames, st);
+    if (e != cudaSuccess) return e;
+    prec_smax_kernel<<<dim3(p.n_bins, n_frames), 128, 0, st>>>(S, p.n_bins, p.ne, p.w.smax);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int groups = (n_frames + FG - 1) / FG;
+    prec_bprep_kernel<FP16, false><<<dim3(p.n_bins, groups), 256, 0, st>>>(
+        S, p.t.ktab, p.t.kwgt, p.K, p.n_bins, p.ne, n_frames, p.w.smax, reinterpret_cast<uint8_t *>(p.w.Bhi),
+        nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (gemm_stages(p.K, false) < 2 || p.K / 16 > 32) return cudaErrorInvalidConfiguration;
+    const int4 kq = make_int4(p.kq[0], p.kq[1], p.kq[2], p.kq[3]);
+    ulonglong2 steps = make_ulonglong2(0ull, 0ull);
+    for (int s = 0; s < p.K / 16; ++s) {
+        const unsigned long long m = (unsigned long long)((p.ktab_h[(size_t)16 * s] & 0x3FFF) >> 3) & 15ull;
+        if (s < 16) steps.x |= m << (4 * s);
+        else steps.y |= m << (4 * (s - 16));
+    }
+    prec_gemm_kernel<3, FP16, false, true><<<dim3(p.nz, groups), gemm_threads<3>(), gemm_smem(p.K, false), st>>>(
+        p.t.c_hi, nullptr, reinterpret_cast<const uint8_t *>(p.w.Bhi), nullptr, steps, kq, p.n_bins, p.nz, n_frames,
+        gemm_stages(p.K, false), p.w.smax, bands, p.w.status, n_bands);
     return cudaGetLastError();
 }
 
@@ -631,17 +697,17 @@ cudaError_t launch_form(const pam_plan_s &p, int n_frames, cudaStream_t st)
     return p.n_apod == 2 ? launch_gemm_t<2, FP16, SPLIT>(p, n_frames, st) : launch_gemm_t<3, FP16, SPLIT>(p, n_frames, st);
 }
 
-template <int NAP, bool FP16, bool SPLIT>
+template <int NAP, bool FP16, bool SPLIT, bool BANDS = false>
 cudaError_t set_gemm_smem()
 {
     static_assert(MAX_NST >= 2, "the copy ring needs two stages");
-    cudaError_t e = cudaFuncSetAttribute(prec_gemm_kernel<NAP, FP16, SPLIT>,
+    cudaError_t e = cudaFuncSetAttribute(prec_gemm_kernel<NAP, FP16, SPLIT, BANDS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM_LIMIT);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess || BANDS) return e;
     // The register split (setmaxnreg) is sized for a launch of exactly REG_LAUNCH
     // registers per thread; with fewer, the increase could never be granted.
     cudaFuncAttributes a;
-    if ((e = cudaFuncGetAttributes(&a, prec_gemm_kernel<NAP, FP16, SPLIT>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&a, prec_gemm_kernel<NAP, FP16, SPLIT, BANDS>)) != cudaSuccess) return e;
     return a.numRegs == REG_LAUNCH ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
@@ -669,6 +735,17 @@ cudaError_t launch_prec(const pam_plan_s &p, int n_frames, cudaStream_t st)
 
 int prec_kernels() { return 3; }
 
+cudaError_t launch_prec_bands(const pam_plan_s &p, const float2 *S, int n_frames, int n_bands, float *bands,
+                              cudaStream_t st)
+{
+    if (p.n_apod != 3 || n_bands < 1 || n_bands > p.n_bins) return cudaErrorInvalidValue;
+    switch (p.form) {
+    case PAM_FORM_GEMM_BF16: return launch_bands_form<false>(p, S, n_frames, n_bands, bands, st);
+    case PAM_FORM_GEMM_FP16: return launch_bands_form<true>(p, S, n_frames, n_bands, bands, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t prepare_prec_kernels()
 {
     cudaError_t e;
@@ -677,6 +754,8 @@ cudaError_t prepare_prec_kernels()
     if ((e = set_gemm_smem<2, true, false>()) != cudaSuccess) return e;
     if ((e = set_gemm_smem<3, true, false>()) != cudaSuccess) return e;
     if ((e = set_gemm_smem<2, false, true>()) != cudaSuccess) return e;
+    if ((e = set_gemm_smem<3, false, false, true>()) != cudaSuccess) return e;
+    if ((e = set_gemm_smem<3, true, false, true>()) != cudaSuccess) return e;
     return set_gemm_smem<3, false, true>();
 }
 

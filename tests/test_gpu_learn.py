@@ -218,6 +218,34 @@ def test_example_features_and_target_match_oracle():
     L.close()
 
 
+def test_tensor_core_band_energies_match_oracle():
+    """With tensor cores on, the band energies come from the BF16 GEMM form:
+    relative error about 6e-4, below the BF16 rounding of the features."""
+    w = synth.workload(2)
+    w.nz = 40
+    rf, _ = synth.make_frame(w, 5)
+    pam = _pam()
+    L = pam.Learned.from_workload(w, max_frames=1)
+    L.configure(tensor_cores=True)
+    feats, _, en = L.example(torch.from_numpy(rf[None]).cuda(), target=False, energy=True)
+    got = pam.unpack_features(feats, w.nz, w.n_elem)[0]
+    bins = w.bins()
+    nb = len(bins)
+    g = oracle.Geometry(w.n_elem, w.nt, w.fs, w.c, w.pitch, w.nz, w.z0, w.dz, bins)
+    e_full = oracle.as_backprop(g, rf)
+    e_bands = []
+    for b in range(4):
+        gb = oracle.Geometry(w.n_elem, w.nt, w.fs, w.c, w.pitch, w.nz, w.z0, w.dz, bins[nb * b // 4: nb * (b + 1) // 4])
+        e_bands.append(oracle.as_backprop(gb, rf))
+    err = rel_l2(en[0].cpu().numpy(), e_full)
+    print(f"tensor-core band energies: rel L2 of E {err:.2e}")
+    assert err <= 2e-3
+    want = co.features(np.stack(e_bands))
+    # half a BF16 ulp plus the form's error through log10 (|d log10(x)| <= 2e-3 / ln 10 relative)
+    assert np.max(np.abs(got - want)) <= 5e-3
+    L.close()
+
+
 # --------------------------------------------------------------- the gate --
 def test_gate_closed_gives_the_plain_method():
     w = synth.workload(1)
