@@ -362,7 +362,8 @@ pam_status pam_learn_get_params(pam_learn_t l, float *params, size_t n);
  * frame through the exact path, +inf accepts every frame). use_tensor_cores: 1
  * runs every layer's forward on tcgen05 and the band energies in the BF16
  * tensor-core form (PAM_FORM_GEMM_BF16, relative error about 6e-4, below the
- * BF16 rounding of the features); nx == 128 with disjoint apertures only, else
+ * BF16 rounding of the features) when that form accepts the apertures (see
+ * PAM_FORM_GEMM_BF16), else on the FP32 path; nx == 128 only, else
  * PAM_ERR_UNSUPPORTED. The first call with 1 builds that form's tables (blocks).
  * 0 runs both on the FP32 path and CUDA cores (default). */
 pam_status pam_learn_configure(pam_learn_t l, float gate_tol, int use_tensor_cores);

@@ -1053,7 +1053,9 @@ pam_status pam_learn_configure(pam_learn_t l, float gate_tol, int use_tensor_cor
         d.apod = l->plan->apod.data();
         d.flags = (d.flags & PAM_EVANESCENT_ZERO) | PAM_FORM_GEMM_BF16;
         pam_status s = pam_plan_create(&d, &l->gemm);
-        if (s != PAM_OK) return s;
+        // apertures the form cannot pack keep the FP32 band energies
+        if (s == PAM_ERR_UNSUPPORTED) l->gemm = nullptr;
+        else if (s != PAM_OK) return s;
     }
     l->gate_tol = gate_tol;
     l->use_tc = use_tensor_cores != 0;
