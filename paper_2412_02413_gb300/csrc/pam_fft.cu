@@ -165,9 +165,7 @@ time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const 
 }
 
 // -------------------------------------------------------- lateral FFT ----
-// Q[f][b][q][u] = live[b][u] / nx * sum_e apod_q[e] S[f][b][e] exp(-2 pi i u e / nx),
-// stored as (Re, Re, Im, Im): the propagation multiplies it by a phasor as two
-// packed FP32x2 operations on these pairs.
+// Q[f][b][q][u] = live[b][u] / nx * sum_e apod_q[e] S[f][b][e] exp(-2 pi i u e / nx).
 // live_fs is the frame stride of the mask (0: one mask for all frames).
 // One CTA per (bin, frame): the napq apodized rows are transformed together
 // by the shared-memory FFT. The 1/nx of the inverse lateral transform is
@@ -177,7 +175,7 @@ constexpr int LAT_THREADS = 128;
 __global__ void __launch_bounds__(LAT_THREADS)
 lateral_kernel(const float2 *__restrict__ S, int ne, int nx, int log2nx, int n_bins, int napq,
                const float *__restrict__ apod, const float2 *__restrict__ twx, const float *__restrict__ live,
-               size_t live_fs, float4 *__restrict__ Q)
+               size_t live_fs, float2 *__restrict__ Q)
 {
     extern __shared__ __align__(16) float2 lbuf[];
     float2 *x = lbuf, *y = lbuf + napq * nx, *tws = lbuf + 2 * napq * nx;
@@ -193,12 +191,11 @@ lateral_kernel(const float2 *__restrict__ S, int ne, int nx, int log2nx, int n_b
     __syncthreads();
     const float2 *X = stockham(x, y, nx, log2nx, napq, tws, threadIdx.x, LAT_THREADS);
     const float inv_nx = 1.0f / (float)nx;
-    float4 *dst = Q + ((size_t)f * n_bins + b) * napq * nx;
+    float2 *dst = Q + ((size_t)f * n_bins + b) * napq * nx;
     for (int i = threadIdx.x; i < napq * nx; i += LAT_THREADS) {
         const int u = i & (nx - 1);
         const float l = live[(size_t)f * live_fs + (size_t)b * nx + u] * inv_nx;
-        const float re = X[i].x * l, im = X[i].y * l;
-        dst[i] = make_float4(re, re, im, im);
+        dst[i] = make_float2(X[i].x * l, X[i].y * l);
     }
 }
 

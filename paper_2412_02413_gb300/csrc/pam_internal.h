@@ -44,7 +44,7 @@ inline int n_acc(int n_apod) { return n_apod == 1 ? 1 : (n_apod == 2 ? 3 : 6); }
 // One frame of a batch (pam_batch_*): its spectra, phase table and geometry,
 // and the offset of its [nz][nx] maps in the packed outputs.
 struct BatchFrame {
-    const float4 *Q;        // [n_bins][napq][nx] as (Re, Re, Im, Im)
+    const float2 *Q;        // [n_bins][napq][nx]
     const uint4 *phase;     // [n_bins][nx]
     const int *bin_evan;    // [n_bins]
     int n_bins, nz, nx, nt;
@@ -54,7 +54,7 @@ struct BatchFrame {
 
 struct Workspace {
     float2 *S = nullptr;        // [max_frames][n_bins][n_elem]      selected time bins
-    float4 *Q = nullptr;        // [max_frames][n_bins][napq][nx]    apodized lateral spectra / nx, (Re, Re, Im, Im)
+    float2 *Q = nullptr;        // [max_frames][n_bins][napq][nx]    apodized lateral spectra / nx
     float *part = nullptr;      // [units][n_acc][nz][nx]            per-split accumulator partials
     size_t part_units = 0;
     float *rho_tmp = nullptr;   // [max_frames][nz][nx]              rho before normalisation
