@@ -64,6 +64,15 @@ typedef enum {
 
 /* descriptor flags */
 #define PAM_EVANESCENT_ZERO 0x1u /* drop components with kx^2 > (w/c)^2 instead of decaying them */
+/* 2x zero-stuffing in the channel direction before apodization and the lateral
+ * transform (Sec. II-D): a virtual array of 2 n_elem channels at pitch/2 whose
+ * channel 2e carries element e and channel 2e+1 is zero. Virtual channel v sits
+ * at x_v = (v - (2 n_elem - 1)/2) pitch/2 and is image column v, so nx = 2 n_elem
+ * (built: n_elem 8..64) and the pixel pitch is pitch/2. Apodizations stay per
+ * physical element (explicit or Pattern-m on the element index). Plain FP32
+ * path only: not with PAM_FORM_GEMM_*, batches, the learned form or
+ * pam_as_tax_static. */
+#define PAM_LATERAL_UPSAMPLE2X 0x2u
 /* Tensor-core form of the propagation (at most one of these; default = plain FP32 FFT path).
  * For a bin w_k and depth row z_j, the element-to-pixel propagator of Eq. 1-2 is circulant:
  *   p~(x_i, z_j) = sum_e c_j[(i - e) mod nx] a_q[e] S[e],
@@ -85,7 +94,8 @@ typedef struct {
     double fs_hz;         /* sampling rate (Hz), > 0 */
     double c_mps;         /* sound speed (m/s), > 0 */
     int n_samples;        /* samples per channel nt: a power of two, 64..8192 */
-    int nx;               /* lateral pixels = lateral DFT length; 0 or n_elem. Built: 16, 32, 64, 128 */
+    int nx;               /* lateral pixels = lateral DFT length: 0 or n_elem (2 n_elem with
+                             PAM_LATERAL_UPSAMPLE2X). Built: 16, 32, 64, 128 */
     int nz;               /* depth rows, 1..65535 */
     double z0_m;          /* depth of row 0 from the array face (m), >= 0 */
     double dz_m;          /* row spacing (m), > 0 */
@@ -97,7 +107,7 @@ typedef struct {
     const float *apod;    /* host [n_apod][n_elem] real weights, or NULL for Pattern-m */
     int pattern_m;        /* Pattern-m (Sec. II-A): element e in aperture q iff floor(e/m) mod n_apod == q */
     float eps;            /* NCC floor (Sec. II-A, usually 0.001), 0 < eps <= 1 */
-    unsigned flags;       /* PAM_EVANESCENT_ZERO, at most one PAM_FORM_GEMM_* */
+    unsigned flags;       /* PAM_EVANESCENT_ZERO, PAM_LATERAL_UPSAMPLE2X, at most one PAM_FORM_GEMM_* */
     int max_frames;       /* frames per kernel batch; larger calls run in batches of this size */
 } pam_plan_desc;
 

@@ -99,8 +99,12 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
                     "n_samples must be in [64, 8192]");
     if (!is_pow2(d->n_samples))
         return fail(PAM_ERR_UNSUPPORTED, "n_samples must be a power of two for the radix-4/2 time FFT");
-    int nx = d->nx == 0 ? d->n_elem : d->nx;
-    if (nx != d->n_elem) return fail(PAM_ERR_UNSUPPORTED, "nx must equal n_elem (lateral padding is not built)");
+    const bool up2 = (d->flags & PAM_LATERAL_UPSAMPLE2X) != 0;
+    const int nev = up2 ? 2 * d->n_elem : d->n_elem;
+    int nx = d->nx == 0 ? nev : d->nx;
+    if (nx != nev)
+        return fail(PAM_ERR_UNSUPPORTED, up2 ? "nx must be 2 n_elem with PAM_LATERAL_UPSAMPLE2X"
+                                             : "nx must equal n_elem (or 2 n_elem with PAM_LATERAL_UPSAMPLE2X)");
     if (nx != 16 && nx != 32 && nx != 64 && nx != 128)
         return fail(PAM_ERR_UNSUPPORTED, "lateral length nx must be 16, 32, 64 or 128");
     if (d->nz < 1 || d->nz > 65535) return fail(PAM_ERR_INVALID_ARG, "nz must be in [1, 65535]");
@@ -110,9 +114,11 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     if (!(d->eps > 0.0f) || !(d->eps <= 1.0f)) return fail(PAM_ERR_INVALID_ARG, "eps must be in (0, 1]");
     if (d->max_frames < 1 || d->max_frames > 65535) return fail(PAM_ERR_INVALID_ARG, "max_frames must be in [1, 65535]");
     const unsigned form_bits = PAM_FORM_GEMM_BF16 | PAM_FORM_GEMM_FP16 | PAM_FORM_GEMM_BF16_SPLIT;
-    if (d->flags & ~(PAM_EVANESCENT_ZERO | form_bits)) return fail(PAM_ERR_INVALID_ARG, "unknown flag bits");
+    if (d->flags & ~(PAM_EVANESCENT_ZERO | PAM_LATERAL_UPSAMPLE2X | form_bits))
+        return fail(PAM_ERR_INVALID_ARG, "unknown flag bits");
     const unsigned form = d->flags & form_bits;
     if (form & (form - 1)) return fail(PAM_ERR_INVALID_ARG, "at most one PAM_FORM_GEMM_* flag");
+    if (form && up2) return fail(PAM_ERR_UNSUPPORTED, "PAM_LATERAL_UPSAMPLE2X runs on the plain FP32 path only");
 
     const int nt = d->n_samples;
     p->bins.clear();
@@ -155,6 +161,8 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     p->d.nx = nx;
     p->d.n_bins = (int)p->bins.size();
     p->ne = ne;
+    p->nev = nev;
+    p->pitch_x = up2 ? 0.5 * d->pitch_m : d->pitch_m;
     p->nt = nt;
     p->log2nt = ilog2(nt);
     p->nx = nx;
@@ -200,7 +208,7 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
 
 pam_status alloc_plan(pam_plan_s *p)
 {
-    const size_t ne = p->ne, nx = p->nx, nb = p->n_bins, F = p->max_frames;
+    const size_t ne = p->nev, nx = p->nx, nb = p->n_bins, F = p->max_frames;   // ne: channels of S
     const size_t npix = (size_t)p->nz * nx;
     cudaError_t e = cudaSuccess;
 #define PAM_TRY(x)                                           \
@@ -250,7 +258,16 @@ pam_status alloc_plan(pam_plan_s *p)
     }
     PAM_TRY(cudaMemset(p->w.status, 0, sizeof(int)));
     PAM_TRY(cudaMemcpy(p->t.bins, p->bins.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
-    PAM_TRY(cudaMemcpy(p->t.apod, p->apod.data(), p->apod.size() * sizeof(float), cudaMemcpyHostToDevice));
+    {
+        // apodization per channel of S: element e's weight at channel e (or 2e when zero-stuffed)
+        const size_t step = (size_t)(p->nev / p->ne);
+        std::vector<float> av((size_t)p->n_apod * ne, 0.0f);
+        for (int q = 0; q < p->n_apod; ++q)
+            for (int e = 0; e < p->ne; ++e) av[(size_t)q * ne + step * e] = p->apod[(size_t)q * p->ne + e];
+        PAM_TRY(cudaMemcpy(p->t.apod, av.data(), av.size() * sizeof(float), cudaMemcpyHostToDevice));
+        // zero-stuffed channels are never written: clear them once
+        if (step > 1) PAM_TRY(cudaMemset(p->w.S, 0, F * nb * ne * sizeof(float2)));
+    }
     std::vector<float> ones(ne, 1.0f);
     PAM_TRY(cudaMemcpy(p->t.ones, ones.data(), ne * sizeof(float), cudaMemcpyHostToDevice));
 #undef PAM_TRY
@@ -423,7 +440,7 @@ pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod
     if ((s = check_dev_ptr(energy, "energy", true)) != PAM_OK) return s;
     if ((s = check_dev_ptr(fields, "fields", false)) != PAM_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const float *apod = apod_index < 0 ? p->t.ones : p->t.apod + (size_t)apod_index * p->ne;
+    const float *apod = apod_index < 0 ? p->t.ones : p->t.apod + (size_t)apod_index * p->nev;
     const size_t npix = (size_t)p->nz * p->nx;
     const size_t fr_in = (size_t)p->ne * p->nt;
     for (int f0 = 0; f0 < n_frames; f0 += p->max_frames) {

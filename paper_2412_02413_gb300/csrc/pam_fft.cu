@@ -136,13 +136,14 @@ __device__ float2 *stockham(float2 *x, float2 *y, int n, int log2n, int batch, c
 // memory. The two half-length spectra are then separated:
 //   E[k] = (Z[k] + conj Z[M-k]) / 2,  O[k] = (Z[k] - conj Z[M-k]) / (2i),
 //   X[k] = E[k] + exp(-2 pi i k / nt) O[k].
-// Only the selected bins leave the CTA, as S[f][b][e]. Block (0, f) also
-// clears the frame's rho maximum for the epilogue.
+// Only the selected bins leave the CTA, as S[f][b][c] with c = e, or c = 2e
+// when the channels are zero-stuffed (nev = 2 ne). Block (0, f) also clears
+// the frame's rho maximum for the epilogue.
 constexpr int TFFT_THREADS = 256;
 
 __global__ void __launch_bounds__(TFFT_THREADS)
 time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const float2 *__restrict__ tw,
-                const int *__restrict__ bins, int n_bins, float2 *__restrict__ S, unsigned *__restrict__ fmax)
+                const int *__restrict__ bins, int n_bins, float2 *__restrict__ S, int nev, unsigned *__restrict__ fmax)
 {
     extern __shared__ __align__(16) float2 sbuf[];
     const int M = nt >> 1;
@@ -160,7 +161,7 @@ time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const 
         const float2 zk = Z[k], zm = Z[M - k];
         const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        S[((size_t)f * n_bins + b) * ne + e] = cadd(E, cmul(tw[k], O));
+        S[((size_t)f * n_bins + b) * nev + (size_t)e * (nev / ne)] = cadd(E, cmul(tw[k], O));
     }
 }
 
@@ -219,7 +220,7 @@ cudaError_t launch_tables(const pam_plan_s &p, cudaStream_t st)
     int n = p.n_bins * p.nx;
     if (p.nt > n) n = p.nt;
     int blocks = (n + 255) / 256;
-    tables_kernel<<<blocks, 256, 0, st>>>(p.t.bins, p.n_bins, p.nx, p.nt, p.d.fs_hz, p.d.c_mps, p.d.pitch_m,
+    tables_kernel<<<blocks, 256, 0, st>>>(p.t.bins, p.n_bins, p.nx, p.nt, p.d.fs_hz, p.d.c_mps, p.pitch_x,
                                           p.d.z0_m, p.d.dz_m, (p.d.flags & PAM_EVANESCENT_ZERO) ? 1 : 0,
                                           p.t.phase, p.t.live, p.t.bin_evan, p.t.tw_t, p.t.tw_x);
     return cudaGetLastError();
@@ -229,14 +230,14 @@ cudaError_t launch_time_fft(const pam_plan_s &p, const float *rf, int n_frames, 
 {
     dim3 grid(p.ne, n_frames);
     time_fft_kernel<<<grid, TFFT_THREADS, time_fft_smem(p.nt), st>>>(rf, p.ne, p.nt, ilog2i(p.nt), p.t.tw_t,
-                                                                      p.t.bins, p.n_bins, p.w.S, p.w.fmax);
+                                                                      p.t.bins, p.n_bins, p.w.S, p.nev, p.w.fmax);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lateral(const pam_plan_s &p, int n_frames, int napq, const float *apod, cudaStream_t st)
 {
     dim3 grid(p.n_bins, n_frames);
-    lateral_kernel<<<grid, LAT_THREADS, lateral_smem(p.nx, napq), st>>>(p.w.S, p.ne, p.nx, ilog2i(p.nx), p.n_bins,
+    lateral_kernel<<<grid, LAT_THREADS, lateral_smem(p.nx, napq), st>>>(p.w.S, p.nev, p.nx, ilog2i(p.nx), p.n_bins,
                                                                         napq, apod, p.t.tw_x, p.t.live, 0, p.w.Q);
     return cudaGetLastError();
 }
@@ -245,7 +246,7 @@ cudaError_t launch_lateral_frames(const pam_plan_s &p, int n_frames, int napq, c
                                   const float *live, size_t live_fs, cudaStream_t st)
 {
     dim3 grid(p.n_bins, n_frames);
-    lateral_kernel<<<grid, LAT_THREADS, lateral_smem(p.nx, napq), st>>>(p.w.S, p.ne, p.nx, ilog2i(p.nx), p.n_bins,
+    lateral_kernel<<<grid, LAT_THREADS, lateral_smem(p.nx, napq), st>>>(p.w.S, p.nev, p.nx, ilog2i(p.nx), p.n_bins,
                                                                         napq, apod, p.t.tw_x, live, live_fs, p.w.Q);
     return cudaGetLastError();
 }
@@ -257,7 +258,7 @@ cudaError_t launch_tables_frame(const pam_plan_s &p, const int *bins, int n_bins
     if (e != cudaSuccess) return e;
     int n = n_bins * p.nx;
     if (nt > n) n = nt;
-    tables_kernel<<<(n + 255) / 256, 256, 0, st>>>(bins, n_bins, p.nx, nt, p.d.fs_hz, p.d.c_mps, p.d.pitch_m,
+    tables_kernel<<<(n + 255) / 256, 256, 0, st>>>(bins, n_bins, p.nx, nt, p.d.fs_hz, p.d.c_mps, p.pitch_x,
                                                     p.d.z0_m, p.d.dz_m, (p.d.flags & PAM_EVANESCENT_ZERO) ? 1 : 0,
                                                     phase, live, bin_evan, tw_t, p.t.tw_x);
     return cudaGetLastError();

@@ -95,6 +95,8 @@ struct pam_plan_s {
     pam_plan_desc d{};
     int device = 0, num_sms = 0;
     int ne = 0, nt = 0, log2nt = 0, nx = 0, nz = 0, n_bins = 0, n_apod = 0, max_frames = 1;
+    int nev = 0;                       // channels of S and of the lateral DFT: ne, or 2 ne zero-stuffed
+    double pitch_x = 0.0;              // their spacing: pitch, or pitch / 2
     std::vector<int> bins;
     std::vector<float> apod;
     pam::Tables t;

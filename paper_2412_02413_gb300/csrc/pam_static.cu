@@ -175,6 +175,8 @@ extern "C" pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf,
     p.d.nx = nx;
     p.d.n_bins = nb;
     p.ne = ne;
+    p.nev = ne;
+    p.pitch_x = d->pitch_m;
     p.nt = nt;
     p.nx = nx;
     p.nz = nz;

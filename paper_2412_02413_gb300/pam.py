@@ -19,6 +19,7 @@ from . import build as _build
 
 PAM_OK = 0
 PAM_EVANESCENT_ZERO = 0x1
+PAM_LATERAL_UPSAMPLE2X = 0x2
 # tensor-core forms of the propagation (include/pam.h PAM_FORM_GEMM_*)
 FORMS = {"fp32": 0x0, "bf16": 0x10, "fp16": 0x20, "bf16split": 0x40}
 _STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_UNSUPPORTED", 3: "PAM_ERR_OOM",
@@ -149,7 +150,7 @@ def _dptr(t) -> Optional[int]:
 
 
 def _make_desc(n_elem, pitch, fs, c, n_samples, nz, z0, dz, bins=None, f_lo=0.0, f_hi=0.0, n_apod=3, apod=None,
-               pattern_m=16, eps=1e-3, evanescent_zero=False, max_frames=1, nx=0, form="fp32"):
+               pattern_m=16, eps=1e-3, evanescent_zero=False, max_frames=1, nx=0, form="fp32", upsample2x=False):
     """A filled ``pam_plan_desc`` and the host arrays it points to (keep them alive)."""
     L = load()
     d = PlanDesc()
@@ -169,7 +170,8 @@ def _make_desc(n_elem, pitch, fs, c, n_samples, nz, z0, dz, bins=None, f_lo=0.0,
     d.pattern_m, d.eps = int(pattern_m), float(eps)
     if form not in FORMS:
         raise ValueError(f"form must be one of {sorted(FORMS)}")
-    d.flags = (PAM_EVANESCENT_ZERO if evanescent_zero else 0) | FORMS[form]
+    d.flags = (PAM_EVANESCENT_ZERO if evanescent_zero else 0) | FORMS[form] | \
+        (PAM_LATERAL_UPSAMPLE2X if upsample2x else 0)
     d.max_frames = int(max_frames)
     return d, bins_keep, apod_keep
 
@@ -184,17 +186,18 @@ class Plan:
     def __init__(self, n_elem: int, pitch: float, fs: float, c: float, n_samples: int, nz: int,
                  z0: float, dz: float, bins: Optional[Sequence[int]] = None, f_lo: float = 0.0,
                  f_hi: float = 0.0, n_apod: int = 3, apod=None, pattern_m: int = 16, eps: float = 1e-3,
-                 evanescent_zero: bool = False, max_frames: int = 1, nx: int = 0, form: str = "fp32"):
+                 evanescent_zero: bool = False, max_frames: int = 1, nx: int = 0, form: str = "fp32",
+                 upsample2x: bool = False):
         _require_cuda()
         L = load()
         d, self._bins_keep, self._apod_keep = _make_desc(
             n_elem, pitch, fs, c, n_samples, nz, z0, dz, bins, f_lo, f_hi, n_apod, apod, pattern_m, eps,
-            evanescent_zero, max_frames, nx, form)
+            evanescent_zero, max_frames, nx, form, upsample2x)
         h = _VP()
         _check(L.pam_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
         self.n_elem, self.n_samples, self.nz, self.n_apod = int(n_elem), int(n_samples), int(nz), int(n_apod)
-        self.nx = self.n_elem if not nx else int(nx)
+        self.nx = (2 if upsample2x else 1) * self.n_elem if not nx else int(nx)
         self.max_frames = int(max_frames)
         self.form = form
         self.bins = self._query_bins()

@@ -271,6 +271,28 @@ def test_gate_closed_gives_the_plain_method():
     L.close()
 
 
+def test_learned_call_larger_than_the_batch():
+    """A call of 5 frames on a learned form built for 2 runs in batches of 2;
+    with the gate closed every frame equals the plain method."""
+    w = synth.workload(1)
+    w.nz = 24
+    pam = _pam()
+    L = pam.Learned.from_workload(w, max_frames=2)
+    L.set_params(flat(rand_params(14)))
+    L.configure(gate_tol=-1.0)
+    rf = torch.from_numpy(np.stack([synth.make_frame(w, 40 + i)[0] for i in range(5)])).cuda()
+    out = L.as_tax(rf)
+    plan = pam.Plan.from_workload(w, max_frames=5)
+    plan.set_split(1)
+    ref = plan.as_tax(rf, rho_n=True)
+    torch.cuda.synchronize()
+    assert out["gate_pass"].cpu().numpy().tolist() == [0] * 5
+    for f in range(5):
+        assert rel_l2(out["image"][f].cpu().numpy(), ref["image"][f].cpu().numpy()) <= 1e-6
+    plan.close()
+    L.close()
+
+
 def test_gate_open_gives_the_network_image():
     w = synth.workload(1)
     w.nz = 40

@@ -199,6 +199,50 @@ def test_evanescent_zero_parity():
     compare_xcorr(out, orc, check_peak=False)
 
 
+def _zero_stuffed(w, rf, apod):
+    """Oracle inputs for 2x zero-stuffing in the channel direction (Sec. II-D):
+    2 n_elem channels at pitch/2, element e on channel 2e, odd channels zero,
+    and each aperture's weight of element e on channel 2e."""
+    ne = w.n_elem
+    rf2 = np.zeros((2 * ne, rf.shape[-1]), np.float32)
+    rf2[0::2] = rf
+    a2 = np.zeros((apod.shape[0], 2 * ne))
+    a2[:, 0::2] = apod
+    dz = w.dz if w.nz > 1 else (w.z_last - w.z_first)
+    g = oracle.Geometry(2 * ne, w.nt, w.fs, w.c, w.pitch / 2, w.nz, w.z0, dz, w.bins())
+    return g, rf2, a2
+
+
+@pytest.mark.parametrize("ne,nt,nz", [(16, 256, 21), (64, 1024, 40)])
+def test_lateral_upsample2x_parity(ne, nt, nz):
+    w = _tiny(ne, nt, nz, pattern_m=4 if ne == 16 else 8)
+    w.source_z = (w.z0, w.z0 + (nz - 1) * w.dz)
+    rf = synth.make_frame(w, 3)[0] if ne == 64 else synth.random_rf(ne, nt, seed=31)
+    plan = _plan(w, upsample2x=True)
+    assert plan.nx == 2 * ne
+    out = _run_tax(plan, rf)
+    apod = oracle.pattern(ne, 3, w.pattern_m)
+    g, rf2, a2 = _zero_stuffed(w, rf, apod)
+    orc = oracle.as_tax(g, rf2, a2)
+    compare_xcorr(out, orc, check_peak=(ne == 64))
+    # the full-aperture back-propagation on the same virtual array
+    e = plan.as_backprop(torch.from_numpy(np.ascontiguousarray(rf)).cuda())
+    want = oracle.as_backprop(g, rf2, np.where(np.arange(2 * ne) % 2 == 0, 1.0, 0.0))
+    assert rel_l2(e[0].cpu().numpy(), want) <= REL_L2_TOL
+    plan.close()
+
+
+def test_lateral_upsample2x_rejections():
+    pam = _pam()
+    w = _tiny(16, 256, 8)
+    with pytest.raises(pam.PamError):          # nx = 2 n_elem = 256 is not built
+        _plan(_tiny(128, 256, 8), upsample2x=True)
+    with pytest.raises(pam.PamError):          # tensor-core forms run without it
+        _plan(_tiny(64, 256, 8), upsample2x=True, form="bf16")
+    with pytest.raises(pam.PamError):          # nx must be 2 n_elem
+        _plan(w, upsample2x=True, nx=16)
+
+
 def test_identical_apertures_give_unit_ncc():
     w = _tiny(64, 512, 40)
     rf = synth.random_rf(64, 512, seed=22)
