@@ -549,7 +549,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched plain / tensor-core forms")
     ap.add_argument("--batch", type=int, default=64, help="frames per call of the batched forms")
     ap.add_argument("--batch-steps", type=int, default=20)
-    ap.add_argument("--forms", default="fp32,bf16,fp16,bf16split", help="comma list of batched forms to time")
+    ap.add_argument("--forms", default="fp32,bf16,fp16,bf16split,fp16split", help="comma list of batched forms to time")
     ap.add_argument("--forms-only", action="store_true", help="time only the batched forms (profiling aid)")
     ap.add_argument("--batch-frames", type=int, default=256, help="frames of the uneven batch (0: skip)")
     ap.add_argument("--batch-calls", type=int, default=10)

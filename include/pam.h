@@ -82,10 +82,12 @@ typedef enum {
  * accumulation in tensor memory. The three apodizations are disjoint K-slices of one GEMM.
  * Requirements: nx == 128, n_apod 2 or 3, apertures with disjoint element sets.
  * Typical relative L2 error of I_TAX against the FP64 oracle at 128 elements, 300 bins:
- * BF16 about 5e-4, FP16 about 6e-5, BF16 split about 2e-6. */
+ * BF16 about 5e-4, FP16 about 6e-5, BF16 split about 2e-6, FP16 split about 1e-6 (the
+ * FP16 split also keeps every NCC map within 1e-5 of the oracle, as the FP32 path does). */
 #define PAM_FORM_GEMM_BF16 0x10u       /* BF16 operands */
 #define PAM_FORM_GEMM_FP16 0x20u       /* FP16 operands (frames scaled by a power of 2) */
 #define PAM_FORM_GEMM_BF16_SPLIT 0x40u /* BF16 hi + lo split: hi*hi + hi*lo + lo*hi */
+#define PAM_FORM_GEMM_FP16_SPLIT 0x80u /* FP16 hi + lo split (frames scaled by a power of 2): 22 significant bits */
 
 /* Acquisition and imaging geometry (Sec. II-A, Fig. 1; band selection Sec. II-D). */
 typedef struct {

@@ -113,7 +113,8 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     if (d->n_apod < 1 || d->n_apod > 3) return fail(PAM_ERR_INVALID_ARG, "n_apod must be 1, 2 or 3");
     if (!(d->eps > 0.0f) || !(d->eps <= 1.0f)) return fail(PAM_ERR_INVALID_ARG, "eps must be in (0, 1]");
     if (d->max_frames < 1 || d->max_frames > 65535) return fail(PAM_ERR_INVALID_ARG, "max_frames must be in [1, 65535]");
-    const unsigned form_bits = PAM_FORM_GEMM_BF16 | PAM_FORM_GEMM_FP16 | PAM_FORM_GEMM_BF16_SPLIT;
+    const unsigned form_bits =
+        PAM_FORM_GEMM_BF16 | PAM_FORM_GEMM_FP16 | PAM_FORM_GEMM_BF16_SPLIT | PAM_FORM_GEMM_FP16_SPLIT;
     if (d->flags & ~(PAM_EVANESCENT_ZERO | PAM_LATERAL_UPSAMPLE2X | form_bits))
         return fail(PAM_ERR_INVALID_ARG, "unknown flag bits");
     const unsigned form = d->flags & form_bits;
@@ -242,7 +243,7 @@ pam_status alloc_plan(pam_plan_s *p)
     PAM_TRY(dalloc(&p->w.fmax, F));
     PAM_TRY(dalloc(&p->w.status, 1));
     if (p->form) {
-        const bool split = p->form == PAM_FORM_GEMM_BF16_SPLIT;
+        const bool split = p->form == PAM_FORM_GEMM_BF16_SPLIT || p->form == PAM_FORM_GEMM_FP16_SPLIT;
         const size_t rows = nb * (size_t)p->nz * nx;
         const size_t groups = (F + pam::kFramesPerGroup - 1) / pam::kFramesPerGroup;
         const size_t tile16 = (size_t)p->K * 2 * pam::kFramesPerGroup * 2 / 16;   // uint4 per (group, bin) tile

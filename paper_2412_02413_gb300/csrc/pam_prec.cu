@@ -716,7 +716,7 @@ cudaError_t set_gemm_smem()
 cudaError_t launch_prec_tables(const pam_plan_s &p, cudaStream_t st)
 {
     dim3 grid(p.nz, p.n_bins);
-    if (p.form == PAM_FORM_GEMM_FP16)
+    if (p.form == PAM_FORM_GEMM_FP16 || p.form == PAM_FORM_GEMM_FP16_SPLIT)
         prec_table_kernel<true><<<grid, NXP, 0, st>>>(p.t.phase, p.t.live, p.nz, p.d.z0_m, p.d.dz_m, p.t.c_hi, p.t.c_lo);
     else
         prec_table_kernel<false><<<grid, NXP, 0, st>>>(p.t.phase, p.t.live, p.nz, p.d.z0_m, p.d.dz_m, p.t.c_hi, p.t.c_lo);
@@ -729,6 +729,7 @@ cudaError_t launch_prec(const pam_plan_s &p, int n_frames, cudaStream_t st)
     case PAM_FORM_GEMM_BF16: return launch_form<false, false>(p, n_frames, st);
     case PAM_FORM_GEMM_FP16: return launch_form<true, false>(p, n_frames, st);
     case PAM_FORM_GEMM_BF16_SPLIT: return launch_form<false, true>(p, n_frames, st);
+    case PAM_FORM_GEMM_FP16_SPLIT: return launch_form<true, true>(p, n_frames, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -754,6 +755,8 @@ cudaError_t prepare_prec_kernels()
     if ((e = set_gemm_smem<2, true, false>()) != cudaSuccess) return e;
     if ((e = set_gemm_smem<3, true, false>()) != cudaSuccess) return e;
     if ((e = set_gemm_smem<2, false, true>()) != cudaSuccess) return e;
+    if ((e = set_gemm_smem<2, true, true>()) != cudaSuccess) return e;
+    if ((e = set_gemm_smem<3, true, true>()) != cudaSuccess) return e;
     if ((e = set_gemm_smem<3, false, false, true>()) != cudaSuccess) return e;
     if ((e = set_gemm_smem<3, true, false, true>()) != cudaSuccess) return e;
     return set_gemm_smem<3, false, true>();

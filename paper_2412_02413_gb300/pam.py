@@ -21,7 +21,7 @@ PAM_OK = 0
 PAM_EVANESCENT_ZERO = 0x1
 PAM_LATERAL_UPSAMPLE2X = 0x2
 # tensor-core forms of the propagation (include/pam.h PAM_FORM_GEMM_*)
-FORMS = {"fp32": 0x0, "bf16": 0x10, "fp16": 0x20, "bf16split": 0x40}
+FORMS = {"fp32": 0x0, "bf16": 0x10, "fp16": 0x20, "bf16split": 0x40, "fp16split": 0x80}
 _STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_UNSUPPORTED", 3: "PAM_ERR_OOM",
            4: "PAM_ERR_CUDA", 5: "PAM_ERR_TIMEOUT", 6: "PAM_ERR_NUMERIC"}
 

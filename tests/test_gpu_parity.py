@@ -370,10 +370,10 @@ def test_profile_counters():
 # stated for the chosen forms: relative L2 <= 1e-2 on the energy maps and the
 # same brightest pixel; NCC deviations are reported. The hi + lo split recovers
 # close to FP32 agreement.
-FORM_TOL = {"bf16": (1e-2, 5e-2), "fp16": (1e-2, 2e-2), "bf16split": (1e-4, 1e-3)}
+FORM_TOL = {"bf16": (1e-2, 5e-2), "fp16": (1e-2, 2e-2), "bf16split": (1e-4, 1e-3), "fp16split": (1e-5, 1e-5)}
 
 
-@pytest.mark.parametrize("form", ["bf16", "fp16", "bf16split"])
+@pytest.mark.parametrize("form", ["bf16", "fp16", "bf16split", "fp16split"])
 def test_gemm_form_workload2(w2_frame, form):
     w, rf, src, orc = w2_frame
     plan = _pam().Plan.from_workload(w, max_frames=1, form=form)
@@ -390,7 +390,7 @@ def test_gemm_form_workload2(w2_frame, form):
     assert peak(img) == peak(orc["image"])
 
 
-@pytest.mark.parametrize("form", ["bf16", "fp16"])
+@pytest.mark.parametrize("form", ["bf16", "fp16", "fp16split"])
 def test_gemm_form_frame_groups(form):
     """20 frames: two groups of 16 frames (the second one ragged) in one call,
     each frame against the oracle."""
@@ -408,7 +408,7 @@ def test_gemm_form_frame_groups(form):
     assert worst <= FORM_TOL[form][0], worst
 
 
-@pytest.mark.parametrize("form", ["bf16", "bf16split"])
+@pytest.mark.parametrize("form", ["bf16", "bf16split", "fp16split"])
 def test_gemm_form_overlapping_apertures(form):
     """AS-DAX with two overlapping apertures of non-uniform weight whose edges
     are not on 8-element boundaries: the element blocks an aperture touches
