@@ -259,6 +259,15 @@ def run_forms(args, w, pool, stream, dev):
         entry = {"frames_per_call": args.batch, "value": args.batch * args.batch_steps / (fms / 1000.0),
                  "unit": "frames/s", "ms_per_frame": fms / (args.batch * args.batch_steps),
                  "main_kernel_us_per_frame": 1000.0 * kms / max(kn, 1) / args.batch}
+        if form != "fp32":
+            # MMA work of the GEMM per frame: M = nx pixels, K = 2 n_elem (Re, Im), N = 2 (Re, Im) per
+            # (bin, row), 2 flops per MAC; the split forms run three products (hi hi, hi lo, lo hi)
+            mma = 2.0 * w.nx * (2 * w.n_elem) * 2 * fp.n_bins * w.nz * (3 if "split" in form else 1)
+            peaks, kind = measured_peaks()
+            tf = mma / (entry["main_kernel_us_per_frame"] * 1e-6) / 1e12
+            entry["tensor"] = {"mma_tflop_per_frame": mma / 1e12, "achieved_tflops": tf,
+                               "peak_tflops": peaks["bf16_tflops"], "frac": tf / peaks["bf16_tflops"],
+                               "peak_basis": f"bf16_tflops ({kind}); FP16 dense rate equals BF16"}
         if form == "fp32":
             ref_img = img
         elif ref_img is not None:
