@@ -293,6 +293,31 @@ def test_learned_call_larger_than_the_batch():
     L.close()
 
 
+def test_gate_catches_an_untrained_network():
+    """At the bench's gate tolerance (0.25) an untrained network's maps miss the
+    gate, and those frames come out as the plain method."""
+    w = synth.workload(1)
+    w.nz = 40
+    pam = _pam()
+    L = pam.Learned.from_workload(w, max_frames=4)
+    L.set_params(flat(co.init_params(21)))
+    L.configure(gate_tol=0.25)
+    rf = torch.from_numpy(np.stack([synth.make_frame(w, 60 + i)[0] for i in range(4)])).cuda()
+    out = L.as_tax(rf)
+    plan = pam.Plan.from_workload(w, max_frames=4)
+    plan.set_split(1)
+    ref = plan.as_tax(rf, rho_n=True)
+    torch.cuda.synchronize()
+    passed = out["gate_pass"].cpu().numpy()
+    errs = out["gate_err"].cpu().numpy()
+    print(f"untrained network: gate errors {np.round(errs, 3).tolist()}")
+    assert passed.sum() == 0 and np.all(errs > 0.25)
+    for f in range(4):
+        assert rel_l2(out["image"][f].cpu().numpy(), ref["image"][f].cpu().numpy()) <= 1e-6
+    plan.close()
+    L.close()
+
+
 def test_gate_open_gives_the_network_image():
     w = synth.workload(1)
     w.nz = 40
