@@ -331,8 +331,10 @@ pam_status pam_image_metrics(const float *maps, int n_frames, int nz, int nx, do
  * image is I = rho_n^2 E (Eq. 11 with the full-aperture energy, which equals
  * sum_k |p~_1 + p~_2 + p~_3|^2 when the apodizations sum to one).
  * Operands of every convolution (activations, weights, gradients) are BF16;
- * every sum is FP32. Training minimises the mean squared error against the
- * exact rho_TAX with Adam (Kingma and Ba 2015: beta1 0.9, beta2 0.999,
+ * every sum is FP32. Training minimises the energy-weighted mean squared error
+ * (1/n) sum w (rho - rho_TAX)^2 against the exact rho_TAX, with per-pixel
+ * weight w = 0.05 + 0.95 min(1, E / max E) (E / max E = 10^(4 x0) - 1e-4 from
+ * input channel 0), with Adam (Kingma and Ba 2015: beta1 0.9, beta2 0.999,
  * eps 1e-8), all on the GPU.
  *
  * Error gate: per frame, the exact method runs on the tile of 16 depth rows
@@ -395,7 +397,7 @@ pam_status pam_learn_example(pam_learn_t l, const float *rf, int n_frames, void 
 /* Network output rho (in [eps, 1)) for packed features: device [n_frames][nz][nx]. */
 pam_status pam_learn_forward(pam_learn_t l, const void *features, int n_frames, float *rho, void *stream);
 
-/* Mean squared error against target ([n_frames][nz][nx]) and its gradient
+/* Energy-weighted mean squared error against target ([n_frames][nz][nx]) and its gradient
  * with respect to every parameter, without an update: grads device
  * [pam_learn_n_params()] or NULL, loss device [1] or NULL. */
 pam_status pam_learn_grads(pam_learn_t l, const void *features, const float *target, int n_frames, float *grads,

@@ -16,7 +16,11 @@ Definitions (all arrays float64, NCHW):
 * network: 5 conv3x3 layers 5 -> 32 -> 32 -> 32 -> 32 -> 1, ReLU after the
   first four, and the head rho = eps + (1 - eps) sigmoid(z), so that the
   prediction lies in [eps, 1) like the clamped NCC of Sec. II-A.
-* loss: mean squared error against the target map.
+* loss: energy-weighted mean squared error against the target map,
+    L = (1/n) sum_px w (rho - target)^2,  w = 0.05 + 0.95 min(1, E/max E),
+  with E/max E = 10^(4 x0) - 1e-4 recovered from input channel 0 (a fixed
+  function of the input): the image is rho^2 E, so the bright pixels matter
+  most, and the floor keeps the background supervised.
 * Adam (Kingma and Ba 2015) with bias correction.
 * features: channel 0 = log10(E / max E + 1e-4) of the full-aperture energy
   E = sum_k |p~|^2 (Eq. 3), channels 1..4 the same for the energy of each
@@ -32,6 +36,7 @@ import numpy as np
 
 CHANNELS = (5, 32, 32, 32, 32, 1)
 FEATURE_FLOOR = 1e-4
+WEIGHT_FLOOR = 0.05
 
 
 def conv3x3(x, w, b):
@@ -93,13 +98,20 @@ def forward(params, x, eps: float = 1e-3):
     raise ValueError("empty network")
 
 
+def loss_weights(x):
+    """Per-pixel loss weight [N][1][H][W] from the input's channel 0."""
+    e = np.clip(10.0 ** (4.0 * np.asarray(x, dtype=np.float64)[:, :1]) - FEATURE_FLOOR, 0.0, 1.0)
+    return WEIGHT_FLOOR + (1.0 - WEIGHT_FLOOR) * e
+
+
 def loss_and_grads(params, x, target, eps: float = 1e-3):
-    """Mean squared error and its gradients with respect to every (w, b)."""
+    """Energy-weighted mean squared error and its gradients with respect to every (w, b)."""
     rho, (acts, s) = forward(params, x, eps)
     diff = rho - target[:, None] if target.ndim == 3 else rho - target
     n = diff.size
-    loss = float(np.sum(diff ** 2) / n)
-    dy = 2.0 * diff / n * (1.0 - eps) * s * (1.0 - s)
+    wgt = loss_weights(x)
+    loss = float(np.sum(wgt * diff ** 2) / n)
+    dy = 2.0 * wgt * diff / n * (1.0 - eps) * s * (1.0 - s)
     grads = [None] * len(params)
     for li in range(len(params) - 1, -1, -1):
         w, b = params[li]

@@ -52,6 +52,7 @@ __host__ __device__ constexpr size_t tc_count(int l) { return (size_t)9 * TC_KCH
 __host__ __device__ constexpr size_t tc_offset(int l) { return l == 0 ? 0 : tc_offset(l - 1) + tc_count(l - 1); }
 constexpr int N_BANDS = 4;
 constexpr float FEATURE_FLOOR = 1e-4f;
+constexpr float WEIGHT_FLOOR = 0.05f;   // loss weight w = floor + (1 - floor) min(1, E / max E)
 constexpr int CT = 128;        // threads (= pixels along a row) of a CUDA-core conv block
 constexpr int PR = 2;          // output rows per conv block
 constexpr int WSPLIT = 131;    // padded row stride (floats) of the weight-gradient staging; odd: no bank conflicts
@@ -445,11 +446,13 @@ __global__ void wgrad_reduce_kernel(const float *__restrict__ part, int n_blocks
 }
 
 // ------------------------------------------------------------ head ----
-// Training: rho = eps + (1-eps) sigmoid(z), loss = mean (rho - target)^2, and
-// dL/dz into channel 0 of a chunked padded tensor (channels 1..7 zero).
+// Training: rho = eps + (1-eps) sigmoid(z), the energy-weighted loss
+// (1/n) sum w (rho - target)^2 with w = floor + (1 - floor) min(1, E / max E)
+// and E / max E = 10^(4 x0) - 1e-4 from the input's channel 0, and dL/dz into
+// channel 0 of a chunked padded tensor (channels 1..7 zero).
 __global__ void __launch_bounds__(EPI_THREADS)
-loss_kernel(const float *__restrict__ z, const float *__restrict__ target, int H, int W, float eps, float inv_n,
-            uint4 *__restrict__ dz, float *__restrict__ loss_part)
+loss_kernel(const float *__restrict__ z, const float *__restrict__ target, const uint4 *__restrict__ feat, int H,
+            int W, float eps, float inv_n, uint4 *__restrict__ dz, float *__restrict__ loss_part)
 {
     const int f = blockIdx.y;
     const int npix = H * W, HP = H + 2, WP = W + 2;
@@ -458,9 +461,12 @@ loss_kernel(const float *__restrict__ z, const float *__restrict__ target, int H
         const float zz = z[(size_t)f * npix + x];
         const float s = 1.0f / (1.0f + expf(-zz));
         const float d = eps + (1.0f - eps) * s - target[(size_t)f * npix + x];
-        l = fmaf(d, d, l);
-        const float g = 2.0f * d * inv_n * (1.0f - eps) * s * (1.0f - s);
         const int i = x / W, j = x % W;
+        const float x0 = bf_lo(feat[((size_t)f * HP + i + 1) * WP + j + 1].x);
+        const float en = fminf(fmaxf(exp10f(4.0f * x0) - FEATURE_FLOOR, 0.0f), 1.0f);
+        const float wgt = WEIGHT_FLOOR + (1.0f - WEIGHT_FLOOR) * en;
+        l = fmaf(wgt * d, d, l);
+        const float g = 2.0f * wgt * d * inv_n * (1.0f - eps) * s * (1.0f - s);
         dz[((size_t)f * HP + i + 1) * WP + j + 1] = make_uint4(pack_bf2(g, 0.0f), 0u, 0u, 0u);
     }
 #pragma unroll
@@ -841,7 +847,7 @@ cudaError_t run_grads(pam_learn_s *l, const uint4 *feat, const float *target, in
     if ((e = run_forward(l, feat, n, true, st)) != cudaSuccess) return e;
     const float inv_n = (float)(1.0 / ((double)n * l->npix));
     dim3 gl(l->loss_blocks, n);
-    pam::loss_kernel<<<gl, pam::EPI_THREADS, 0, st>>>(l->z, target, H, W, l->plan->d.eps, inv_n, l->dz,
+    pam::loss_kernel<<<gl, pam::EPI_THREADS, 0, st>>>(l->z, target, feat, H, W, l->plan->d.eps, inv_n, l->dz,
                                                       l->loss_part);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (loss) {

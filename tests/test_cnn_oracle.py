@@ -94,3 +94,16 @@ def test_features_range_and_max():
     assert np.isclose(f[0].max(), np.log10(1 + 1e-4) / 4)
     assert np.isclose(f[0][np.unravel_index(np.argmin(e), e.shape)],
                       np.log10(e.min() / e.max() + 1e-4) / 4)
+
+
+def test_loss_weight_closed_forms():
+    # channel 0 = log10(E/max + 1e-4)/4: the brightest pixel has weight 1, an empty pixel the floor
+    x = np.zeros((1, 5, 1, 3))
+    x[0, 0, 0] = [np.log10(1 + 1e-4) / 4, np.log10(0.5 + 1e-4) / 4, np.log10(1e-4) / 4]
+    w = co.loss_weights(x)[0, 0, 0]
+    assert np.allclose(w, [1.0, co.WEIGHT_FLOOR + (1 - co.WEIGHT_FLOOR) * 0.5, co.WEIGHT_FLOOR], atol=1e-12)
+    # the weighted loss of a uniform error d is d^2 times the mean weight
+    params = co.init_params(9, channels=(5, 3, 1))
+    rho, _ = co.forward(params, x)
+    loss, _ = co.loss_and_grads(params, x, rho[:, 0] - 0.1)
+    assert np.isclose(loss, 0.01 * w.mean())

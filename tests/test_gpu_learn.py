@@ -85,8 +85,9 @@ def grads_rounded(params, x, target):
     s = co.sigmoid(z)
     diff = EPS + (1.0 - EPS) * s - target[:, None]
     n = diff.size
-    loss = float(np.sum(diff ** 2) / n)
-    dy = bf16(2.0 * diff / n * (1.0 - EPS) * s * (1.0 - s))
+    wgt = co.loss_weights(x)
+    loss = float(np.sum(wgt * diff ** 2) / n)
+    dy = bf16(2.0 * wgt * diff / n * (1.0 - EPS) * s * (1.0 - s))
     grads = [None] * len(params)
     for li in range(len(params) - 1, -1, -1):
         w, _ = params[li]
