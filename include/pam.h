@@ -179,6 +179,16 @@ pam_status pam_as_dax(pam_plan_t p, const float *rf, int n_frames, float *image_
 pam_status pam_as_xcorr_host(pam_plan_t p, const float *rf_host, int n_frames,
                              float *image_host, float *rho_n_host, void *stream);
 
+/* As pam_as_xcorr_host, but returns once the upload, the kernels and the
+ * downloads are queued on `stream`: the results are in host memory when the
+ * stream reaches that point (cudaStreamSynchronize, an event, or pam_sync).
+ * The host buffers must stay valid and unmodified until then; with pageable
+ * (not pinned) buffers the copies may block. Calls on one plan share its
+ * staging buffers, so they must be ordered on one stream; to overlap the
+ * copies of one frame with the kernels of another, use one plan per stream. */
+pam_status pam_as_xcorr_host_async(pam_plan_t p, const float *rf_host, int n_frames, float *image_host,
+                                   float *rho_n_host, void *stream);
+
 /* Size of the device array that pam_as_tax_static works in. It is part of the
  * library image on every GPU that loads the library. */
 #define PAM_STATIC_SCRATCH_BYTES (16u << 20)

@@ -496,8 +496,8 @@ pam_status pam_as_dax(pam_plan_t p, const float *rf, int n_frames, float *image_
     return run_xcorr(p, rf, n_frames, image_dax, rho_n, rho_pair, image_as, static_cast<cudaStream_t>(stream));
 }
 
-pam_status pam_as_xcorr_host(pam_plan_t p, const float *rf_host, int n_frames, float *image_host,
-                             float *rho_n_host, void *stream)
+pam_status pam_as_xcorr_host_async(pam_plan_t p, const float *rf_host, int n_frames, float *image_host,
+                                   float *rho_n_host, void *stream)
 {
     if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
     if (p->n_apod < 2) return fail(PAM_ERR_INVALID_ARG, "pam_as_xcorr_host needs n_apod of 2 or 3");
@@ -534,7 +534,15 @@ pam_status pam_as_xcorr_host(pam_plan_t p, const float *rf_host, int n_frames, f
             if (e != cudaSuccess) return cuda_fail(e, "rho_n download");
         }
     }
-    e = cudaStreamSynchronize(st);
+    return PAM_OK;
+}
+
+pam_status pam_as_xcorr_host(pam_plan_t p, const float *rf_host, int n_frames, float *image_host,
+                             float *rho_n_host, void *stream)
+{
+    pam_status s = pam_as_xcorr_host_async(p, rf_host, n_frames, image_host, rho_n_host, stream);
+    if (s != PAM_OK || n_frames == 0) return s;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
     return PAM_OK;
 }

@@ -66,6 +66,7 @@ _SIGS = {
     "pam_as_tax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pam_as_dax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pam_as_xcorr_host": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
+    "pam_as_xcorr_host_async": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
     "pam_as_tax_static": (ctypes.c_int, [ctypes.POINTER(PlanDesc), _VP, ctypes.c_int, _VP, _VP, _VP]),
     "pam_sync": (ctypes.c_int, [_VP, _VP]),
     "pam_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -327,6 +328,19 @@ class Plan:
         _check(load().pam_as_xcorr_host(self._h, rf_host.ctypes.data, F, image_out.ctypes.data,
                                         None if rho_n_out is None else rho_n_out.ctypes.data,
                                         _stream_ptr(stream)))
+
+    def as_xcorr_host_async(self, rf_host: np.ndarray, image_out: np.ndarray,
+                            rho_n_out: Optional[np.ndarray] = None, stream=None):
+        """As :meth:`as_xcorr_host` through ``pam_as_xcorr_host_async``: returns
+        once the work is queued on ``stream``; the results are in the host arrays
+        when the stream gets there (keep the arrays alive until then)."""
+        for a in (rf_host, image_out) + ((rho_n_out,) if rho_n_out is not None else ()):
+            if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+                raise TypeError("host buffers must be C-contiguous float32")
+        F = rf_host.shape[0] if rf_host.ndim == 3 else 1
+        _check(load().pam_as_xcorr_host_async(self._h, rf_host.ctypes.data, F, image_out.ctypes.data,
+                                              None if rho_n_out is None else rho_n_out.ctypes.data,
+                                              _stream_ptr(stream)))
 
     def set_split(self, n_split: int = 0):
         """Bin chunks per row tile of the fused kernel (0 = automatic)."""

@@ -336,6 +336,29 @@ def test_host_entry_point_matches_device(w1_frames):
         assert rel_l2(img[f], orc[f]["image"]) <= REL_L2_TOL
 
 
+def test_async_host_entry_point_pipelined(w1_frames):
+    """pam_as_xcorr_host_async on two plans and two streams, results read after
+    each stream's event: identical to the blocking entry point."""
+    w, frames, _ = w1_frames
+    pam = _pam()
+    plans = [pam.Plan.from_workload(w), pam.Plan.from_workload(w)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    rf = [np.ascontiguousarray(fr[0]) for fr in frames]
+    pinned = [torch.from_numpy(r).pin_memory().numpy() for r in rf]
+    outs = [(torch.zeros(1, w.nz, w.nx).pin_memory().numpy(), torch.zeros(1, w.nz, w.nx).pin_memory().numpy())
+            for _ in rf]
+    for i, r in enumerate(pinned):
+        plans[i % 2].as_xcorr_host_async(r, outs[i][0], outs[i][1], stream=streams[i % 2])
+    torch.cuda.synchronize()
+    for i, r in enumerate(rf):
+        img = np.zeros((1, w.nz, w.nx), np.float32)
+        rho = np.zeros((1, w.nz, w.nx), np.float32)
+        plans[0].as_xcorr_host(r, img, rho)
+        assert np.array_equal(outs[i][0], img) and np.array_equal(outs[i][1], rho)
+    for p in plans:
+        p.close()
+
+
 def test_plans_of_different_sizes_coexist():
     """A plan with a smaller time FFT created later must not break an earlier
     plan with a larger one (kernel attributes are process-wide)."""
