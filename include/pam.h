@@ -40,6 +40,11 @@
  *   - A plan is not thread-safe: calls on one plan must not overlap. No call
  *     aborts the process. pam_last_error() gives the message of the calling
  *     thread's last failure.
+ *   - The public calls are NVTX ranges named after the call (visible under
+ *     nsys / ncu; free when no tool is attached).
+ *   - Fault injection for tests (host side): with the environment variable
+ *     PAM_FAULT=alloc, pam_plan_create fails with PAM_ERR_OOM part way through
+ *     its allocations (and frees what it allocated).
  */
 #ifndef PAM_H
 #define PAM_H
@@ -216,6 +221,14 @@ pam_status pam_as_xcorr_host_async(pam_plan_t p, const float *rf_host, int n_fra
  * from the stack. */
 pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf, int n_frames, float *image_tax,
                              float *rho_n, void *stream);
+
+/* Failure-path check: launches on `stream` one small kernel that waits on an
+ * mbarrier nothing ever completes, with the same bounded wait (about one
+ * second) that the staging pipelines use. When the wait gives up, the kernel
+ * sets the plan's device status word and exits, so the next pam_sync returns
+ * PAM_ERR_TIMEOUT and clears it; the CUDA context stays usable. No fault, trap
+ * or hang is involved. For tests of the timeout path. */
+pam_status pam_debug_expire_wait(pam_plan_t p, void *stream);
 
 /* Waits for the plan's work on `stream` and reads the device status word.
  * Returns PAM_ERR_TIMEOUT if a kernel reported an expired wait (then clears

@@ -2,10 +2,12 @@
 // ("pre-run", Sec. II-E), workspace, and the C entry points of include/pam.h.
 // The arithmetic of every step runs in the kernels of pam_fft.cu and pam_prop.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -19,6 +21,15 @@ namespace {
 thread_local char g_err[512];
 
 }  // namespace
+
+bool pam::fault_injected(const char *what)
+{
+    const char *v = std::getenv("PAM_FAULT");
+    return v && std::strcmp(v, what) == 0;
+}
+
+pam::TraceRange::TraceRange(const char *name) { nvtxRangePushA(name); }
+pam::TraceRange::~TraceRange() { nvtxRangePop(); }
 
 pam_status pam::set_error(pam_status s, const char *msg)
 {
@@ -232,6 +243,7 @@ pam_status alloc_plan(pam_plan_s *p)
     PAM_TRY(dalloc(&p->t.bin_evan, nb));
     PAM_TRY(dalloc(&p->w.S, F * nb * ne));
     PAM_TRY(dalloc(&p->w.Q, F * nb * (size_t)p->n_apod * nx));
+    if (pam::fault_injected("alloc")) return fail(PAM_ERR_OOM, "injected allocation failure (PAM_FAULT=alloc)");
     int rows = pam::prop_rows_per_cta(p->nx);
     int row_tiles = (p->nz + rows - 1) / rows;
     size_t target = 2 * (size_t)p->num_sms;
@@ -372,6 +384,7 @@ void pam_plan_desc_init(pam_plan_desc *d)
 
 pam_status pam_plan_create(const pam_plan_desc *d, pam_plan_t *out)
 {
+    pam::TraceRange trace_("pam_plan_create");
     if (!out) return fail(PAM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!d) return fail(PAM_ERR_INVALID_ARG, "descriptor is NULL");
@@ -432,6 +445,7 @@ int pam_plan_apod(pam_plan_t p, float *apod_out)
 pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod_index,
                            float *energy, float *fields, void *stream)
 {
+    pam::TraceRange trace_("pam_as_backprop");
     if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
     if (n_frames < 0) return fail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
     if (apod_index < -1 || apod_index >= p->n_apod) return fail(PAM_ERR_INVALID_ARG, "apod_index out of range");
@@ -467,6 +481,7 @@ pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod
 pam_status pam_as_tax(pam_plan_t p, const float *rf, int n_frames, float *image_tax,
                       float *rho_n, float *rho_pairs, float *image_as, void *stream)
 {
+    pam::TraceRange trace_("pam_as_tax");
     if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
     if (p->n_apod != 3) return fail(PAM_ERR_INVALID_ARG, "pam_as_tax needs a plan with n_apod == 3");
     if (n_frames < 0) return fail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
@@ -483,6 +498,7 @@ pam_status pam_as_tax(pam_plan_t p, const float *rf, int n_frames, float *image_
 pam_status pam_as_dax(pam_plan_t p, const float *rf, int n_frames, float *image_dax,
                       float *rho_n, float *rho_pair, float *image_as, void *stream)
 {
+    pam::TraceRange trace_("pam_as_dax");
     if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
     if (p->n_apod != 2) return fail(PAM_ERR_INVALID_ARG, "pam_as_dax needs a plan with n_apod == 2");
     if (n_frames < 0) return fail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
@@ -499,6 +515,7 @@ pam_status pam_as_dax(pam_plan_t p, const float *rf, int n_frames, float *image_
 pam_status pam_as_xcorr_host_async(pam_plan_t p, const float *rf_host, int n_frames, float *image_host,
                                    float *rho_n_host, void *stream)
 {
+    pam::TraceRange trace_("pam_as_xcorr_host_async");
     if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
     if (p->n_apod < 2) return fail(PAM_ERR_INVALID_ARG, "pam_as_xcorr_host needs n_apod of 2 or 3");
     if (n_frames < 0) return fail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
@@ -544,6 +561,15 @@ pam_status pam_as_xcorr_host(pam_plan_t p, const float *rf_host, int n_frames, f
     if (s != PAM_OK || n_frames == 0) return s;
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    return PAM_OK;
+}
+
+pam_status pam_debug_expire_wait(pam_plan_t p, void *stream)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    cudaError_t e = pam::launch_expire_wait(p->w.status, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "expire-wait launch");
+    p->kernels += 1;
     return PAM_OK;
 }
 

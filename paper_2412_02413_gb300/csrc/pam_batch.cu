@@ -513,6 +513,7 @@ int pam_batch_bins(pam_batch_t b, int frame, int *bins_out)
 
 pam_status pam_batch_as_tax(pam_batch_t b, const float *rf, float *image, float *rho_n, void *stream)
 {
+    pam::TraceRange trace_("pam_batch_as_tax");
     if (!b) return pam::fail(PAM_ERR_INVALID_ARG, "batch is NULL");
     pam_status s;
     if ((s = pam::check_dev(rf, "rf", true)) != PAM_OK) return s;

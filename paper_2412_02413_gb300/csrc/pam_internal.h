@@ -148,6 +148,20 @@ cudaError_t launch_prop_bands(const pam_plan_s &p, int n_frames, int n_bands, fl
 cudaError_t launch_normalize_batch(int n_frames, int max_npix, const BatchFrame *frames, const EpiOut &out,
                                    cudaStream_t st);
 bool prop_uses_cluster(int n_split);
+// A kernel whose bounded mbarrier wait never completes (failure-path test).
+cudaError_t launch_expire_wait(int *status, cudaStream_t st);
+
+// Host-side fault injection for tests: true when the environment variable
+// PAM_FAULT names `what` ("alloc": plan allocation fails part way).
+bool fault_injected(const char *what);
+
+// NVTX range over one public call (a no-op unless a tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name);
+    ~TraceRange();
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 cudaError_t prepare_kernels(const pam_plan_s &p);
 
 // Tensor-core form (pam_prec.cu): plan-time point-spread table, and the per-call

@@ -1073,6 +1073,7 @@ size_t pam_learn_feature_bytes(pam_learn_t l) { return l ? l->ppix * 16 : 0; }
 pam_status pam_learn_example(pam_learn_t l, const float *rf, int n_frames, void *features, float *target,
                              float *energy, void *stream)
 {
+    pam::TraceRange trace_("pam_learn_example");
     pam_status s;
     if ((s = check_frames(l, n_frames)) != PAM_OK) return s;
     if ((s = check_dev(rf, "rf", true)) != PAM_OK) return s;
@@ -1145,6 +1146,7 @@ pam_status pam_learn_grads(pam_learn_t l, const void *features, const float *tar
 pam_status pam_learn_train_step(pam_learn_t l, const void *features, const float *target, int n_frames, float lr,
                                 float *loss, void *stream)
 {
+    pam::TraceRange trace_("pam_learn_train_step");
     pam_status s;
     if ((s = check_frames(l, n_frames)) != PAM_OK) return s;
     if ((s = check_dev(features, "features", true)) != PAM_OK) return s;
@@ -1168,6 +1170,7 @@ pam_status pam_learn_train_step(pam_learn_t l, const void *features, const float
 pam_status pam_learn_tax(pam_learn_t l, const float *rf, int n_frames, float *image, float *rho_n, float *gate_err,
                          int *gate_pass, void *stream)
 {
+    pam::TraceRange trace_("pam_learn_tax");
     if (!l) return lfail(PAM_ERR_INVALID_ARG, "learned-form handle is NULL");
     if (n_frames < 0) return lfail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
     if (n_frames == 0) return PAM_OK;

@@ -151,6 +151,7 @@ pam_status pam_image_metrics(const float *maps, int n_frames, int nz, int nx, do
 
 pam_status pam_as3(pam_plan_t p, const float *rf, int n_frames, float *image, void *stream)
 {
+    pam::TraceRange trace_("pam_as3");
     if (!p) return pam::mfail(PAM_ERR_INVALID_ARG, "plan is NULL");
     pam_status s = pam_as_backprop(p, rf, n_frames, -1, image, nullptr, stream);
     if (s != PAM_OK || n_frames == 0) return s;

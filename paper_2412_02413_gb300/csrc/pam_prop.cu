@@ -774,7 +774,29 @@ cudaError_t launch_bands_nx(const pam_plan_s &p, int n_frames, int n_bands, floa
     return launch_prop_t<1, NX, false, false>(p, n_frames, n_bands, nullptr, out, st, bands);
 }
 
+// Failure-path check: one warp waits on an mbarrier that no thread or copy
+// ever completes, with the bounded wait every staging pipeline uses. The wait
+// gives up after about one second and the kernel reports through the status
+// word, as a real stalled pipeline would, then exits normally.
+__global__ void expire_wait_kernel(int *__restrict__ status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0);
+    if (!ok && threadIdx.x == 0) atomicOr(status, 1);
+}
+
 }  // namespace
+
+cudaError_t launch_expire_wait(int *status, cudaStream_t st)
+{
+    expire_wait_kernel<<<1, 32, 0, st>>>(status);
+    return cudaGetLastError();
+}
 
 int prop_rows_per_cta(int nx) { return PROP_WARPS * (32 / (nx / 8)); }
 

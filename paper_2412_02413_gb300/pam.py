@@ -69,6 +69,7 @@ _SIGS = {
     "pam_as_xcorr_host_async": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP]),
     "pam_as_tax_static": (ctypes.c_int, [ctypes.POINTER(PlanDesc), _VP, ctypes.c_int, _VP, _VP, _VP]),
     "pam_sync": (ctypes.c_int, [_VP, _VP]),
+    "pam_debug_expire_wait": (ctypes.c_int, [_VP, _VP]),
     "pam_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                         ctypes.POINTER(ctypes.c_longlong)]),
@@ -355,6 +356,11 @@ class Plan:
         ms, n, k = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
         _check(load().pam_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)))
         return ms.value, n.value, k.value
+
+    def debug_expire_wait(self, stream=None):
+        """Launch the failure-path check kernel (``pam_debug_expire_wait``): the
+        next :meth:`sync` raises PAM_ERR_TIMEOUT after about one second."""
+        _check(load().pam_debug_expire_wait(self._h, _stream_ptr(stream)))
 
     def sync(self, stream=None):
         _check(load().pam_sync(self._h, _stream_ptr(stream)))
