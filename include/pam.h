@@ -395,6 +395,15 @@ pam_status pam_learn_set_params(pam_learn_t l, const float *params, size_t n);
 /* Copies the current parameters to host memory. Blocks. */
 pam_status pam_learn_get_params(pam_learn_t l, float *params, size_t n);
 
+/* Training state for checkpoint and resume: parameters, Adam first and second
+ * moments (3 x pam_learn_n_params() floats, in that order) and the Adam step
+ * count. A training run restored with pam_learn_set_state continues exactly
+ * where the saved one was: every kernel of the step reduces in a fixed order,
+ * so the same batches give the same bits. Both calls block. */
+size_t pam_learn_state_size(void);
+pam_status pam_learn_get_state(pam_learn_t l, float *state, size_t n, long long *adam_steps);
+pam_status pam_learn_set_state(pam_learn_t l, const float *state, size_t n, long long adam_steps);
+
 /* gate_tol: relative L2 bound of the gate (default 0.05; < 0 sends every
  * frame through the exact path, +inf accepts every frame). use_tensor_cores: 1
  * runs every layer's forward on tcgen05 and the band energies in the BF16

@@ -1045,6 +1045,41 @@ pam_status pam_learn_get_params(pam_learn_t l, float *params, size_t n)
     return PAM_OK;
 }
 
+size_t pam_learn_state_size(void) { return 3 * pam::N_PARAMS; }
+
+pam_status pam_learn_get_state(pam_learn_t l, float *state, size_t n, long long *adam_steps)
+{
+    if (!l || !state) return lfail(PAM_ERR_INVALID_ARG, "NULL argument");
+    if (n != 3 * pam::N_PARAMS) return lfail(PAM_ERR_INVALID_ARG, "state size differs from pam_learn_state_size()");
+    const size_t np = pam::N_PARAMS;
+    LTRY(cudaDeviceSynchronize());
+    LTRY(cudaMemcpy(state, l->params, np * sizeof(float), cudaMemcpyDeviceToHost));
+    LTRY(cudaMemcpy(state + np, l->adam_m, np * sizeof(float), cudaMemcpyDeviceToHost));
+    LTRY(cudaMemcpy(state + 2 * np, l->adam_v, np * sizeof(float), cudaMemcpyDeviceToHost));
+    if (adam_steps) *adam_steps = l->t;
+    return PAM_OK;
+}
+
+pam_status pam_learn_set_state(pam_learn_t l, const float *state, size_t n, long long adam_steps)
+{
+    if (!l || !state) return lfail(PAM_ERR_INVALID_ARG, "NULL argument");
+    if (n != 3 * pam::N_PARAMS) return lfail(PAM_ERR_INVALID_ARG, "state size differs from pam_learn_state_size()");
+    if (adam_steps < 0) return lfail(PAM_ERR_INVALID_ARG, "adam_steps must be >= 0");
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(state[i])) return lfail(PAM_ERR_NUMERIC, "non-finite state value");
+    for (size_t i = 2 * pam::N_PARAMS; i < n; ++i)
+        if (state[i] < 0.0f) return lfail(PAM_ERR_INVALID_ARG, "Adam second moments must be >= 0");
+    const size_t np = pam::N_PARAMS;
+    LTRY(cudaDeviceSynchronize());
+    LTRY(cudaMemcpy(l->params, state, np * sizeof(float), cudaMemcpyHostToDevice));
+    LTRY(cudaMemcpy(l->adam_m, state + np, np * sizeof(float), cudaMemcpyHostToDevice));
+    LTRY(cudaMemcpy(l->adam_v, state + 2 * np, np * sizeof(float), cudaMemcpyHostToDevice));
+    l->t = adam_steps;
+    LTRY(run_prep(l, nullptr));
+    LTRY(cudaDeviceSynchronize());
+    return PAM_OK;
+}
+
 pam_status pam_learn_configure(pam_learn_t l, float gate_tol, int use_tensor_cores)
 {
     if (!l) return lfail(PAM_ERR_INVALID_ARG, "learned-form handle is NULL");

@@ -15,6 +15,12 @@ the GPU with torch so that 20k frames take seconds. Held-out frames come from
 ``synth.make_frame`` (independent sources and seeds).
 
   python -m paper_2412_02413_gb300.learn [--frames 20000] [--epochs 3] [--out PATH]
+      [--checkpoint PATH --checkpoint-every N] [--resume PATH]
+
+Checkpoint and resume: the training state (parameters, Adam moments, step)
+is saved every N steps; --resume restores it, rebuilds the same seeded
+examples and batch order, and continues from the saved step. The kernels
+reduce in a fixed order, so a resumed run reproduces the uninterrupted one.
 """
 from __future__ import annotations
 
@@ -100,6 +106,32 @@ def load_checkpoint(path: str = CHECKPOINT):
     return d["params"], json.loads(str(d["meta"]))
 
 
+def save_training_state(path: str, learned, step: int, meta: dict):
+    """Parameters, Adam moments and the step reached (written atomically)."""
+    state, adam_steps = learned.get_state()
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, state=state, adam_steps=np.int64(adam_steps), step=np.int64(step), meta=np.array(json.dumps(meta)))
+    os.replace(tmp, path)
+
+
+def load_training_state(path: str):
+    d = np.load(path)
+    return d["state"], int(d["adam_steps"]), int(d["step"]), json.loads(str(d["meta"]))
+
+
+def batch_schedule(n_batches: int, epochs: int, seed: int):
+    """Batch index of every step: a seeded permutation per epoch."""
+    import torch
+    gen = torch.Generator().manual_seed(seed)
+    return [b for _ in range(epochs) for b in torch.randperm(n_batches, generator=gen).tolist()]
+
+
+def lr_at(step: int, steps: int, lr: float, lr_min: float) -> float:
+    """Cosine decay from lr to lr_min over the run."""
+    return lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * step / steps))
+
+
 def held_out_frames(w, n: int, first: int = HELD_OUT_FIRST, workers: int = 0) -> np.ndarray:
     jobs = [(w, first + i) for i in range(n)]
     workers = workers or max(1, min(16, os.cpu_count() or 1))
@@ -175,17 +207,21 @@ def train(args):
     nb = N // B
     steps = args.epochs * nb
     loss = torch.zeros(4, dtype=torch.float32, device="cuda")
-    order_gen = torch.Generator().manual_seed(args.seed + 29)
+    schedule = batch_schedule(nb, args.epochs, args.seed + 29)
     log = []
+    start = 0
+    if args.resume:
+        state, adam_steps, start, _ = load_training_state(args.resume)
+        L.set_state(state, adam_steps)
     t2 = time.time()
-    step = 0
-    for ep in range(args.epochs):
-        for bi in torch.randperm(nb, generator=order_gen).tolist():
-            lr = args.lr_min + 0.5 * (args.lr - args.lr_min) * (1.0 + math.cos(math.pi * step / steps))
-            L.train_step(feats[bi * B:(bi + 1) * B], target[bi * B:(bi + 1) * B], lr, loss=loss)
-            if step % args.log_every == 0 or step == steps - 1:
-                log.append((step, float(loss[0].item())))
-            step += 1
+    for step in range(start, steps):
+        bi = schedule[step]
+        L.train_step(feats[bi * B:(bi + 1) * B], target[bi * B:(bi + 1) * B],
+                     lr_at(step, steps, args.lr, args.lr_min), loss=loss)
+        if step % args.log_every == 0 or step == steps - 1:
+            log.append((step, float(loss[0].item())))
+        if args.checkpoint and (step + 1) % args.checkpoint_every == 0:
+            save_training_state(args.checkpoint, L, step + 1, {"steps": steps, "frames": N, "seed": args.seed})
     L.sync()
     t_train = time.time() - t2
     params = L.get_params()
@@ -225,6 +261,9 @@ def main():
     ap.add_argument("--log-every", type=int, default=100)
     ap.add_argument("--workers", type=int, default=0)
     ap.add_argument("--out", default=CHECKPOINT)
+    ap.add_argument("--checkpoint", default="", help="training-state file written every --checkpoint-every steps")
+    ap.add_argument("--checkpoint-every", type=int, default=500)
+    ap.add_argument("--resume", default="", help="training-state file to continue from")
     train(ap.parse_args())
 
 

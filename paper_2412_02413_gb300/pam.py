@@ -93,6 +93,11 @@ _SIGS = {
     "pam_learn_set_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
     "pam_learn_get_params": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t]),
     "pam_learn_configure": (ctypes.c_int, [_VP, ctypes.c_float, ctypes.c_int]),
+    "pam_learn_state_size": (ctypes.c_size_t, []),
+    "pam_learn_get_state": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t,
+                                           ctypes.POINTER(ctypes.c_longlong)]),
+    "pam_learn_set_state": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t,
+                                           ctypes.c_longlong]),
     "pam_learn_feature_bytes": (ctypes.c_size_t, [_VP]),
     "pam_learn_example": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "pam_learn_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
@@ -523,6 +528,20 @@ class Learned:
         p = np.zeros(self.n_params, dtype=np.float32)
         _check(load().pam_learn_get_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size))
         return p
+
+    def get_state(self):
+        """(state, adam_steps): parameters, Adam m and v as one float32 array."""
+        L = load()
+        st = np.zeros(int(L.pam_learn_state_size()), dtype=np.float32)
+        t = ctypes.c_longlong()
+        _check(L.pam_learn_get_state(self._h, st.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), st.size,
+                                     ctypes.byref(t)))
+        return st, int(t.value)
+
+    def set_state(self, state, adam_steps: int):
+        st = np.ascontiguousarray(np.asarray(state, dtype=np.float32).ravel())
+        _check(load().pam_learn_set_state(self._h, st.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), st.size,
+                                          int(adam_steps)))
 
     def configure(self, gate_tol: float = 0.05, tensor_cores: bool = False):
         _check(load().pam_learn_configure(self._h, float(gate_tol), int(bool(tensor_cores))))

@@ -388,6 +388,46 @@ def test_tensor_core_forward_matches():
     L.close()
 
 
+def test_training_resumes_bit_exactly(tmp_path):
+    """12 Adam steps straight through equal 6 steps, a saved training state, a
+    new learned form restored from it, and 6 more steps: bit for bit."""
+    from paper_2412_02413_gb300 import learn
+    w = synth.workload(1)
+    w.nz = 24
+    pam = _pam()
+    B = 4
+    rf = torch.from_numpy(np.stack([synth.make_frame(w, 80 + i)[0] for i in range(2 * B)])).cuda()
+    La = pam.Learned.from_workload(w, max_frames=2 * B)
+    La.set_params(learn.init_params(3))
+    feats, tgt, _ = La.example(rf)
+    sched = learn.batch_schedule(2, 6, 7)          # 12 steps over 2 batches
+    lrs = [learn.lr_at(k, 12, 2e-3, 5e-5) for k in range(12)]
+
+    def run(L, steps):
+        for k in steps:
+            b = sched[k]
+            L.train_step(feats[b * B:(b + 1) * B], tgt[b * B:(b + 1) * B], lrs[k])
+        L.sync()
+
+    run(La, range(12))
+    p_straight = La.get_params()
+    Lb = pam.Learned.from_workload(w, max_frames=2 * B)
+    Lb.set_params(learn.init_params(3))
+    run(Lb, range(6))
+    path = str(tmp_path / "state.npz")
+    learn.save_training_state(path, Lb, 6, {"test": True})
+    Lb.close()
+    state, adam_steps, step, _ = learn.load_training_state(path)
+    assert step == 6 and adam_steps == 6
+    Lc = pam.Learned.from_workload(w, max_frames=2 * B)
+    Lc.set_state(state, adam_steps)
+    run(Lc, range(6, 12))
+    assert np.array_equal(Lc.get_params(), p_straight)
+    assert Lc.info()["adam_steps"] == 12
+    La.close()
+    Lc.close()
+
+
 # --------------------------------------------------------------- training --
 def _isnr_esa(img, pix_area):
     """Eq. 12: ISNR = 10 log10(mean inside A_0.5 / mean outside), and the
