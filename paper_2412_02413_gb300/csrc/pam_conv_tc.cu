@@ -30,9 +30,12 @@
 #include <stdint.h>
 
 #include "pam_internal.h"
+#include "pam_ptx.h"
 
 namespace pam {
 namespace {
+
+using namespace ptx;
 
 constexpr int W = 128, WP = W + 2;
 constexpr int ROWS = 16;                       // output rows per CTA
@@ -50,76 +53,11 @@ struct ConvShape {
     static constexpr int WT_BYTES = 9 * TAP_BYTES;
     static constexpr size_t SMEM = (size_t)WT_BYTES + (size_t)NSLOT * ROW_BYTES + 256;
     // kind::f16, FP32 accumulate, A = B = BF16, both K-major, N = NCO, M = 128.
-    static constexpr unsigned IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(NCO >> 3) << 17) |
-                                      ((128u >> 4) << 24);
+    static constexpr unsigned IDESC = ptx::umma_idesc(false, 128, NCO);
 };
 
-__device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void bar_init(uint64_t *b, unsigned n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void bar_expect(uint64_t *b, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(uint64_t *b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool bar_try(uint64_t *b, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity), "r"(10000u)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *b)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     su32(dst)),
-                 "l"(src), "r"(bytes), "r"(su32(b))
-                 : "memory");
-}
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// Shared-memory matrix descriptor: canonical K-major, no swizzle, version 1.
-__device__ __forceinline__ uint64_t sdesc(unsigned addr, unsigned lbo, unsigned sbo)
-{
-    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-__device__ __forceinline__ void mma_elect(unsigned d, uint64_t a, uint64_t b, unsigned idesc, unsigned acc)
-{
-    asm volatile(
-        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
-        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void commit_elect(uint64_t *b)
-{
-    asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
-                 " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(su32(b))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld32(unsigned taddr, unsigned (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-}
 __device__ __forceinline__ unsigned pack2(float a, float b)
 {
     unsigned r;
@@ -154,22 +92,22 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
     const int nin = nr + 2;                  // input rows (padded rows r_first .. r_first + nr + 1)
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tslot)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
                      "r"(64u)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 32) {
         for (int s = 0; s < NSLOT; ++s) {
-            bar_init(&full[s], 1);
-            bar_init(&sfree[s], 1);
+            mbar_init(&full[s], 1);
+            mbar_init(&sfree[s], 1);
         }
         for (int t = 0; t < 2; ++t) {
-            bar_init(&afull[t], 1);
-            bar_init(&aempty[t], 4);
+            mbar_init(&afull[t], 1);
+            mbar_init(&aempty[t], 4);
         }
-        bar_init(wbar, 1);
-        bar_init(dbar, 1);
+        mbar_init(wbar, 1);
+        mbar_init(dbar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -182,15 +120,15 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
-    fence_before();
+    tc_fence_before();
     __syncthreads();
-    fence_after();
+    tc_fence_after();
     const unsigned tmem = *tslot;
 
     auto wait = [&](uint64_t *b, unsigned parity) -> bool {
-        if (bar_try(b, parity)) return true;
+        if (mbar_try_wait_sleep(b, parity)) return true;
         const long long t0 = clock64();
-        while (!bar_try(b, parity)) {
+        while (!mbar_try_wait_sleep(b, parity)) {
             if (*abort_flag) return false;
             if (clock64() - t0 > (1ll << 31)) {
                 *abort_flag = 1;
@@ -206,16 +144,16 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
         int issued = 0;
         bool ok = true;
         if (lane == 0) {
-            bar_expect(wbar, WT_BYTES);
-            bulk_load(sW, wt, WT_BYTES, wbar);
+            mbar_expect_tx(wbar, WT_BYTES);
+            bulk_g2s(sW, wt, WT_BYTES, wbar);
             for (int k = 0; k < nin && ok; ++k) {
                 const int s = k % NSLOT;
                 if (k >= NSLOT) ok = wait(&sfree[s], (unsigned)(k / NSLOT - 1) & 1u);
                 if (!ok) break;
-                bar_expect(&full[s], NCI * CH_BYTES);
+                mbar_expect_tx(&full[s], NCI * CH_BYTES);
                 const int prow = r_first + k;
                 for (int c = 0; c < NCI; ++c)
-                    bulk_load(sRow + s * ROW_BYTES + c * CH_BYTES, in + (((size_t)f * NCI + c) * HP + prow) * WP,
+                    bulk_g2s(sRow + s * ROW_BYTES + c * CH_BYTES, in + (((size_t)f * NCI + c) * HP + prow) * WP,
                               CH_BYTES, &full[s]);
                 issued = k + 1;
             }
@@ -231,7 +169,7 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
         // ---------------- MMA issue ----------------
         bool ok = __all_sync(0xffffffffu, wait(wbar, 0));
         bool any = false;
-        const unsigned wbase = su32(sW), rbase = su32(sRow);
+        const unsigned wbase = smem_u32(sW), rbase = smem_u32(sRow);
         for (int r = 0; r < nr && ok; ++r) {
             // input rows r, r+1, r+2 (the first two were waited for by earlier rows)
             for (int k = (r == 0 ? 0 : r + 2); k <= r + 2 && ok; ++k)
@@ -239,7 +177,7 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
             const int t = r & 1;
             if (ok && r >= 2) ok = __all_sync(0xffffffffu, wait(&aempty[t], (unsigned)((r >> 1) - 1) & 1u));
             if (!ok) break;
-            fence_after();
+            tc_fence_after();
             const unsigned d = tmem + (unsigned)(t * 32);
 #pragma unroll
             for (int tap = 0; tap < 9; ++tap) {
@@ -247,18 +185,18 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
                 const unsigned arow = rbase + (unsigned)(((r + u) % NSLOT) * ROW_BYTES + v * 16);
 #pragma unroll
                 for (int h = 0; h < KCH / 2; ++h) {
-                    const uint64_t a = sdesc(arow + (unsigned)(2 * h * CH_BYTES), CH_BYTES, 128);
-                    const uint64_t b = sdesc(wbase + (unsigned)(tap * CS::TAP_BYTES + h * 2 * NCO * 16), NCO * 16, 128);
-                    mma_elect(d, a, b, CS::IDESC, (tap | h) ? 1u : 0u);
+                    const uint64_t a = umma_desc(arow + (unsigned)(2 * h * CH_BYTES), CH_BYTES, 128);
+                    const uint64_t b = umma_desc(wbase + (unsigned)(tap * CS::TAP_BYTES + h * 2 * NCO * 16), NCO * 16, 128);
+                    umma_elect(d, a, b, CS::IDESC, (tap | h) ? 1u : 0u);
                 }
             }
             any = true;
-            commit_elect(&afull[t]);
-            commit_elect(&sfree[r % NSLOT]);
+            umma_commit_elect(&afull[t]);
+            umma_commit_elect(&sfree[r % NSLOT]);
         }
         if (!ok && any && lane == 0) {
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                             su32(dbar))
+                             smem_u32(dbar))
                          : "memory");
             wait(dbar, 0);
         }
@@ -274,22 +212,23 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
         for (int r = 0; r < nr; ++r) {
             const int t = r & 1;
             if (!__all_sync(0xffffffffu, wait(&afull[t], (unsigned)(r >> 1) & 1u))) break;
-            fence_after();
+            tc_fence_after();
             const unsigned taddr = tmem + (unsigned)(t * 32) + ((unsigned)(32 * quarter) << 16);
             if constexpr (F32OUT) {
                 unsigned a0;
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];\n" : "=r"(a0) : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                fence_before();
+                tc_fence_before();
                 __syncwarp();
-                if (lane == 0) bar_arrive(&aempty[t]);
+                if (lane == 0) mbar_arrive(&aempty[t]);
                 reinterpret_cast<float *>(out)[((size_t)f * H + r_first + r) * W + j] = __uint_as_float(a0) + b[0];
             } else {
                 unsigned acc[32];
                 tmem_ld32(taddr, acc);
-                fence_before();
+                tmem_wait_ld();
+                tc_fence_before();
                 __syncwarp();
-                if (lane == 0) bar_arrive(&aempty[t]);
+                if (lane == 0) mbar_arrive(&aempty[t]);
                 const int prow = r_first + r + 1;
                 uint4 *dst = reinterpret_cast<uint4 *>(out) + (((size_t)f * 4) * HP + prow) * WP + (j + 1);
 #pragma unroll
@@ -303,9 +242,9 @@ conv_tc_kernel(const uint4 *__restrict__ in, const uint4 *__restrict__ wt, const
             }
         }
     }
-    fence_before();
+    tc_fence_before();
     __syncthreads();
-    fence_after();
+    tc_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(64u) : "memory");
 }

@@ -25,9 +25,12 @@
 #include <stdint.h>
 
 #include "pam_internal.h"
+#include "pam_ptx.h"
 
 namespace pam {
 namespace {
+
+using namespace ptx;
 
 constexpr int NXP = 128;                    // lateral length of this form
 constexpr int FG = kFramesPerGroup;         // frames per CTA
@@ -35,7 +38,6 @@ constexpr int NG = 2 * FG;                  // GEMM N
 constexpr int CS_B = NG / 8 * 128;          // bytes between K chunks of B
 
 __host__ __device__ __forceinline__ int K_of(int4 kq) { return kq.w; }
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 // ---- 16-bit conversions ----
 template <bool FP16>
@@ -51,83 +53,10 @@ __device__ __forceinline__ float from16(unsigned short u)
     else return __bfloat162float(__ushort_as_bfloat16(u));
 }
 
-// ---- mbarrier / bulk copy / tcgen05 (inline PTX) ----
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// try_wait that lets the hardware suspend the thread (up to about 10 us) until
-// the phase completes: waiting warps then neither issue nor poll shared memory,
-// which the tensor core reads at full bandwidth.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(10000u)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait (about one second of SM cycles); false on expiry.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > (1ll << 31)) return false;
-    return true;
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// UMMA shared-memory descriptor, canonical K-major layout without swizzle:
-// 8-row x 16-byte core matrices, `lbo` bytes between core matrices along K,
-// `sbo` bytes between 8-row groups, descriptor version 1.
-__device__ __forceinline__ uint64_t umma_desc(unsigned saddr, unsigned lbo, unsigned sbo)
-{
-    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
 
-// kind::f16 instruction descriptor: FP32 accumulators, A and B both BF16 (1)
-// or FP16 (0), K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-template <bool FP16>
-__device__ __forceinline__ unsigned umma_idesc()
-{
-    const unsigned fmt = FP16 ? 0u : 1u;
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((unsigned)(NG >> 3) << 17) | ((unsigned)(NXP >> 4) << 24);
-}
 
-__device__ __forceinline__ void umma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
-                 : "memory");
-}
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 // ------------------------------------------------------- plan tables ----
 // c_j[d] for one (row j, bin b) per CTA, d = threadIdx.x. Phasors come from
@@ -273,51 +202,10 @@ constexpr int gemm_threads() { return 384; }   // 8 build/fold warps, 1 copy war
 constexpr int REG_LAUNCH = 168, REG_CTRL = 96, REG_FOLD = 200;
 static_assert(2 * 128 * REG_FOLD + 128 * REG_CTRL <= 384 * REG_LAUNCH, "register split exceeds the launch budget");
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
 
-// MMA issued by one elected lane of a converged warp (operands stay warp-uniform).
-__device__ __forceinline__ void umma_elect(unsigned tmem_d, uint64_t a, uint64_t b, unsigned idesc, unsigned accumulate)
-{
-    asm volatile(
-        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
-        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
 
-__device__ __forceinline__ void umma_commit_elect(uint64_t *bar)
-{
-    asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
-                 " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
 
-__device__ __forceinline__ void tmem_ld8(unsigned taddr, float *v)
-{
-    unsigned r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int t = 0; t < 8; ++t) v[t] = __uint_as_float(r[t]);
-}
 
-__device__ __forceinline__ void tmem_ld16(unsigned taddr, float *v)
-{
-    unsigned r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                 "[%16];\n"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15])
-                 : "r"(taddr));
-#pragma unroll
-    for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[t]);
-}
 
 // Shared memory of one pipeline stage: NPART x (A blocks, B tile, c words).
 __host__ __device__ constexpr size_t gemm_stage_bytes(int K, int npart)
@@ -423,7 +311,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
         // -------- warp 0: bulk-copy ring; warps 1..NAP: MMA chain of aperture q --------
         const int q = warp - 1;
         const bool producer = q < 0;
-        const unsigned idesc = umma_idesc<FP16>();
+        const unsigned idesc = umma_idesc(FP16, NXP, NG);
         const int s0 = (q <= 0 ? kq.x : q == 1 ? kq.y : kq.z) / 16;
         const int s1 = (q <= 0 ? kq.y : q == 1 ? kq.z : kq.w) / 16;
         int issued = 0;
