@@ -65,7 +65,7 @@ def fp32_peak_tflops(sm_mhz):
 
 def prop_source_hash():
     h = hashlib.sha256()
-    for f in ("pam_prop.cu", "pam_internal.h"):
+    for f in ("pam_prop.cu", "pam_internal.h", "pam_ptx.h"):
         with open(os.path.join(ROOT, "paper_2412_02413_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
