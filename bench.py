@@ -361,33 +361,49 @@ def run_learned(args, w, pool, stream, dev):
     params, meta = learn.load_checkpoint()
     B = args.learned_batch
     P = pool.shape[0]
+    NS = max(1, args.streams)
     rf = pool[torch.arange(B, device=dev) % P].contiguous()
-    L = pam.Learned.from_workload(w, max_frames=B)
-    L.set_params(params)
-    L.configure(gate_tol=args.gate_tol, tensor_cores=True)
-    plan = pam.Plan.from_workload(w, max_frames=B)
-    img = torch.empty(B, w.nz, w.nx, device=dev)
-    rn = torch.empty(B, w.nz, w.nx, device=dev)
-    outs = {"image": torch.empty(B, w.nz, w.nx, device=dev), "rho_n": torch.empty(B, w.nz, w.nx, device=dev),
-            "image_as": torch.empty(B, w.nz, w.nx, device=dev)}
+    # calls alternate over NS learned forms (and NS plain plans) on NS streams, as the
+    # headline steps do: one batch's latency-bound gate and fallback overlap the next
+    # batch's band energies
+    Ls, plans = [], []
+    for _ in range(NS):
+        L_ = pam.Learned.from_workload(w, max_frames=B)
+        L_.set_params(params)
+        L_.configure(gate_tol=args.gate_tol, tensor_cores=True)
+        Ls.append(L_)
+        plans.append(pam.Plan.from_workload(w, max_frames=B))
+    streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(NS - 1)]
+    imgs = [torch.empty(B, w.nz, w.nx, device=dev) for _ in range(NS)]
+    rns = [torch.empty(B, w.nz, w.nx, device=dev) for _ in range(NS)]
+    outss = [{"image": torch.empty(B, w.nz, w.nx, device=dev), "rho_n": torch.empty(B, w.nz, w.nx, device=dev),
+              "image_as": torch.empty(B, w.nz, w.nx, device=dev)} for _ in range(NS)]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
     def timed(fn):
-        for _ in range(2):
-            fn()
+        for i in range(2 * NS):
+            fn(i)
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(args.learned_calls):
-            fn()
+        for st_ in streams[1:]:
+            st_.wait_event(e0)
+        for i in range(args.learned_calls):
+            fn(i)
+        for st_ in streams[1:]:
+            e_ = torch.cuda.Event()
+            e_.record(st_)
+            stream.wait_event(e_)
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / args.learned_calls
 
-    L.info()
-    ms_l = timed(lambda: L.as_tax(rf, image=img, rho_n=rn, stream=stream))
-    kernels = L.info()["kernel_launches"] // (args.learned_calls + 2)
-    ms_p = timed(lambda: plan.as_tax(rf, outs=outs, image_as=True, stream=stream))
+    for L_ in Ls:
+        L_.info()
+    ms_l = timed(lambda i: Ls[i % NS].as_tax(rf, image=imgs[i % NS], rho_n=rns[i % NS], stream=streams[i % NS]))
+    kernels = sum(L_.info()["kernel_launches"] for L_ in Ls) // (args.learned_calls + 2 * NS)
+    ms_p = timed(lambda i: plans[i % NS].as_tax(rf, outs=outss[i % NS], image_as=True, stream=streams[i % NS]))
+    L, plan, img, rn, outs = Ls[0], plans[0], imgs[0], rns[0], outss[0]
     res = L.as_tax(rf, image=img, rho_n=rn, stream=stream)
     plan.as_tax(rf, outs=outs, image_as=True, stream=stream)
     torch.cuda.synchronize()
@@ -405,9 +421,10 @@ def run_learned(args, w, pool, stream, dev):
                      "isnr_as": learn.isnr_esa(ia, pix)[0], "esa_learned": learn.isnr_esa(il, pix)[1],
                      "esa_tax": learn.isnr_esa(it, pix)[1], "esa_as": learn.isnr_esa(ia, pix)[1]})
     acc = learn.summarize(rows)
-    L.close()
-    plan.close()
-    return {"workload": w.name, "frames_per_call": B, "value": B / (ms_l / 1000.0), "unit": "frames/s",
+    for L_, p_ in zip(Ls, plans):
+        L_.close()
+        p_.close()
+    return {"workload": w.name, "frames_per_call": B, "streams": NS, "value": B / (ms_l / 1000.0), "unit": "frames/s",
             "us_per_frame": 1000.0 * ms_l / B, "plain_value": B / (ms_p / 1000.0),
             "plain_us_per_frame": 1000.0 * ms_p / B, "speedup_vs_plain": ms_p / ms_l, "kernels_per_call": kernels,
             "gate_tol": args.gate_tol, "accuracy_vs_plain": acc,
@@ -618,7 +635,7 @@ def main():
     ap.add_argument("--batch-loop-frames", type=int, default=32, help="frames of the one-frame-call loop")
     ap.add_argument("--batch-only", action="store_true", help="time only the uneven batch (profiling aid)")
     ap.add_argument("--learned-batch", type=int, default=256, help="frames per learned-form call (0: skip)")
-    ap.add_argument("--learned-calls", type=int, default=5)
+    ap.add_argument("--learned-calls", type=int, default=6)
     ap.add_argument("--gate-tol", type=float, default=0.25, help="error-gate bound of the learned form")
     ap.add_argument("--learned-only", action="store_true", help="time only the learned form (profiling aid)")
     args = ap.parse_args()
