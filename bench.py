@@ -520,23 +520,26 @@ def run_ours(args):
 
     # End to end through the host-buffer entry points: every step uploads its frame
     # from pinned memory and downloads its image and rho_n into pinned memory.
-    # Pipelined (the value reported): two plans on two streams with
-    # pam_as_xcorr_host_async, so one frame's copies overlap the other's kernels; a
-    # step's host buffers are reused two steps later, after its download has landed.
+    # Pipelined (the value reported): max(2, --streams) plans on as many streams with
+    # pam_as_xcorr_host_async, so one frame's copies overlap another's kernels; a
+    # step's host buffers are reused that many steps later, after its download landed.
     # Blocking: pam_as_xcorr_host, which returns with the results in host memory.
     n_host = min(8, P)
     rf_host = torch.from_numpy(pool_np[: n_host * F].reshape(n_host, F, w.n_elem, w.nt).copy()).pin_memory()
-    outs_host = [(torch.empty(F, w.nz, w.nx).pin_memory(), torch.empty(F, w.nz, w.nx).pin_memory()) for _ in range(2)]
+    NE = max(2, NS)                      # frames in flight
+    outs_host = [(torch.empty(F, w.nz, w.nx).pin_memory(), torch.empty(F, w.nz, w.nx).pin_memory())
+                 for _ in range(NE)]
     outs_np = [(a.numpy(), b.numpy()) for a, b in outs_host]
-    plans2 = (plan, plans[1] if NS > 1 else pam.Plan.from_workload(w, max_frames=F))
-    streams2 = (stream, streams[1] if NS > 1 else torch.cuda.Stream(device=dev))
-    done = [torch.cuda.Event(), torch.cuda.Event()]
+    extra = [pam.Plan.from_workload(w, max_frames=F) for _ in range(NE - NS)]
+    plans2 = plans + extra
+    streams2 = streams + [torch.cuda.Stream(device=dev) for _ in range(NE - NS)]
+    done = [torch.cuda.Event() for _ in range(NE)]
     e2e_steps = max(1, min(args.steps, 500))
 
     def e2e_pipelined(n):
         for i in range(n):
-            k = i & 1
-            if i >= 2:
+            k = i % NE
+            if i >= NE:
                 done[k].synchronize()
             plans2[k].as_xcorr_host_async(rf_host[i % n_host].numpy(), outs_np[k][0], outs_np[k][1],
                                           stream=streams2[k])
@@ -557,8 +560,8 @@ def run_ours(args):
         plan.as_xcorr_host(rf_host[i % n_host].numpy(), outs_np[0][0], outs_np[0][1], stream=stream)
     t_blk = dist.max_over_ranks(time.perf_counter() - t0, device=dev)
     e2e_blocking = dist.sum_over_ranks(e2e_steps * F, device=dev) / t_blk
-    if NS == 1:
-        plans2[1].close()
+    for p_ in extra:
+        p_.close()
 
     # Batched forms: 64 frames per call, the plain FP32 path and the tensor-core forms.
     forms = {} if args.no_forms else run_forms(args, w, pool, stream, dev)
@@ -591,7 +594,7 @@ def run_ours(args):
                              " > 129 MB L2", "parallelism": f"frames sharded over {world} GPU(s)"},
             "e2e": {"value": e2e_value, "unit": "frames/s",
                     "h2d_bytes_per_step": F * w.n_elem * w.nt * 4, "d2h_bytes_per_step": 2 * F * w.nz * w.nx * 4,
-                    "mode": "pam_as_xcorr_host_async, two plans on two streams (copies overlap kernels)",
+                    "mode": f"pam_as_xcorr_host_async, {NE} plans on {NE} streams (copies overlap kernels)",
                     "blocking_value": e2e_blocking},
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "kernel": "prop_corr_kernel<3,128>", "achieved": achieved_tf,
