@@ -77,6 +77,8 @@ def test_desc_defaults(lib):
     ("nz", 0, 1), ("z0_m", -1e-3, 1), ("dz_m", 0.0, 1), ("n_apod", 4, 1), ("eps", 0.0, 1),
     ("eps", 1.5, 1), ("max_frames", 0, 1), ("flags", 0x100, 1), ("flags", 0x30, 1), ("flags", 0x10, 2),
     ("nx", 128, 2), ("pattern_m", 0, 1),
+    ("flags", 0x12, 2),                           # zero-stuffing runs on the plain FP32 path only
+    ("flags", 0x82, 2),
     ("f_lo_hz", 9e6, 1),
 ])
 def test_bad_descriptor_is_rejected(lib, field, value, status):
@@ -167,3 +169,35 @@ def test_batch_null_handles(lib):
     assert lib.pam_batch_layout(None, None, None, None, None) == 1
     assert lib.pam_batch_bins(None, 0, None) == 0
     lib.pam_batch_destroy(None)
+
+
+def test_zero_stuffing_needs_twice_the_lateral_length(lib):
+    d = _desc(lib, flags=0x2, nx=64)              # 64 elements: nx must be 128
+    s, _ = _create(lib, d)
+    assert s == 2
+
+
+def test_new_entry_points_validate_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.pam_learn_n_params() == 29505
+    assert lib.pam_learn_state_size() == 3 * 29505
+    assert lib.pam_learn_create(None, ctypes.byref(h)) == 1
+    d = _desc(lib, n_apod=2)
+    assert lib.pam_learn_create(ctypes.byref(d), ctypes.byref(h)) == 1 and not h.value   # the TAX weight needs 3
+    d = _desc(lib, flags=0x10)
+    assert lib.pam_learn_create(ctypes.byref(d), ctypes.byref(h)) == 2 and not h.value   # plain path only
+    lib.pam_learn_destroy(None)
+    assert lib.pam_learn_set_params(None, None, 0) == 1
+    assert lib.pam_learn_get_params(None, None, 0) == 1
+    assert lib.pam_learn_get_state(None, None, 0, None) == 1
+    assert lib.pam_learn_set_state(None, None, 0, 0) == 1
+    assert lib.pam_learn_configure(None, 0.1, 0) == 1
+    assert lib.pam_learn_feature_bytes(None) == 0
+    assert lib.pam_learn_tax(None, None, 1, None, None, None, None, None) == 1
+    assert lib.pam_learn_info(None, None, None, None) == 1
+    assert lib.pam_as3(None, None, 1, None, None) == 1
+    assert lib.pam_debug_expire_wait(None, None) == 1
+    assert lib.pam_as_xcorr_host_async(None, None, 1, None, None, None) == 1
+    assert lib.pam_image_metrics(None, 1, 8, 8, 0.0, 1.0, 0.0, 1.0, 0.7, None, None) == 1
+    assert lib.pam_image_metrics(None, 1, 8, 8, 0.0, 1.0, 0.0, 1.0, 1.5, None, None) == 1   # alpha in (0, 1)
+    assert lib.pam_image_metrics(None, 0, 8, 8, 0.0, 1.0, 0.0, 1.0, 0.7, None, None) == 0   # no frames: nothing to do
