@@ -49,6 +49,12 @@ def fused_flops_per_frame(n_bins, nz, nx, n_apod=3):
     return float(n_bins * nz * per_row)
 
 
+def workload_config(w, frames_per_step):
+    """The workload part of the JSON line's config, shared by both arms."""
+    return {"workload": w.name, "frames_per_step": frames_per_step, "n_elem": w.n_elem, "n_samples": w.nt,
+            "nx": w.nx, "nz": w.nz, "n_bins": int(len(w.bins())), "n_apod": 3}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -212,7 +218,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "frames_per_step": 1},
+            "config": {**workload_config(w, 1), "streams": 1,
+                       "sample": "oracle on a bounded sample of bins x depth rows, scaled to whole frames"},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads, "kind": "oracle",
                              "sample": sample + " per step"},
@@ -587,9 +594,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Green's-function point sources, 20 dB channel SNR)",
-            "config": {"workload": w.name, "frames_per_step": F, "streams": NS, "n_elem": w.n_elem,
-                       "n_samples": w.nt,
-                       "nx": w.nx, "nz": w.nz, "n_bins": int(plan.n_bins), "n_apod": 3,
+            "config": {**workload_config(w, F), "streams": NS,
                        "l2": f"rotating pool of {P} distinct input frames ({P * w.n_elem * w.nt * 4 / 1e6:.0f} MB)"
                              " > 129 MB L2", "parallelism": f"frames sharded over {world} GPU(s)"},
             "e2e": {"value": e2e_value, "unit": "frames/s",
