@@ -525,6 +525,18 @@ def run_ours(args):
     frames_total = dist.sum_over_ranks(args.steps * F, device=dev)
     value = frames_total / (ms_max / 1000.0)
 
+    # The dominant kernel alone: a short single-stream run right after the timed
+    # region (with several streams its launches share the SMs with the other
+    # streams' kernels, which lengthens them).
+    iso_steps = max(1, min(args.steps, 300))
+    plan.profile_enable(True)
+    for i in range(iso_steps):
+        s_ = (i * F) % (P - F + 1)
+        plan.as_tax(pool[s_:s_ + F], outs=outs, stream=stream)
+    torch.cuda.synchronize()
+    iso_ms, iso_n, _ = plan.profile_read()
+    plan.profile_enable(False)
+
     # End to end through the host-buffer entry points: every step uploads its frame
     # from pinned memory and downloads its image and rho_n into pinned memory.
     # Pipelined (the value reported): max(2, --streams) plans on as many streams with
@@ -607,7 +619,11 @@ def run_ours(args):
                          "peak_basis": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
                                        f"(sm_max_mhz, {peak_kind})",
                          "flops_per_launch": flops, "avg_launch_us": avg_launch_s * 1e6,
-                         "share_of_step": (prop_ms / ms) if ms > 0 else None},
+                         "share_of_step": (prop_ms / ms) if ms > 0 else None,
+                         "alone": {"avg_launch_us": 1000.0 * iso_ms / max(iso_n, 1),
+                                   "achieved": flops / (iso_ms / max(iso_n, 1) / 1000.0) / 1e12,
+                                   "frac": flops / (iso_ms / max(iso_n, 1) / 1000.0) / 1e12 / peak_tf,
+                                   "note": f"{iso_n} launches on one stream after the timed region"}},
             "clocks": ck,
             "forms": forms,
             "batch": batch,
