@@ -232,6 +232,46 @@ def as_tax(geom: Geometry, rf: np.ndarray, apod: np.ndarray, eps: float = 1e-3, 
     return as_xcorr(geom, rf, apod, eps, threads)
 
 
+# ---- 2x lateral padding (Sec. II-D) ----
+# Reading: the channel record is extended by n_elem zero channels appended
+# after the last element (element e stays on channel e, at the element pitch),
+# the lateral transforms of Eq. 1-2 run over 2 n_elem points, and the image is
+# cropped back to the n_elem element columns. The TAX weight is normalised to
+# its maximum over the cropped image (Eq. 11), and I = rho_n^2 E_full there.
+def _padded(geom: Geometry, rf: np.ndarray, apod):
+    ne = geom.n_elem
+    g2 = Geometry(2 * ne, geom.nt, geom.fs, geom.c, geom.pitch, geom.nz, geom.z0, geom.dz, geom.bins,
+                  geom.evanescent_zero)
+    rf = np.asarray(rf, dtype=np.float32)
+    rf2 = np.zeros((2 * ne, rf.shape[-1]), dtype=np.float32)
+    rf2[:ne] = rf
+    a2 = None
+    if apod is not None:
+        apod = np.asarray(apod, dtype=np.float64)
+        a2 = np.zeros(apod.shape[:-1] + (2 * ne,))
+        a2[..., :ne] = apod
+    return g2, rf2, a2
+
+
+def as_backprop_pad2x(geom: Geometry, rf: np.ndarray, apod=None, threads=None) -> np.ndarray:
+    """[nz][n_elem] AS energy (Eq. 3) with 2x lateral padding."""
+    g2, rf2, a2 = _padded(geom, rf, apod)
+    return np.ascontiguousarray(as_backprop(g2, rf2, a2, threads)[:, :geom.n_elem])
+
+
+def as_xcorr_pad2x(geom: Geometry, rf: np.ndarray, apod: np.ndarray, eps: float = 1e-3, threads=None):
+    """AS-DAX / AS-TAX (Eq. 5, 10-11) with 2x lateral padding: the maps of
+    :func:`as_xcorr` on the padded record, cropped to the element columns, with
+    rho_n renormalised over the crop and the image rebuilt from it."""
+    g2, rf2, a2 = _padded(geom, rf, apod)
+    full = as_xcorr(g2, rf2, a2, eps, threads)
+    out = {k: np.ascontiguousarray(v[..., :geom.n_elem]) for k, v in full.items()}
+    rho_n = out["rho_n"] / out["rho_n"].max()
+    out["rho_n"] = rho_n
+    out["image"] = rho_n * rho_n * out["image_as"]
+    return out
+
+
 def set_mutation(mid: int) -> None:
     """Test hook: switch on deliberate mistake ``mid`` (0 restores the oracle)."""
     lib().pam_oracle_set_mutation(int(mid))

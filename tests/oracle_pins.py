@@ -341,16 +341,20 @@ def pin_green_sources_near_truth():
 
 
 # ---------------------------------------------------------- brute force --
-def numpy_as_xcorr(rf, fs, pitch, nz, z0, dz, bins, A, eps=EPS):
-    """Independent tiny-case implementation with numpy's FFT routines."""
+def numpy_as_xcorr(rf, fs, pitch, nz, z0, dz, bins, A, eps=EPS, pad=1):
+    """Independent tiny-case implementation with numpy's FFT routines. With
+    pad = 2 the lateral transforms use numpy's zero padding to 2 n_elem points
+    (``fft(..., n=2 ne)``) and the fields are cropped to the n_elem element
+    columns before the sums."""
     ne, nt = rf.shape
+    nf = pad * ne
     S = np.fft.rfft(rf.astype(np.float64), axis=1)[:, bins].T         # [nb][ne]
-    kx = 2 * np.pi * np.fft.fftfreq(ne, d=pitch)
+    kx = 2 * np.pi * np.fft.fftfreq(nf, d=pitch)
     k = 2 * np.pi * (np.asarray(bins) * fs / nt) / C
     kz = np.sqrt((k[:, None] ** 2 - kx[None, :] ** 2).astype(complex))  # principal branch
     z = z0 + np.arange(nz) * dz
-    ph = np.exp(1j * kz[:, None, :] * z[None, :, None])                # [nb][nz][nx]
-    p = [np.fft.ifft(np.fft.fft(a[None, :] * S, axis=1)[:, None, :] * ph, axis=2) for a in A]
+    ph = np.exp(1j * kz[:, None, :] * z[None, :, None])                # [nb][nz][nf]
+    p = [np.fft.ifft(np.fft.fft(a[None, :] * S, n=nf, axis=1)[:, None, :] * ph, axis=2)[..., :ne] for a in A]
     Aq = [np.sum(np.abs(x) ** 2, axis=0) for x in p]
     pairs = [(0, 1), (1, 2), (2, 0)] if len(A) == 3 else [(0, 1)]
     rho = []
@@ -379,6 +383,44 @@ def pin_numpy_brute_force():
         for key in ("image", "rho_n", "rho_pairs", "image_as"):
             err = np.max(np.abs(got[key] - want[key])) / np.max(np.abs(want[key]))
             assert err < 1e-10, (na, key, err)
+
+
+def pin_pad2x_numpy_brute_force():
+    """2x lateral padding (Sec. II-D): AS-TAX and AS-DAX of the padded,
+    cropped oracle against numpy's zero-padded FFTs on a tiny case."""
+    ne, nt, fs, pitch = 16, 128, 20e6, 0.3e-3
+    rf = _rand_rf(ne, nt, 23)
+    bins = oracle.band_bins(nt, fs, 1e6, 8e6)
+    nz, z0, dz = 5, 2e-3, 0.8e-3
+    g = oracle.Geometry(ne, nt, fs, C, pitch, nz, z0, dz, bins)
+    for na in (3, 2):
+        A = oracle.pattern(ne, na, 2)
+        got = oracle.as_xcorr_pad2x(g, rf, A)
+        want = numpy_as_xcorr(rf, fs, pitch, nz, z0, dz, bins, A, pad=2)
+        for key in ("image", "rho_n", "rho_pairs", "image_as"):
+            assert got[key].shape == want[key].shape, key
+            err = np.max(np.abs(got[key] - want[key])) / np.max(np.abs(want[key]))
+            assert err < 1e-10, (na, key, err)
+        assert got["rho_n"].max() == 1.0
+
+
+def pin_pad2x_z0_and_effect():
+    """At the array face the padded, cropped energy is the channel power of
+    each element, sum_k |S[k][i]|^2 (so the crop keeps the element columns).
+    At depth the padding changes the map: the wrap-around of the n_elem-point
+    transforms is gone."""
+    ne, nt = 16, 128
+    rf = _rand_rf(ne, nt, 24)
+    bins = [9, 17, 30]
+    g0 = oracle.Geometry(ne, nt, 20e6, C, 0.3e-3, 1, 0.0, 1e-3, bins)
+    e0 = oracle.as_backprop_pad2x(g0, rf)[0]
+    S = np.fft.rfft(rf.astype(np.float64), axis=1)[:, bins]
+    want = np.sum(np.abs(S) ** 2, axis=1)
+    assert np.max(np.abs(e0 - want)) < 1e-11 * want.max()
+    g = _geom(ne, nt, nz=4, z0=6e-3)
+    ep, eu = oracle.as_backprop_pad2x(g, rf), oracle.as_backprop(g, rf)
+    assert ep.shape == eu.shape
+    assert np.max(np.abs(ep - eu)) > 1e-2 * eu.max()
 
 
 def pin_band_bins_of_workloads():
