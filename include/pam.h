@@ -78,6 +78,15 @@ typedef enum {
  * path only: not with PAM_FORM_GEMM_*, batches, the learned form or
  * pam_as_tax_static. */
 #define PAM_LATERAL_UPSAMPLE2X 0x2u
+/* 2x padding in the channel direction (Sec. II-D, the other reading of its
+ * "2x" lateral extension): n_elem zero channels are appended after the last
+ * element, the lateral transforms of Eq. 1-2 run over 2 n_elem points at the
+ * element pitch (so the circular wrap-around of an n_elem-point transform is
+ * gone), and every map is cropped back to the n_elem element columns: nx =
+ * n_elem (built: n_elem 8..64). rho_n is normalised to its maximum over the
+ * cropped image and I = rho_n^2 E_full there (Eq. 11). Plain FP32 path only,
+ * like PAM_LATERAL_UPSAMPLE2X (not both), and without the `fields` output. */
+#define PAM_LATERAL_PAD2X 0x4u
 /* Tensor-core form of the propagation (at most one of these; default = plain FP32 FFT path).
  * For a bin w_k and depth row z_j, the element-to-pixel propagator of Eq. 1-2 is circulant:
  *   p~(x_i, z_j) = sum_e c_j[(i - e) mod nx] a_q[e] S[e],
@@ -101,8 +110,9 @@ typedef struct {
     double fs_hz;         /* sampling rate (Hz), > 0 */
     double c_mps;         /* sound speed (m/s), > 0 */
     int n_samples;        /* samples per channel nt: a power of two, 64..8192 */
-    int nx;               /* lateral pixels = lateral DFT length: 0 or n_elem (2 n_elem with
-                             PAM_LATERAL_UPSAMPLE2X). Built: 16, 32, 64, 128 */
+    int nx;               /* lateral pixels: 0 or n_elem (2 n_elem with PAM_LATERAL_UPSAMPLE2X).
+                             The lateral DFT length is nx, or 2 n_elem with PAM_LATERAL_PAD2X.
+                             Built lateral lengths: 16, 32, 64, 128 */
     int nz;               /* depth rows, 1..65535 */
     double z0_m;          /* depth of row 0 from the array face (m), >= 0 */
     double dz_m;          /* row spacing (m), > 0 */
@@ -114,7 +124,8 @@ typedef struct {
     const float *apod;    /* host [n_apod][n_elem] real weights, or NULL for Pattern-m */
     int pattern_m;        /* Pattern-m (Sec. II-A): element e in aperture q iff floor(e/m) mod n_apod == q */
     float eps;            /* NCC floor (Sec. II-A, usually 0.001), 0 < eps <= 1 */
-    unsigned flags;       /* PAM_EVANESCENT_ZERO, PAM_LATERAL_UPSAMPLE2X, at most one PAM_FORM_GEMM_* */
+    unsigned flags;       /* PAM_EVANESCENT_ZERO, PAM_LATERAL_UPSAMPLE2X or PAM_LATERAL_PAD2X,
+                             at most one PAM_FORM_GEMM_* */
     int max_frames;       /* frames per kernel batch; larger calls run in batches of this size */
 } pam_plan_desc;
 
@@ -157,7 +168,7 @@ pam_status pam_plan_set_split(pam_plan_t p, int n_split);
  *   fields      device complex64 as interleaved float pairs
  *               [n_frames][n_bins][nz][nx][2], or NULL. This is a debug and test
  *               output: it writes every monochromatic field p~(x_i, z_j, w_k)
- *               to memory.
+ *               to memory. PAM_ERR_UNSUPPORTED with PAM_LATERAL_PAD2X.
  *   stream      cudaStream_t or NULL */
 pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod_index,
                            float *energy, float *fields, void *stream);

@@ -74,6 +74,7 @@ void free_plan_memory(pam_plan_s *p)
     fr(p->t.phase); fr(p->t.live); fr(p->t.bin_evan);
     fr(p->w.S); fr(p->w.Q); fr(p->w.part); fr(p->w.rho_tmp); fr(p->w.e_tmp);
     fr(p->w.fmax); fr(p->w.status); fr(p->w.rf_stage); fr(p->w.img_stage); fr(p->w.rho_stage);
+    fr(p->w.pad_img); fr(p->w.pad_rho); fr(p->w.pad_as); fr(p->w.pad_pairs);
     fr(p->t.c_hi); fr(p->t.c_lo); fr(p->t.ktab); fr(p->t.kwgt); fr(p->w.Bhi); fr(p->w.Blo); fr(p->w.smax);
     p->t = pam::Tables{};
     p->w = pam::Workspace{};
@@ -111,13 +112,17 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     if (!is_pow2(d->n_samples))
         return fail(PAM_ERR_UNSUPPORTED, "n_samples must be a power of two for the radix-4/2 time FFT");
     const bool up2 = (d->flags & PAM_LATERAL_UPSAMPLE2X) != 0;
-    const int nev = up2 ? 2 * d->n_elem : d->n_elem;
-    int nx = d->nx == 0 ? nev : d->nx;
-    if (nx != nev)
+    const bool pad2 = (d->flags & PAM_LATERAL_PAD2X) != 0;
+    if (up2 && pad2) return fail(PAM_ERR_INVALID_ARG, "PAM_LATERAL_UPSAMPLE2X and PAM_LATERAL_PAD2X exclude each other");
+    const int nev = up2 || pad2 ? 2 * d->n_elem : d->n_elem;   // channels of S = lateral DFT length
+    const int nx_out = up2 ? nev : d->n_elem;                    // image columns
+    int nx = d->nx == 0 ? nx_out : d->nx;
+    if (nx != nx_out)
         return fail(PAM_ERR_UNSUPPORTED, up2 ? "nx must be 2 n_elem with PAM_LATERAL_UPSAMPLE2X"
                                              : "nx must equal n_elem (or 2 n_elem with PAM_LATERAL_UPSAMPLE2X)");
-    if (nx != 16 && nx != 32 && nx != 64 && nx != 128)
-        return fail(PAM_ERR_UNSUPPORTED, "lateral length nx must be 16, 32, 64 or 128");
+    if (nev != 16 && nev != 32 && nev != 64 && nev != 128)
+        return fail(PAM_ERR_UNSUPPORTED, "the lateral DFT length (n_elem, or 2 n_elem with PAM_LATERAL_UPSAMPLE2X "
+                                         "or PAM_LATERAL_PAD2X) must be 16, 32, 64 or 128");
     if (d->nz < 1 || d->nz > 65535) return fail(PAM_ERR_INVALID_ARG, "nz must be in [1, 65535]");
     if (!std::isfinite(d->z0_m) || d->z0_m < 0.0) return fail(PAM_ERR_INVALID_ARG, "z0_m must be finite and >= 0");
     if (!finite_pos(d->dz_m)) return fail(PAM_ERR_INVALID_ARG, "dz_m must be finite and > 0");
@@ -126,11 +131,12 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     if (d->max_frames < 1 || d->max_frames > 65535) return fail(PAM_ERR_INVALID_ARG, "max_frames must be in [1, 65535]");
     const unsigned form_bits =
         PAM_FORM_GEMM_BF16 | PAM_FORM_GEMM_FP16 | PAM_FORM_GEMM_BF16_SPLIT | PAM_FORM_GEMM_FP16_SPLIT;
-    if (d->flags & ~(PAM_EVANESCENT_ZERO | PAM_LATERAL_UPSAMPLE2X | form_bits))
+    if (d->flags & ~(PAM_EVANESCENT_ZERO | PAM_LATERAL_UPSAMPLE2X | PAM_LATERAL_PAD2X | form_bits))
         return fail(PAM_ERR_INVALID_ARG, "unknown flag bits");
     const unsigned form = d->flags & form_bits;
     if (form & (form - 1)) return fail(PAM_ERR_INVALID_ARG, "at most one PAM_FORM_GEMM_* flag");
     if (form && up2) return fail(PAM_ERR_UNSUPPORTED, "PAM_LATERAL_UPSAMPLE2X runs on the plain FP32 path only");
+    if (form && pad2) return fail(PAM_ERR_UNSUPPORTED, "PAM_LATERAL_PAD2X runs on the plain FP32 path only");
 
     const int nt = d->n_samples;
     p->bins.clear();
@@ -174,10 +180,12 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     p->d.n_bins = (int)p->bins.size();
     p->ne = ne;
     p->nev = nev;
+    p->chan_step = up2 ? 2 : 1;
     p->pitch_x = up2 ? 0.5 * d->pitch_m : d->pitch_m;
     p->nt = nt;
     p->log2nt = ilog2(nt);
-    p->nx = nx;
+    p->nx = nev;
+    p->nx_out = nx;
     p->nz = d->nz;
     p->n_bins = (int)p->bins.size();
     p->n_apod = na;
@@ -269,17 +277,25 @@ pam_status alloc_plan(pam_plan_s *p)
         PAM_TRY(cudaMemcpy(p->t.ktab, p->ktab_h.data(), p->K * sizeof(short), cudaMemcpyHostToDevice));
         PAM_TRY(cudaMemcpy(p->t.kwgt, p->kwgt_h.data(), p->K * sizeof(float), cudaMemcpyHostToDevice));
     }
+    if (p->nx_out != p->nx) {   // PAM_LATERAL_PAD2X: full-width maps, cropped after the epilogue
+        PAM_TRY(dalloc(&p->w.pad_img, F * npix));
+        if (p->n_apod >= 2) {
+            PAM_TRY(dalloc(&p->w.pad_rho, F * npix));
+            PAM_TRY(dalloc(&p->w.pad_as, F * npix));
+            PAM_TRY(dalloc(&p->w.pad_pairs, F * (p->n_apod == 3 ? 3 : 1) * npix));
+        }
+    }
     PAM_TRY(cudaMemset(p->w.status, 0, sizeof(int)));
     PAM_TRY(cudaMemcpy(p->t.bins, p->bins.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
     {
         // apodization per channel of S: element e's weight at channel e (or 2e when zero-stuffed)
-        const size_t step = (size_t)(p->nev / p->ne);
+        const size_t step = (size_t)p->chan_step;
         std::vector<float> av((size_t)p->n_apod * ne, 0.0f);
         for (int q = 0; q < p->n_apod; ++q)
             for (int e = 0; e < p->ne; ++e) av[(size_t)q * ne + step * e] = p->apod[(size_t)q * p->ne + e];
         PAM_TRY(cudaMemcpy(p->t.apod, av.data(), av.size() * sizeof(float), cudaMemcpyHostToDevice));
-        // zero-stuffed channels are never written: clear them once
-        if (step > 1) PAM_TRY(cudaMemset(p->w.S, 0, F * nb * ne * sizeof(float2)));
+        // zero-stuffed or padding channels are never written: clear them once
+        if (p->nev > p->ne) PAM_TRY(cudaMemset(p->w.S, 0, F * nb * ne * sizeof(float2)));
     }
     std::vector<float> ones(ne, 1.0f);
     PAM_TRY(cudaMemcpy(p->t.ones, ones.data(), ne * sizeof(float), cudaMemcpyHostToDevice));
@@ -330,18 +346,20 @@ pam::EpiOut epi_out(const pam_plan_s *p, float *main, float *rho_n, float *rho_p
 pam_status run_xcorr(pam_plan_t p, const float *rf, int n_frames, float *image, float *rho_n,
                      float *rho_pairs, float *image_as, cudaStream_t st)
 {
-    const size_t npix = (size_t)p->nz * p->nx;
+    const size_t npix = (size_t)p->nz * p->nx_out;   // caller's maps
     const size_t fr_in = (size_t)p->ne * p->nt;
     const int npairs = p->n_apod == 3 ? 3 : 1;
+    const bool crop = p->nx_out != p->nx;             // PAM_LATERAL_PAD2X
     for (int f0 = 0; f0 < n_frames; f0 += p->max_frames) {
         int Fc = std::min(p->max_frames, n_frames - f0);
+        float *c_img = image + (size_t)f0 * npix, *c_rho = rho_n ? rho_n + (size_t)f0 * npix : nullptr;
+        float *c_pairs = rho_pairs ? rho_pairs + (size_t)f0 * npairs * npix : nullptr;
+        float *c_as = image_as ? image_as + (size_t)f0 * npix : nullptr;
         cudaError_t e = pam::launch_time_fft(*p, rf + (size_t)f0 * fr_in, Fc, st);
         if (e != cudaSuccess) return cuda_fail(e, "time FFT launch");
         if (p->form) {
             // tensor-core form: pack operands, GEMM per (row, bin), epilogue from its sums
-            pam::EpiOut out = epi_out(p, image + (size_t)f0 * npix, rho_n ? rho_n + (size_t)f0 * npix : nullptr,
-                                      rho_pairs ? rho_pairs + (size_t)f0 * npairs * npix : nullptr,
-                                      image_as ? image_as + (size_t)f0 * npix : nullptr);
+            pam::EpiOut out = epi_out(p, c_img, c_rho, c_pairs, c_as);
             if ((e = prof_begin(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
             e = pam::launch_prec(*p, Fc, st);
             if (e != cudaSuccess) return cuda_fail(e, "tensor-core form launch");
@@ -354,9 +372,9 @@ pam_status run_xcorr(pam_plan_t p, const float *rf, int n_frames, float *image, 
         e = pam::launch_lateral(*p, Fc, p->n_apod, p->t.apod, st);
         if (e != cudaSuccess) return cuda_fail(e, "lateral DFT launch");
         int ns = pam::choose_split(*p, Fc);
-        pam::EpiOut out = epi_out(p, image + (size_t)f0 * npix, rho_n ? rho_n + (size_t)f0 * npix : nullptr,
-                                  rho_pairs ? rho_pairs + (size_t)f0 * npairs * npix : nullptr,
-                                  image_as ? image_as + (size_t)f0 * npix : nullptr);
+        // with padding the epilogue writes full-width maps (rho_n and E always) for the crop
+        pam::EpiOut out = crop ? epi_out(p, p->w.pad_img, p->w.pad_rho, c_pairs ? p->w.pad_pairs : nullptr, p->w.pad_as)
+                               : epi_out(p, c_img, c_rho, c_pairs, c_as);
         if ((e = prof_begin(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
         e = pam::launch_prop(*p, Fc, p->n_apod, ns, nullptr, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "propagate/correlate launch");
@@ -364,6 +382,12 @@ pam_status run_xcorr(pam_plan_t p, const float *rf, int n_frames, float *image, 
         e = pam::launch_epilogue(*p, Fc, p->n_apod, ns, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "epilogue launch");
         p->kernels += 3 + pam::epilogue_kernels(p->n_apod, ns);
+        if (crop) {
+            e = pam::launch_pad_crop(p->w.pad_rho, p->w.pad_as, p->w.pad_pairs, npairs, Fc, p->nz, p->nx, p->nx_out,
+                                     c_img, c_rho, c_pairs, c_as, st);
+            if (e != cudaSuccess) return cuda_fail(e, "crop launch");
+            p->kernels += 1;
+        }
     }
     return PAM_OK;
 }
@@ -454,9 +478,11 @@ pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod
     if ((s = check_dev_ptr(rf, "rf", true)) != PAM_OK) return s;
     if ((s = check_dev_ptr(energy, "energy", true)) != PAM_OK) return s;
     if ((s = check_dev_ptr(fields, "fields", false)) != PAM_OK) return s;
+    const bool crop = p->nx_out != p->nx;   // PAM_LATERAL_PAD2X
+    if (fields && crop) return fail(PAM_ERR_UNSUPPORTED, "the fields output is not built with PAM_LATERAL_PAD2X");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const float *apod = apod_index < 0 ? p->t.ones : p->t.apod + (size_t)apod_index * p->nev;
-    const size_t npix = (size_t)p->nz * p->nx;
+    const size_t npix = (size_t)p->nz * p->nx_out;
     const size_t fr_in = (size_t)p->ne * p->nt;
     for (int f0 = 0; f0 < n_frames; f0 += p->max_frames) {
         int Fc = std::min(p->max_frames, n_frames - f0);
@@ -466,7 +492,7 @@ pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod
         if (e != cudaSuccess) return cuda_fail(e, "lateral DFT launch");
         int ns = pam::choose_split(*p, Fc);
         float *fl = fields ? fields + (size_t)f0 * p->n_bins * npix * 2 : nullptr;
-        pam::EpiOut out = epi_out(p, energy + (size_t)f0 * npix, nullptr, nullptr, nullptr);
+        pam::EpiOut out = epi_out(p, crop ? p->w.pad_img : energy + (size_t)f0 * npix, nullptr, nullptr, nullptr);
         if ((e = prof_begin(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
         e = pam::launch_prop(*p, Fc, 1, ns, fl, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "propagate launch");
@@ -474,6 +500,12 @@ pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod
         e = pam::launch_epilogue(*p, Fc, 1, ns, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "epilogue launch");
         p->kernels += 3 + pam::epilogue_kernels(1, ns);
+        if (crop) {   // element columns of the padded energy map
+            const size_t w_out = (size_t)p->nx_out * sizeof(float), w_in = (size_t)p->nx * sizeof(float);
+            e = cudaMemcpy2DAsync(energy + (size_t)f0 * npix, w_out, p->w.pad_img, w_in, w_out, (size_t)Fc * p->nz,
+                                  cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "crop copy");
+        }
     }
     return PAM_OK;
 }
@@ -522,7 +554,7 @@ pam_status pam_as_xcorr_host_async(pam_plan_t p, const float *rf_host, int n_fra
     if (n_frames == 0) return PAM_OK;
     if (!rf_host || !image_host) return fail(PAM_ERR_INVALID_ARG, "rf_host and image_host are required");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t npix = (size_t)p->nz * p->nx;
+    const size_t npix = (size_t)p->nz * p->nx_out;
     const size_t fr_in = (size_t)p->ne * p->nt;
     const size_t F = p->max_frames;
     cudaError_t e;

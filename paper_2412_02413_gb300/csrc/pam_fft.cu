@@ -136,14 +136,15 @@ __device__ float2 *stockham(float2 *x, float2 *y, int n, int log2n, int batch, c
 // memory. The two half-length spectra are then separated:
 //   E[k] = (Z[k] + conj Z[M-k]) / 2,  O[k] = (Z[k] - conj Z[M-k]) / (2i),
 //   X[k] = E[k] + exp(-2 pi i k / nt) O[k].
-// Only the selected bins leave the CTA, as S[f][b][c] with c = e, or c = 2e
-// when the channels are zero-stuffed (nev = 2 ne). Block (0, f) also clears
-// the frame's rho maximum for the epilogue.
+// Only the selected bins leave the CTA, as S[f][b][c] with c = cstep e
+// (cstep = 2 when the channels are zero-stuffed) in rows of nev channels.
+// Block (0, f) also clears the frame's rho maximum for the epilogue.
 constexpr int TFFT_THREADS = 256;
 
 __global__ void __launch_bounds__(TFFT_THREADS)
 time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const float2 *__restrict__ tw,
-                const int *__restrict__ bins, int n_bins, float2 *__restrict__ S, int nev, unsigned *__restrict__ fmax)
+                const int *__restrict__ bins, int n_bins, float2 *__restrict__ S, int nev, int cstep,
+                unsigned *__restrict__ fmax)
 {
     extern __shared__ __align__(16) float2 sbuf[];
     const int M = nt >> 1;
@@ -161,7 +162,7 @@ time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const 
         const float2 zk = Z[k], zm = Z[M - k];
         const float2 E = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         const float2 O = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-        S[((size_t)f * n_bins + b) * nev + (size_t)e * (nev / ne)] = cadd(E, cmul(tw[k], O));
+        S[((size_t)f * n_bins + b) * nev + (size_t)e * cstep] = cadd(E, cmul(tw[k], O));
     }
 }
 
@@ -230,7 +231,8 @@ cudaError_t launch_time_fft(const pam_plan_s &p, const float *rf, int n_frames, 
 {
     dim3 grid(p.ne, n_frames);
     time_fft_kernel<<<grid, TFFT_THREADS, time_fft_smem(p.nt), st>>>(rf, p.ne, p.nt, ilog2i(p.nt), p.t.tw_t,
-                                                                      p.t.bins, p.n_bins, p.w.S, p.nev, p.w.fmax);
+                                                                      p.t.bins, p.n_bins, p.w.S, p.nev, p.chan_step,
+                                                                      p.w.fmax);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,9 @@ struct Workspace {
     unsigned *smax = nullptr;               // [max_frames] max |Re S|, |Im S| bits
     // host-buffer entry point staging (allocated on first use)
     float *rf_stage = nullptr, *img_stage = nullptr, *rho_stage = nullptr;
+    // PAM_LATERAL_PAD2X: full-width maps before the crop, [max_frames][npix] each
+    // (pad_pairs: [max_frames][pairs][npix]; only pad_img for n_apod == 1)
+    float *pad_img = nullptr, *pad_rho = nullptr, *pad_as = nullptr, *pad_pairs = nullptr;
 };
 
 struct Tables {
@@ -95,8 +98,10 @@ struct pam_plan_s {
     pam_plan_desc d{};
     int device = 0, num_sms = 0;
     int ne = 0, nt = 0, log2nt = 0, nx = 0, nz = 0, n_bins = 0, n_apod = 0, max_frames = 1;
-    int nev = 0;                       // channels of S and of the lateral DFT: ne, or 2 ne zero-stuffed
-    double pitch_x = 0.0;              // their spacing: pitch, or pitch / 2
+    int nev = 0;                       // channels of S and of the lateral DFT: ne, or 2 ne (stuffed or padded)
+    int chan_step = 1;                 // element e sits on channel chan_step * e of S (2 when zero-stuffed)
+    int nx_out = 0;                    // image columns: nx, or ne when the lateral DFTs run padded to 2 ne
+    double pitch_x = 0.0;              // channel spacing: pitch, or pitch / 2
     std::vector<int> bins;
     std::vector<float> apod;
     pam::Tables t;
@@ -150,6 +155,14 @@ cudaError_t launch_normalize_batch(int n_frames, int max_npix, const BatchFrame 
 bool prop_uses_cluster(int n_split);
 // A kernel whose bounded mbarrier wait never completes (failure-path test).
 cudaError_t launch_expire_wait(int *status, cudaStream_t st);
+
+// PAM_LATERAL_PAD2X crop: columns [0, nx_out) of the full-width maps (row
+// width nx) of n_frames frames. rho_n is renormalised to its maximum over the
+// crop and the image rebuilt as rho_n^2 E from the full-aperture energy E.
+// Outputs other than image may be NULL.
+cudaError_t launch_pad_crop(const float *rho_full, const float *e_full, const float *pairs_full, int n_pairs,
+                            int n_frames, int nz, int nx, int nx_out, float *image, float *rho_n, float *pairs,
+                            float *image_as, cudaStream_t st);
 
 // Host-side fault injection for tests: true when the environment variable
 // PAM_FAULT names `what` ("alloc": plan allocation fails part way).

@@ -1,6 +1,7 @@
-// pam_metrics.cu -- the AS^3 image (Eq. 20) and the image-quality measures
-// of the paper (Eq. 12-13): energy spread area A_0.5, image signal-to-noise
-// ratio and the thresholded centroid.
+// pam_metrics.cu -- image-level kernels: the AS^3 image (Eq. 20), the
+// image-quality measures of the paper (Eq. 12-13: energy spread area A_0.5,
+// image signal-to-noise ratio and the thresholded centroid), and the crop of
+// the maps computed with 2x lateral padding (Sec. II-D).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -109,6 +110,32 @@ __global__ void __launch_bounds__(MT) as3_kernel(float *__restrict__ img, size_t
     }
 }
 
+// Crop of maps computed over 2 ne padded columns to the ne element columns
+// (row width nx -> nxo), one block per frame. Pass 1: the maximum of rho
+// over the crop. Pass 2: rho_n = rho / max and I = rho_n^2 E (Eq. 11), plus
+// the optional copies of E and of the pair NCCs.
+__global__ void __launch_bounds__(MT)
+pad_crop_kernel(const float *__restrict__ rho_full, const float *__restrict__ e_full,
+                const float *__restrict__ pairs_full, int n_pairs, int nz, int nx, int nxo, float *__restrict__ image,
+                float *__restrict__ rho_n, float *__restrict__ pairs, float *__restrict__ image_as)
+{
+    __shared__ float shf[MT / 32];
+    const size_t npix = (size_t)nz * nx, npo = (size_t)nz * nxo, f = blockIdx.x;
+    const float *R = rho_full + f * npix, *E = e_full + f * npix;
+    float m = 0.0f;
+    for (size_t o = threadIdx.x; o < npo; o += MT) m = fmaxf(m, R[(o / nxo) * nx + o % nxo]);
+    m = block_max(m, shf);
+    for (size_t o = threadIdx.x; o < npo; o += MT) {
+        const size_t x = (o / nxo) * nx + o % nxo;
+        const float r = m > 0.0f ? R[x] / m : 0.0f, e = E[x];
+        image[f * npo + o] = r * r * e;
+        if (rho_n) rho_n[f * npo + o] = r;
+        if (image_as) image_as[f * npo + o] = e;
+        if (pairs)
+            for (int k = 0; k < n_pairs; ++k) pairs[(f * n_pairs + k) * npo + o] = pairs_full[(f * n_pairs + k) * npix + x];
+    }
+}
+
 pam_status mfail(pam_status s, const std::string &m) { return set_error(s, m.c_str()); }
 
 pam_status dev_ok(const void *p, const char *name)
@@ -127,6 +154,17 @@ pam_status dev_ok(const void *p, const char *name)
 }
 
 }  // namespace
+
+cudaError_t launch_pad_crop(const float *rho_full, const float *e_full, const float *pairs_full, int n_pairs,
+                            int n_frames, int nz, int nx, int nx_out, float *image, float *rho_n, float *pairs,
+                            float *image_as, cudaStream_t st)
+{
+    if (n_frames == 0) return cudaSuccess;
+    pad_crop_kernel<<<n_frames, MT, 0, st>>>(rho_full, e_full, pairs ? pairs_full : nullptr, n_pairs, nz, nx, nx_out,
+                                             image, rho_n, pairs, image_as);
+    return cudaGetLastError();
+}
+
 }  // namespace pam
 
 extern "C" {
@@ -155,7 +193,7 @@ pam_status pam_as3(pam_plan_t p, const float *rf, int n_frames, float *image, vo
     if (!p) return pam::mfail(PAM_ERR_INVALID_ARG, "plan is NULL");
     pam_status s = pam_as_backprop(p, rf, n_frames, -1, image, nullptr, stream);
     if (s != PAM_OK || n_frames == 0) return s;
-    pam::as3_kernel<<<n_frames, pam::MT, 0, static_cast<cudaStream_t>(stream)>>>(image, (size_t)p->nz * p->nx);
+    pam::as3_kernel<<<n_frames, pam::MT, 0, static_cast<cudaStream_t>(stream)>>>(image, (size_t)p->nz * p->nx_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return pam::mfail(PAM_ERR_CUDA, std::string("AS3 launch: ") + cudaGetErrorString(e));
     p->kernels += 1;

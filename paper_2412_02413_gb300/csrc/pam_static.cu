@@ -179,6 +179,7 @@ extern "C" pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf,
     p.pitch_x = d->pitch_m;
     p.nt = nt;
     p.nx = nx;
+    p.nx_out = nx;
     p.nz = nz;
     p.n_bins = nb;
     p.n_apod = 3;

@@ -20,6 +20,7 @@ from . import build as _build
 PAM_OK = 0
 PAM_EVANESCENT_ZERO = 0x1
 PAM_LATERAL_UPSAMPLE2X = 0x2
+PAM_LATERAL_PAD2X = 0x4
 # tensor-core forms of the propagation (include/pam.h PAM_FORM_GEMM_*)
 FORMS = {"fp32": 0x0, "bf16": 0x10, "fp16": 0x20, "bf16split": 0x40, "fp16split": 0x80}
 _STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_UNSUPPORTED", 3: "PAM_ERR_OOM",
@@ -157,7 +158,8 @@ def _dptr(t) -> Optional[int]:
 
 
 def _make_desc(n_elem, pitch, fs, c, n_samples, nz, z0, dz, bins=None, f_lo=0.0, f_hi=0.0, n_apod=3, apod=None,
-               pattern_m=16, eps=1e-3, evanescent_zero=False, max_frames=1, nx=0, form="fp32", upsample2x=False):
+               pattern_m=16, eps=1e-3, evanescent_zero=False, max_frames=1, nx=0, form="fp32", upsample2x=False,
+               pad2x=False):
     """A filled ``pam_plan_desc`` and the host arrays it points to (keep them alive)."""
     L = load()
     d = PlanDesc()
@@ -178,7 +180,7 @@ def _make_desc(n_elem, pitch, fs, c, n_samples, nz, z0, dz, bins=None, f_lo=0.0,
     if form not in FORMS:
         raise ValueError(f"form must be one of {sorted(FORMS)}")
     d.flags = (PAM_EVANESCENT_ZERO if evanescent_zero else 0) | FORMS[form] | \
-        (PAM_LATERAL_UPSAMPLE2X if upsample2x else 0)
+        (PAM_LATERAL_UPSAMPLE2X if upsample2x else 0) | (PAM_LATERAL_PAD2X if pad2x else 0)
     d.max_frames = int(max_frames)
     return d, bins_keep, apod_keep
 
@@ -188,18 +190,21 @@ class Plan:
 
     Geometry is given in SI units. Either ``bins`` (explicit DFT bin indices)
     or the band ``(f_lo, f_hi)`` selects Omega. ``apod`` is [n_apod][n_elem]
-    or None for Pattern-``pattern_m``."""
+    or None for Pattern-``pattern_m``. ``upsample2x`` and ``pad2x`` are the two
+    2x lateral extensions of Sec. II-D: zero-stuffed channels at pitch/2 (the
+    image is 2 n_elem wide), or n_elem zero channels appended (transforms over
+    2 n_elem points, the image cropped to the n_elem element columns)."""
 
     def __init__(self, n_elem: int, pitch: float, fs: float, c: float, n_samples: int, nz: int,
                  z0: float, dz: float, bins: Optional[Sequence[int]] = None, f_lo: float = 0.0,
                  f_hi: float = 0.0, n_apod: int = 3, apod=None, pattern_m: int = 16, eps: float = 1e-3,
                  evanescent_zero: bool = False, max_frames: int = 1, nx: int = 0, form: str = "fp32",
-                 upsample2x: bool = False):
+                 upsample2x: bool = False, pad2x: bool = False):
         _require_cuda()
         L = load()
         d, self._bins_keep, self._apod_keep = _make_desc(
             n_elem, pitch, fs, c, n_samples, nz, z0, dz, bins, f_lo, f_hi, n_apod, apod, pattern_m, eps,
-            evanescent_zero, max_frames, nx, form, upsample2x)
+            evanescent_zero, max_frames, nx, form, upsample2x, pad2x)
         h = _VP()
         _check(L.pam_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h

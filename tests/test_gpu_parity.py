@@ -232,6 +232,66 @@ def test_lateral_upsample2x_parity(ne, nt, nz):
     plan.close()
 
 
+@pytest.mark.parametrize("ne,nt,nz", [(16, 256, 21), (64, 1024, 40)])
+def test_lateral_pad2x_parity(ne, nt, nz):
+    """2x lateral padding (Sec. II-D): transforms over 2 n_elem points, maps
+    cropped to the element columns, rho_n normalised over the crop."""
+    w = _tiny(ne, nt, nz, pattern_m=4 if ne == 16 else 8)
+    w.source_z = (w.z0, w.z0 + (nz - 1) * w.dz)
+    rf = synth.make_frame(w, 4)[0] if ne == 64 else synth.random_rf(ne, nt, seed=33)
+    plan = _plan(w, pad2x=True)
+    assert plan.nx == ne
+    out = _run_tax(plan, rf)
+    assert tuple(out["image"].shape) == (1, nz, ne)
+    apod = oracle.pattern(ne, 3, w.pattern_m)
+    orc = oracle.as_xcorr_pad2x(_geom(w), rf, apod)
+    compare_xcorr(out, orc, check_peak=(ne == 64))
+    assert float(out["rho_n"].max()) == 1.0
+    rft = torch.from_numpy(np.ascontiguousarray(rf)).cuda()
+    e = plan.as_backprop(rft)
+    assert rel_l2(e[0].cpu().numpy(), oracle.as_backprop_pad2x(_geom(w), rf)) <= REL_L2_TOL
+    # the padding matters: the unpadded maps differ well above the tolerance
+    plain = _plan(w)
+    assert rel_l2(plain.as_backprop(rft)[0].cpu().numpy(), oracle.as_backprop_pad2x(_geom(w), rf)) > 1e-3
+    plain.close()
+    plan.close()
+
+
+def test_lateral_pad2x_dax_host_and_frames():
+    """AS-DAX, several frames per call (max_frames 2, so two chunks) and the
+    host-buffer entry point, all with 2x lateral padding."""
+    w = _tiny(32, 256, 9, pattern_m=4)
+    rfs = np.stack([synth.random_rf(32, 256, seed=40 + f) for f in range(3)])
+    A = oracle.pattern(32, 2, 4)
+    plan = _plan(w, n_apod=2, pad2x=True, max_frames=2)
+    out = plan.as_dax(torch.from_numpy(rfs).cuda(), rho_n=True, rho_pairs=True, image_as=True)
+    img_h = np.zeros((3, w.nz, 32), np.float32)
+    rho_h = np.zeros_like(img_h)
+    plan.as_xcorr_host(rfs, img_h, rho_h)
+    for f in range(3):
+        orc = oracle.as_xcorr_pad2x(_geom(w), rfs[f], A)
+        compare_xcorr(out, orc, f=f, check_peak=False)
+        assert rel_l2(img_h[f], orc["image"]) <= REL_L2_TOL
+        assert np.max(np.abs(rho_h[f] - orc["rho_n"])) <= NCC_TOL
+    plan.close()
+
+
+def test_lateral_pad2x_rejections():
+    pam = _pam()
+    with pytest.raises(pam.PamError):          # 2 n_elem = 256 is not built
+        _plan(_tiny(128, 256, 8), pad2x=True)
+    with pytest.raises(pam.PamError):          # tensor-core forms run without it
+        _plan(_tiny(64, 256, 8), pad2x=True, form="bf16")
+    with pytest.raises(pam.PamError):          # not together with zero-stuffing
+        _plan(_tiny(16, 256, 8), pad2x=True, upsample2x=True)
+    with pytest.raises(pam.PamError):          # the image is n_elem wide
+        _plan(_tiny(16, 256, 8), pad2x=True, nx=32)
+    plan = _plan(_tiny(16, 256, 8), pad2x=True)
+    with pytest.raises(pam.PamError):          # no fields output
+        plan.as_backprop(torch.zeros((1, 16, 256), device="cuda"), fields=True)
+    plan.close()
+
+
 def test_lateral_upsample2x_rejections():
     pam = _pam()
     w = _tiny(16, 256, 8)
