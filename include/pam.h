@@ -42,9 +42,11 @@
  *     thread's last failure.
  *   - The public calls are NVTX ranges named after the call (visible under
  *     nsys / ncu; free when no tool is attached).
- *   - Fault injection for tests (host side): with the environment variable
- *     PAM_FAULT=alloc, pam_plan_create fails with PAM_ERR_OOM part way through
- *     its allocations (and frees what it allocated).
+ *   - Fault injection for tests (host side), by the environment variable
+ *     PAM_FAULT: "alloc" makes pam_plan_create fail with PAM_ERR_OOM part way
+ *     through its allocations (it frees what it allocated); "launch" makes
+ *     pam_as_backprop, pam_as_dax, pam_as_tax and the host-buffer entry points
+ *     return PAM_ERR_CUDA before they queue any work.
  */
 #ifndef PAM_H
 #define PAM_H

@@ -350,6 +350,8 @@ pam_status run_xcorr(pam_plan_t p, const float *rf, int n_frames, float *image, 
     const size_t fr_in = (size_t)p->ne * p->nt;
     const int npairs = p->n_apod == 3 ? 3 : 1;
     const bool crop = p->nx_out != p->nx;             // PAM_LATERAL_PAD2X
+    if (pam::fault_injected("launch"))
+        return fail(PAM_ERR_CUDA, "injected launch failure (PAM_FAULT=launch): nothing was queued");
     for (int f0 = 0; f0 < n_frames; f0 += p->max_frames) {
         int Fc = std::min(p->max_frames, n_frames - f0);
         float *c_img = image + (size_t)f0 * npix, *c_rho = rho_n ? rho_n + (size_t)f0 * npix : nullptr;
@@ -480,6 +482,8 @@ pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod
     if ((s = check_dev_ptr(fields, "fields", false)) != PAM_OK) return s;
     const bool crop = p->nx_out != p->nx;   // PAM_LATERAL_PAD2X
     if (fields && crop) return fail(PAM_ERR_UNSUPPORTED, "the fields output is not built with PAM_LATERAL_PAD2X");
+    if (pam::fault_injected("launch"))
+        return fail(PAM_ERR_CUDA, "injected launch failure (PAM_FAULT=launch): nothing was queued");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const float *apod = apod_index < 0 ? p->t.ones : p->t.apod + (size_t)apod_index * p->nev;
     const size_t npix = (size_t)p->nz * p->nx_out;

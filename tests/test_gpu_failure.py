@@ -5,6 +5,8 @@
   and pam_sync returns PAM_ERR_TIMEOUT; the next call on the same plan works.
 * Host-side fault injection (PAM_FAULT=alloc): plan creation fails part way
   with PAM_ERR_OOM and leaves no device memory behind.
+* PAM_FAULT=launch: a compute call fails with PAM_ERR_CUDA before queueing
+  anything, and the same plan then gives the same result bit for bit.
 No test here traps, faults or hangs the GPU.
 """
 import time
@@ -67,4 +69,27 @@ def test_injected_allocation_failure_leaves_nothing(monkeypatch):
     assert abs(free1 - free0) <= 2 * 1024 * 1024, (free0, free1)
     monkeypatch.delenv("PAM_FAULT")
     plan = pam.Plan.from_workload(w, max_frames=64)   # creation works again
+    plan.close()
+
+
+def test_injected_launch_failure_leaves_the_plan_usable(monkeypatch):
+    from paper_2412_02413_gb300 import pam
+    w = _small()
+    plan = pam.Plan.from_workload(w)
+    rft = torch.from_numpy(synth.make_frame(w, 71)[0]).cuda()
+    ref = plan.as_tax(rft, rho_n=True)
+    ref_e = plan.as_backprop(rft)
+    plan.sync()
+    monkeypatch.setenv("PAM_FAULT", "launch")
+    for call in (lambda: plan.as_tax(rft), lambda: plan.as_backprop(rft)):
+        with pytest.raises(pam.PamError) as exc:
+            call()
+        assert exc.value.status == 4              # PAM_ERR_CUDA
+        assert "injected" in str(exc.value)
+    monkeypatch.delenv("PAM_FAULT")
+    out = plan.as_tax(rft, rho_n=True)
+    e = plan.as_backprop(rft)
+    plan.sync()
+    assert torch.equal(out["image"], ref["image"]) and torch.equal(out["rho_n"], ref["rho_n"])
+    assert torch.equal(e, ref_e)
     plan.close()
