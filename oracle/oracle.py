@@ -238,8 +238,13 @@ def as_tax(geom: Geometry, rf: np.ndarray, apod: np.ndarray, eps: float = 1e-3, 
 # the lateral transforms of Eq. 1-2 run over 2 n_elem points, and the image is
 # cropped back to the n_elem element columns. The TAX weight is normalised to
 # its maximum over the cropped image (Eq. 11), and I = rho_n^2 E_full there.
+_py_mutation = 0   # deliberate mistakes 11-12 of the mutation tests live in this file
+
+
 def _padded(geom: Geometry, rf: np.ndarray, apod):
     ne = geom.n_elem
+    if _py_mutation == 12:   # planted mistake: no padding at all
+        return geom, np.asarray(rf, dtype=np.float32), None if apod is None else np.asarray(apod, np.float64)
     g2 = Geometry(2 * ne, geom.nt, geom.fs, geom.c, geom.pitch, geom.nz, geom.z0, geom.dz, geom.bins,
                   geom.evanescent_zero)
     rf = np.asarray(rf, dtype=np.float32)
@@ -253,10 +258,15 @@ def _padded(geom: Geometry, rf: np.ndarray, apod):
     return g2, rf2, a2
 
 
+def _crop(geom: Geometry) -> slice:
+    ne = geom.n_elem
+    return slice(ne, 2 * ne) if _py_mutation == 11 else slice(0, ne)   # 11: the padding columns
+
+
 def as_backprop_pad2x(geom: Geometry, rf: np.ndarray, apod=None, threads=None) -> np.ndarray:
     """[nz][n_elem] AS energy (Eq. 3) with 2x lateral padding."""
     g2, rf2, a2 = _padded(geom, rf, apod)
-    return np.ascontiguousarray(as_backprop(g2, rf2, a2, threads)[:, :geom.n_elem])
+    return np.ascontiguousarray(as_backprop(g2, rf2, a2, threads)[:, _crop(geom)])
 
 
 def as_xcorr_pad2x(geom: Geometry, rf: np.ndarray, apod: np.ndarray, eps: float = 1e-3, threads=None):
@@ -265,7 +275,7 @@ def as_xcorr_pad2x(geom: Geometry, rf: np.ndarray, apod: np.ndarray, eps: float 
     rho_n renormalised over the crop and the image rebuilt from it."""
     g2, rf2, a2 = _padded(geom, rf, apod)
     full = as_xcorr(g2, rf2, a2, eps, threads)
-    out = {k: np.ascontiguousarray(v[..., :geom.n_elem]) for k, v in full.items()}
+    out = {k: np.ascontiguousarray(v[..., _crop(geom)]) for k, v in full.items()}
     rho_n = out["rho_n"] / out["rho_n"].max()
     out["rho_n"] = rho_n
     out["image"] = rho_n * rho_n * out["image_as"]
@@ -273,5 +283,8 @@ def as_xcorr_pad2x(geom: Geometry, rf: np.ndarray, apod: np.ndarray, eps: float 
 
 
 def set_mutation(mid: int) -> None:
-    """Test hook: switch on deliberate mistake ``mid`` (0 restores the oracle)."""
+    """Test hook: switch on deliberate mistake ``mid`` (0 restores the oracle).
+    Mistakes 1-10 are in pam_oracle.c, 11-12 in the padding reading above."""
+    global _py_mutation
+    _py_mutation = int(mid)
     lib().pam_oracle_set_mutation(int(mid))

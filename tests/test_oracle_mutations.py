@@ -6,13 +6,15 @@ The mutations are switched inside pam_oracle.c:
  3 kx without the FFT-order wrap (Eq. 2)     8 eps clamp after the cube root (Sec. II-A)
  4 NCC denominator without sqrt (Eq. 4)      9 Pattern-m shifted by one element
  5 incoherent energy sum (Eq. 11)            10 rho normalised by its mean, not its max
+and, in the 2x lateral padding reading (oracle.py):
+11 the crop keeps the padding columns        12 no padding: n_elem-point transforms
 """
 import pytest
 
 import oracle
 import oracle_pins
 
-MUTATIONS = list(range(1, 11))
+MUTATIONS = list(range(1, 13))
 
 
 def _failing_pins():
