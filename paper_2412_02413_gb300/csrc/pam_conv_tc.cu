@@ -56,8 +56,6 @@ struct ConvShape {
     static constexpr unsigned IDESC = ptx::umma_idesc(false, 128, NCO);
 };
 
-
-
 __device__ __forceinline__ unsigned pack2(float a, float b)
 {
     unsigned r;

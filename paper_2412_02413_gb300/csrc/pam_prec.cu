@@ -53,11 +53,6 @@ __device__ __forceinline__ float from16(unsigned short u)
     else return __bfloat162float(__ushort_as_bfloat16(u));
 }
 
-
-
-
-
-
 // ------------------------------------------------------- plan tables ----
 // c_j[d] for one (row j, bin b) per CTA, d = threadIdx.x. Phasors come from
 // the exact fixed-point phase words with accurate sincospif (the table is
@@ -201,11 +196,6 @@ template <int NAP>
 constexpr int gemm_threads() { return 384; }   // 8 build/fold warps, 1 copy warp, NAP MMA warps (+ idle)
 constexpr int REG_LAUNCH = 168, REG_CTRL = 96, REG_FOLD = 200;
 static_assert(2 * 128 * REG_FOLD + 128 * REG_CTRL <= 384 * REG_LAUNCH, "register split exceeds the launch budget");
-
-
-
-
-
 
 // Shared memory of one pipeline stage: NPART x (A blocks, B tile, c words).
 __host__ __device__ constexpr size_t gemm_stage_bytes(int K, int npart)
