@@ -590,6 +590,7 @@ def run_ours(args):
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tf = fp32_peak_tflops(sm_max)
+    fma_tf = pam.fp32_fma_rate() if rank == 0 else None   # after the timed region
     flops = fused_flops_per_frame(plan.n_bins, w.nz, w.nx, 3) * F
     avg_launch_s = prop_ms / max(prop_launches, 1) / 1000.0
     achieved_tf = flops / avg_launch_s / 1e12
@@ -623,7 +624,11 @@ def run_ours(args):
                          "alone": {"avg_launch_us": 1000.0 * iso_ms / max(iso_n, 1),
                                    "achieved": flops / (iso_ms / max(iso_n, 1) / 1000.0) / 1e12,
                                    "frac": flops / (iso_ms / max(iso_n, 1) / 1000.0) / 1e12 / peak_tf,
-                                   "note": f"{iso_n} launches on one stream after the timed region"}},
+                                   "note": f"{iso_n} launches on one stream after the timed region"},
+                         "peak_fp32_measured": {"value": fma_tf, "unit": "TFLOP/s",
+                                                "frac_of_peak": fma_tf / peak_tf if fma_tf else None,
+                                                "how": "pam_fp32_fma_rate: independent FMA chains on every SM, "
+                                                       "after the timed region"}},
             "clocks": ck,
             "forms": forms,
             "batch": batch,

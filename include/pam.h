@@ -355,6 +355,16 @@ typedef struct {
 pam_status pam_image_metrics(const float *maps, int n_frames, int nz, int nx, double x0_m, double dx_m, double z0_m,
                              double dz_m, float alpha, pam_image_metrics_t *out, void *stream);
 
+/* The FP32 FMA rate of the current device, measured: a kernel of independent
+ * FMA chains (8 per thread, `iters` dependent steps each) on every SM at full
+ * occupancy, one warm-up launch and one launch timed with CUDA events, both on
+ * the default stream. *tflops = 2 x FMAs / time in TFLOP/s. Synchronous. The
+ * fused kernel's roofline divides by the FP32 peak from unit counts (SMs x 128
+ * lanes x 2 flops x clock); this measures what the CUDA cores sustain.
+ * Errors: PAM_ERR_INVALID_ARG (iters outside [1, 2^24] or tflops NULL),
+ * PAM_ERR_CUDA. */
+pam_status pam_fp32_fma_rate(int iters, double *tflops);
+
 /* ------------------------------------------------------------------------
  * Learned form (AS-TAX with a predicted NCC weight). A 5-layer convolutional
  * network predicts rho_TAX (Eq. 10, before the max normalisation) from the

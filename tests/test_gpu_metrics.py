@@ -68,3 +68,12 @@ def test_measures_match_oracle(alpha):
         assert got[f]["isnr_db"] > got[3 + f]["isnr_db"]
         assert got[f]["esa_m2"] <= got[3 + f]["esa_m2"]
     plan.close()
+
+
+def test_fp32_fma_rate_is_plausible():
+    """The FMA probe's rate lies between a quarter of the unit-count peak at
+    1 GHz and that peak at 2.2 GHz (128 FP32 lanes per SM, 2 flops per FMA)."""
+    from paper_2412_02413_gb300 import pam
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rate = pam.fp32_fma_rate(1024)
+    assert 0.25 * sms * 128 * 2 * 1.0e9 / 1e12 < rate < sms * 128 * 2 * 2.2e9 / 1e12, rate
