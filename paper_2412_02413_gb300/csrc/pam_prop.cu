@@ -333,7 +333,11 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
 #pragma unroll
             for (int n1 = 0; n1 < 8; ++n1) {
                 const int u0 = L2 * n1 + n2;
-                x[n1] = cadd(cmul(cQ[q * NX + u0], ph0[n1]), cmul(cQ[q * NX + u0 + H], ph1[n1]));
+                // Q0 ph0 + Q1 ph1 as two chains of one multiply and three FMAs: 8 FMA-pipe
+                // instructions where two complex products and a packed add take 9
+                const float2 a = cQ[q * NX + u0], c = cQ[q * NX + u0 + H], p = ph0[n1], r = ph1[n1];
+                x[n1] = make_float2(fmaf(a.x, p.x, fmaf(-a.y, p.y, fmaf(c.x, r.x, -c.y * r.y))),
+                                    fmaf(a.x, p.y, fmaf(a.y, p.x, fmaf(c.x, r.y, c.y * r.x))));
             }
             IDft<8>::run(x);
             float2 *reg = myT + ((q * RPW + r) * 2 + g) * RS;
