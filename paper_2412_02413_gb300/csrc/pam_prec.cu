@@ -512,6 +512,19 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                      : "memory");
 }
 
+// The element block of every K step of 16 (4 bits per step, steps 0-15 in x and
+// 16-31 in y): the MMA of a step starts its A descriptor at block 16 - m.
+ulonglong2 gemm_steps(const pam_plan_s &p)
+{
+    ulonglong2 steps = make_ulonglong2(0ull, 0ull);
+    for (int s = 0; s < p.K / 16; ++s) {
+        const unsigned long long m = (unsigned long long)((p.ktab_h[(size_t)16 * s] & 0x3FFF) >> 3) & 15ull;
+        if (s < 16) steps.x |= m << (4 * s);
+        else steps.y |= m << (4 * (s - 16));
+    }
+    return steps;
+}
+
 template <int NAP, bool FP16, bool SPLIT>
 cudaError_t launch_gemm_t(const pam_plan_s &p, int n_frames, cudaStream_t st)
 {
@@ -519,12 +532,7 @@ cudaError_t launch_gemm_t(const pam_plan_s &p, int n_frames, cudaStream_t st)
     dim3 grid(p.nz, groups);
     const int4 kq = make_int4(p.kq[0], p.kq[1], p.kq[2], p.kq[3]);
     if (gemm_stages(p.K, SPLIT) < 2 || p.K / 16 > 32) return cudaErrorInvalidConfiguration;
-    ulonglong2 steps = make_ulonglong2(0ull, 0ull);
-    for (int s = 0; s < p.K / 16; ++s) {
-        const unsigned long long m = (unsigned long long)((p.ktab_h[(size_t)16 * s] & 0x3FFF) >> 3) & 15ull;
-        if (s < 16) steps.x |= m << (4 * s);
-        else steps.y |= m << (4 * (s - 16));
-    }
+    const ulonglong2 steps = gemm_steps(p);
     prec_gemm_kernel<NAP, FP16, SPLIT><<<grid, gemm_threads<NAP>(), gemm_smem(p.K, SPLIT), st>>>(
         p.t.c_hi, p.t.c_lo, reinterpret_cast<const uint8_t *>(p.w.Bhi), reinterpret_cast<const uint8_t *>(p.w.Blo),
         steps, kq, p.n_bins, p.nz, n_frames, gemm_stages(p.K, SPLIT), p.w.smax, p.w.part, p.w.status, 0);
@@ -548,12 +556,7 @@ cudaError_t launch_bands_form(const pam_plan_s &p, const float2 *S, int n_frames
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (gemm_stages(p.K, false) < 2 || p.K / 16 > 32) return cudaErrorInvalidConfiguration;
     const int4 kq = make_int4(p.kq[0], p.kq[1], p.kq[2], p.kq[3]);
-    ulonglong2 steps = make_ulonglong2(0ull, 0ull);
-    for (int s = 0; s < p.K / 16; ++s) {
-        const unsigned long long m = (unsigned long long)((p.ktab_h[(size_t)16 * s] & 0x3FFF) >> 3) & 15ull;
-        if (s < 16) steps.x |= m << (4 * s);
-        else steps.y |= m << (4 * (s - 16));
-    }
+    const ulonglong2 steps = gemm_steps(p);
     prec_gemm_kernel<3, FP16, false, true><<<dim3(p.nz, groups), gemm_threads<3>(), gemm_smem(p.K, false), st>>>(
         p.t.c_hi, nullptr, reinterpret_cast<const uint8_t *>(p.w.Bhi), nullptr, steps, kq, p.n_bins, p.nz, n_frames,
         gemm_stages(p.K, false), p.w.smax, bands, p.w.status, n_bands);
