@@ -151,7 +151,9 @@ void pam_oracle_propagate(const double *Q, const double *kz, int nx, double dz,
     for (int u = 0; u < nx; ++u) {
         double kr = kz[2 * u], ki = kz[2 * u + 1];
         double amp, ph;
-        if (ki > 0.0 && evanescent_zero) { amp = 0.0; ph = 0.0; }
+        int drop = evanescent_zero && (MUT(13) ? ki == 0.0 : ki > 0.0);
+        if (MUT(14)) drop = 0;
+        if (drop) { amp = 0.0; ph = 0.0; }
         else { amp = exp(-ki * dz); ph = sgn * kr * dz; }
         double c = amp * cos(ph), s = amp * sin(ph);
         double qr = Q[2 * u], qi = Q[2 * u + 1];

@@ -137,6 +137,50 @@ def pin_plane_wave_exact_phase():
         assert err < 5e-5, (u0, k0, err)   # float32 rf limits the agreement
 
 
+def pin_evanescent_zero_plane_waves():
+    """The evanescent-zero reading of Eq. 2: a plane wave whose lateral
+    wavenumber exceeds w/c (kz imaginary) is removed at every depth, while a
+    propagating one keeps the exact phase shift kz0*z of the closed form."""
+    ne, nt, fs, pitch = 16, 128, 20e6, 0.3e-3
+    z = 1e-3 + np.arange(5) * 0.9e-3
+    # (4, 8): f0 = 1.25 MHz, |kx0| = 5236 rad/m > w/c = 5100 rad/m -> evanescent
+    # (kappa = 1190 rad/m, so the principal branch still leaves 0.4% at 4.6 mm)
+    rf, kx0, kz0, xe = _plane_wave_case(4, 8, ne, nt, fs, pitch)
+    assert kz0.imag > 0 and kz0.real == 0
+    g = oracle.Geometry(ne, nt, fs, C, pitch, 5, 1e-3, 0.9e-3, [8], evanescent_zero=True)
+    F = oracle.fields(g, rf.astype(np.float32), None)[0]
+    # float32 rf leaks about 1e-7 of the amplitude into the other lateral bins;
+    # those are evanescent too at 1.25 MHz except u = 0, +-1 (|kx| <= 2094 rad/m)
+    lead = np.max(np.abs(F))
+    assert lead < 1e-5 * nt / 2, lead
+    g0 = oracle.Geometry(ne, nt, fs, C, pitch, 5, 1e-3, 0.9e-3, [8], evanescent_zero=False)
+    F0 = oracle.fields(g0, rf.astype(np.float32), None)[0]
+    decay = nt / 2 * np.exp(-kz0.imag * z)
+    assert np.allclose(np.max(np.abs(F0), axis=1), decay, rtol=1e-3), "principal branch keeps the decay"
+    # (3, 20): f0 = 3.125 MHz, |kx0| = 3927 rad/m < w/c = 12750 rad/m -> propagating
+    rf, kx0, kz0, xe = _plane_wave_case(3, 20, ne, nt, fs, pitch)
+    assert kz0.imag == 0
+    g = oracle.Geometry(ne, nt, fs, C, pitch, 5, 1e-3, 0.9e-3, [20], evanescent_zero=True)
+    F = oracle.fields(g, rf.astype(np.float32), None)[0]
+    want = nt / 2 * np.exp(1j * (kx0 * xe[None, :] + kz0.real * z[:, None]))
+    assert np.max(np.abs(F - want)) / (nt / 2) < 5e-5
+
+
+def pin_evanescent_zero_propagator():
+    """Eq. 2 with evanescent components dropped, on a random spectrum at a bin
+    that holds both kinds: the propagating entries equal Q exp(i kz z) and the
+    evanescent entries are exactly zero."""
+    rng = np.random.default_rng(31)
+    nx, z = 32, 3.3e-3
+    _, kzv = oracle.kz(1.6e6, C, 0.3e-3, nx)
+    ev = kzv.imag > 0
+    assert ev.any() and (~ev).any()
+    Q = rng.standard_normal(nx) + 1j * rng.standard_normal(nx)
+    P = oracle.propagate(Q, kzv, z, evanescent_zero=True)
+    assert np.all(P[ev] == 0)
+    assert np.max(np.abs(P[~ev] - Q[~ev] * np.exp(1j * kzv[~ev].real * z))) < 1e-12 * np.max(np.abs(Q))
+
+
 def pin_composition_law():
     """Eq. 2 composes: propagating by z1 then z2 equals propagating by z1+z2,
     for propagating and evanescent components alike."""
@@ -341,11 +385,12 @@ def pin_green_sources_near_truth():
 
 
 # ---------------------------------------------------------- brute force --
-def numpy_as_xcorr(rf, fs, pitch, nz, z0, dz, bins, A, eps=EPS, pad=1):
+def numpy_as_xcorr(rf, fs, pitch, nz, z0, dz, bins, A, eps=EPS, pad=1, evz=False):
     """Independent tiny-case implementation with numpy's FFT routines. With
     pad = 2 the lateral transforms use numpy's zero padding to 2 n_elem points
     (``fft(..., n=2 ne)``) and the fields are cropped to the n_elem element
-    columns before the sums."""
+    columns before the sums. With evz the propagator of every component whose
+    kz is imaginary is zero."""
     ne, nt = rf.shape
     nf = pad * ne
     S = np.fft.rfft(rf.astype(np.float64), axis=1)[:, bins].T         # [nb][ne]
@@ -354,6 +399,8 @@ def numpy_as_xcorr(rf, fs, pitch, nz, z0, dz, bins, A, eps=EPS, pad=1):
     kz = np.sqrt((k[:, None] ** 2 - kx[None, :] ** 2).astype(complex))  # principal branch
     z = z0 + np.arange(nz) * dz
     ph = np.exp(1j * kz[:, None, :] * z[None, :, None])                # [nb][nz][nf]
+    if evz:
+        ph = np.where(np.imag(kz)[:, None, :] > 0, 0.0, ph)
     p = [np.fft.ifft(np.fft.fft(a[None, :] * S, n=nf, axis=1)[:, None, :] * ph, axis=2)[..., :ne] for a in A]
     Aq = [np.sum(np.abs(x) ** 2, axis=0) for x in p]
     pairs = [(0, 1), (1, 2), (2, 0)] if len(A) == 3 else [(0, 1)]
@@ -383,6 +430,28 @@ def pin_numpy_brute_force():
         for key in ("image", "rho_n", "rho_pairs", "image_as"):
             err = np.max(np.abs(got[key] - want[key])) / np.max(np.abs(want[key]))
             assert err < 1e-10, (na, key, err)
+
+
+def pin_numpy_brute_force_evanescent_zero():
+    """AS-TAX and plain AS with evanescent components dropped, against the
+    numpy implementation with the imaginary-kz propagators set to zero. The
+    band starts at 0.5 MHz, where most lateral components are evanescent, so
+    the result differs clearly from the principal-branch reading."""
+    ne, nt, fs, pitch = 16, 128, 20e6, 0.3e-3
+    rf = _rand_rf(ne, nt, 29)
+    bins = oracle.band_bins(nt, fs, 0.5e6, 8e6)
+    nz, z0, dz = 5, 0.2e-3, 0.3e-3
+    g = oracle.Geometry(ne, nt, fs, C, pitch, nz, z0, dz, bins, evanescent_zero=True)
+    A = oracle.pattern(ne, 3, 2)
+    got = oracle.as_xcorr(g, rf, A)
+    want = numpy_as_xcorr(rf, fs, pitch, nz, z0, dz, bins, A, evz=True)
+    for key in ("image", "rho_n", "rho_pairs", "image_as"):
+        err = np.max(np.abs(got[key] - want[key])) / np.max(np.abs(want[key]))
+        assert err < 1e-10, (key, err)
+    keep = numpy_as_xcorr(rf, fs, pitch, nz, z0, dz, bins, A, evz=False)
+    assert np.max(np.abs(keep["image_as"] - want["image_as"])) > 1e-3 * np.max(want["image_as"])
+    e = oracle.as_backprop(g, rf)
+    assert np.max(np.abs(e - want["image_as"])) < 1e-10 * np.max(want["image_as"])
 
 
 def pin_pad2x_numpy_brute_force():

@@ -8,13 +8,15 @@ The mutations are switched inside pam_oracle.c:
  5 incoherent energy sum (Eq. 11)            10 rho normalised by its mean, not its max
 and, in the 2x lateral padding reading (oracle.py):
 11 the crop keeps the padding columns        12 no padding: n_elem-point transforms
+and, in the evanescent-zero reading of Eq. 2 (pam_oracle.c):
+13 the propagating components are dropped   14 the flag is ignored (nothing dropped)
 """
 import pytest
 
 import oracle
 import oracle_pins
 
-MUTATIONS = list(range(1, 13))
+MUTATIONS = list(range(1, 15))
 
 
 def _failing_pins():
