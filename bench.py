@@ -90,6 +90,23 @@ def committed_traffic():
     return d.get("dram_bytes_per_launch")
 
 
+def fp32_fma_rates(iters=2048):
+    """(scalar, packed two-wide) FP32 FMA rates in TFLOP/s from the bench-side
+    probe library, or (None, None) when it is missing."""
+    import ctypes
+    from paper_2412_02413_gb300 import build
+    if not os.path.exists(build.PROBE_LIB):
+        return None, None
+    lib = ctypes.CDLL(build.PROBE_LIB)
+    lib.pam_probe_fp32_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.pam_probe_fp32_fma_rate.restype = ctypes.c_int
+    out = []
+    for packed in (0, 1):
+        v = ctypes.c_double(0.0)
+        out.append(v.value if lib.pam_probe_fp32_fma_rate(iters, packed, ctypes.byref(v)) == 0 else None)
+    return tuple(out)
+
+
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -590,7 +607,7 @@ def run_ours(args):
     peaks, peak_kind = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tf = fp32_peak_tflops(sm_max)
-    fma_tf = pam.fp32_fma_rate() if rank == 0 else None   # after the timed region
+    fma_tf, fma2_tf = (fp32_fma_rates() if rank == 0 else (None, None))   # after the timed region
     flops = fused_flops_per_frame(plan.n_bins, w.nz, w.nx, 3) * F
     avg_launch_s = prop_ms / max(prop_launches, 1) / 1000.0
     achieved_tf = flops / avg_launch_s / 1e12
@@ -627,8 +644,10 @@ def run_ours(args):
                                    "note": f"{iso_n} launches on one stream after the timed region"},
                          "peak_fp32_measured": {"value": fma_tf, "unit": "TFLOP/s",
                                                 "frac_of_peak": fma_tf / peak_tf if fma_tf else None,
-                                                "how": "pam_fp32_fma_rate: independent FMA chains on every SM, "
-                                                       "after the timed region"}},
+                                                "packed_fma2_value": fma2_tf,
+                                                "how": "libpam_probe.so (bench-side probe): independent FMA chains "
+                                                       "on every SM, scalar and packed two-wide, after the timed "
+                                                       "region"}},
             "clocks": ck,
             "forms": forms,
             "batch": batch,

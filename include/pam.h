@@ -225,13 +225,20 @@ pam_status pam_as_xcorr_host_async(pam_plan_t p, const float *rf_host, int n_fra
  * PAM_STATIC_SCRATCH_BYTES. A geometry that needs more (for example a very
  * large nz * nx or n_bins) is rejected with PAM_ERR_INVALID_ARG and a message
  * that gives the size it needs. The first call on a device sets that device
- * up: it looks up the array's device address and sets kernel attributes. Make
- * that first call before any stream capture. Every call shares the one array
- * and leaves its contents behind: calls that overlap on the GPU (concurrent
- * streams or host threads on the same device) race and must be serialised by
- * the caller. The call calls no cudaMalloc, cudaFree or other allocating
- * routine; the bins and apodizations go to the device by cudaMemcpyAsync
- * from the stack. */
+ * up: it looks up the array's device address and sets kernel attributes.
+ * Every call shares the one array and leaves its contents behind: calls that
+ * overlap on the GPU (concurrent streams or host threads on the same device)
+ * race and must be serialised by the caller. The call calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ * Every call uploads the bins and apodizations by cudaMemcpyAsync from
+ * pageable stack memory, so the CUDA runtime may block the calling thread
+ * until `stream`'s earlier work is done. Stream capture does not allow such
+ * copies: on a capturing stream the call returns PAM_ERR_UNSUPPORTED before
+ * queueing anything, and the capture stays valid.
+ * Errors inside the kernels: there is no plan and so no pam_sync. If a
+ * bounded wait in a kernel expired (a stalled staging pipeline; the call's
+ * results would be partial), every element of image_tax and rho_n is NaN when
+ * the stream reaches the end of the call; otherwise none is. */
 pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf, int n_frames, float *image_tax,
                              float *rho_n, void *stream);
 
@@ -355,15 +362,6 @@ typedef struct {
 pam_status pam_image_metrics(const float *maps, int n_frames, int nz, int nx, double x0_m, double dx_m, double z0_m,
                              double dz_m, float alpha, pam_image_metrics_t *out, void *stream);
 
-/* The FP32 FMA rate of the current device, measured: a kernel of independent
- * FMA chains (8 per thread, `iters` dependent steps each) on every SM at full
- * occupancy, one warm-up launch and one launch timed with CUDA events, both on
- * the default stream. *tflops = 2 x FMAs / time in TFLOP/s. Synchronous. The
- * fused kernel's roofline divides by the FP32 peak from unit counts (SMs x 128
- * lanes x 2 flops x clock); this measures what the CUDA cores sustain.
- * Errors: PAM_ERR_INVALID_ARG (iters outside [1, 2^24] or tflops NULL),
- * PAM_ERR_CUDA. */
-pam_status pam_fp32_fma_rate(int iters, double *tflops);
 
 /* ------------------------------------------------------------------------
  * Learned form (AS-TAX with a predicted NCC weight). A 5-layer convolutional
@@ -412,17 +410,24 @@ pam_status pam_learn_create(const pam_plan_desc *d, pam_learn_t *out);
 void pam_learn_destroy(pam_learn_t l);
 
 /* Copies n = pam_learn_n_params() host floats into the network and resets the
- * Adam state. Blocks. PAM_ERR_NUMERIC for a non-finite value. */
+ * Adam state. Blocks until the copy is done. PAM_ERR_NUMERIC for a non-finite
+ * value.
+ * This call and the three below order themselves after the most recent
+ * queued call of this handle (pam_learn_example, _forward, _grads,
+ * _train_step, _tax) on its stream, and wait for that work only: other streams
+ * of the process keep running. Calls of one handle on different streams must
+ * be ordered by the caller, as for every other call of the handle. */
 pam_status pam_learn_set_params(pam_learn_t l, const float *params, size_t n);
 
-/* Copies the current parameters to host memory. Blocks. */
+/* Copies the current parameters to host memory. Blocks until they are there. */
 pam_status pam_learn_get_params(pam_learn_t l, float *params, size_t n);
 
 /* Training state for checkpoint and resume: parameters, Adam first and second
  * moments (3 x pam_learn_n_params() floats, in that order) and the Adam step
  * count. A training run restored with pam_learn_set_state continues exactly
  * where the saved one was: every kernel of the step reduces in a fixed order,
- * so the same batches give the same bits. Both calls block. */
+ * so the same batches give the same bits. Both calls block until their copies
+ * are done. */
 size_t pam_learn_state_size(void);
 pam_status pam_learn_get_state(pam_learn_t l, float *state, size_t n, long long *adam_steps);
 pam_status pam_learn_set_state(pam_learn_t l, const float *state, size_t n, long long adam_steps);

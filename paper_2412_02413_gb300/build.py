@@ -4,6 +4,8 @@ Each .cu translation unit compiles in parallel to ``_build/``, and the
 objects link into ``paper_2412_02413_gb300/libpam.so``. A rebuild happens only
 when a source or header is newer than the library. There is no cmake and no
 torch extension machinery: the library is a plain C-ABI shared object.
+The benchmark's FP32 FMA-rate probe (``probe/fma_probe.cu``) links into its
+own ``libpam_probe.so``, outside the product library.
 """
 from __future__ import annotations
 
@@ -20,6 +22,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpam.so")
+PROBE_SRC = os.path.join(PKG, "probe", "fma_probe.cu")
+PROBE_LIB = os.path.join(PKG, "libpam_probe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -42,10 +46,10 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
+    return all(os.path.getmtime(d) <= t for d in _deps() + [PROBE_SRC])
 
 
 def _compile(src: str, verbose: bool, ptxas_v: bool) -> str:
@@ -61,15 +65,8 @@ def _compile(src: str, verbose: bool, ptxas_v: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    """Compile and link libpam.so; returns its path."""
-    if not force and not ptxas_v and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, ptxas_v), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+def _link(objs, out: str, verbose: bool) -> None:
+    tmp = out + f".tmp{os.getpid()}"
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(shutil.which(nvcc()) or nvcc()))), "lib64")
     cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "-rpath", "-Xlinker", cuda_lib,
                              "-o", tmp] + objs
@@ -78,7 +75,19 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
+    """Compile and link libpam.so (and the benchmark's libpam_probe.so); returns libpam's path."""
+    if not force and not ptxas_v and up_to_date():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    srcs = sources() + [PROBE_SRC]
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(lambda s: _compile(s, verbose, ptxas_v), srcs))
+    _link(objs[:-1], LIB, verbose)
+    _link(objs[-1:], PROBE_LIB, verbose)
     return LIB
 
 

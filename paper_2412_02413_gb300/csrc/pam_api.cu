@@ -100,7 +100,9 @@ pam_status check_dev_ptr(const void *ptr, const char *name, bool required)
     return PAM_OK;
 }
 
-pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
+}  // namespace
+
+pam_status pam::check_desc_ranges(const pam_plan_desc *d)
 {
     if (d->n_elem < 8 || d->n_elem > 256) return fail(PAM_ERR_INVALID_ARG, "n_elem must be in [8, 256]");
     if (!finite_pos(d->pitch_m)) return fail(PAM_ERR_INVALID_ARG, "pitch_m must be finite and > 0");
@@ -111,6 +113,61 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
                     "n_samples must be in [64, 8192]");
     if (!is_pow2(d->n_samples))
         return fail(PAM_ERR_UNSUPPORTED, "n_samples must be a power of two for the radix-4/2 time FFT");
+    if (d->nz < 1 || d->nz > 65535) return fail(PAM_ERR_INVALID_ARG, "nz must be in [1, 65535]");
+    if (!std::isfinite(d->z0_m) || d->z0_m < 0.0) return fail(PAM_ERR_INVALID_ARG, "z0_m must be finite and >= 0");
+    if (!finite_pos(d->dz_m)) return fail(PAM_ERR_INVALID_ARG, "dz_m must be finite and > 0");
+    if (!(d->eps > 0.0f) || !(d->eps <= 1.0f)) return fail(PAM_ERR_INVALID_ARG, "eps must be in (0, 1]");
+    return PAM_OK;
+}
+
+pam_status pam::desc_bins(const pam_plan_desc *d, int *bins, int *n_out)
+{
+    const int nt = d->n_samples;
+    int nb = 0;
+    if (d->bins) {
+        if (d->n_bins < 1 || d->n_bins > 8192) return fail(PAM_ERR_INVALID_ARG, "n_bins must be in [1, 8192]");
+        for (int b = 0; b < d->n_bins; ++b) {
+            // bins[b] >= b + 1 and 2 bins[b] < nt <= 8192, so at most kMaxBins - 1 entries are written
+            const int k = d->bins[b];
+            if (k <= 0 || 2 * k >= nt) return fail(PAM_ERR_INVALID_ARG, "every bin must satisfy 0 < k < n_samples/2");
+            if (b > 0 && k <= d->bins[b - 1]) return fail(PAM_ERR_INVALID_ARG, "bins must be strictly increasing");
+            bins[nb++] = k;
+        }
+    } else {
+        if (!std::isfinite(d->f_lo_hz) || !std::isfinite(d->f_hi_hz) || d->f_hi_hz < d->f_lo_hz)
+            return fail(PAM_ERR_INVALID_ARG, "band must satisfy f_lo_hz <= f_hi_hz (finite)");
+        for (int k = 1; 2 * k < nt; ++k) {
+            const double f = (double)k * d->fs_hz / (double)nt;
+            if (f >= d->f_lo_hz && f <= d->f_hi_hz) bins[nb++] = k;
+        }
+        if (nb == 0) return fail(PAM_ERR_INVALID_ARG, "the band holds no DFT bin");
+    }
+    *n_out = nb;
+    return PAM_OK;
+}
+
+pam_status pam::desc_apod(const pam_plan_desc *d, int n_apod, float *apod)
+{
+    const int ne = d->n_elem;
+    if (d->apod) {
+        for (int x = 0; x < n_apod * ne; ++x) {
+            if (!std::isfinite(d->apod[x])) return fail(PAM_ERR_INVALID_ARG, "apodization weights must be finite");
+            apod[x] = d->apod[x];
+        }
+    } else {
+        if (d->pattern_m < 1 || d->pattern_m > ne) return fail(PAM_ERR_INVALID_ARG, "pattern_m must be in [1, n_elem]");
+        for (int q = 0; q < n_apod; ++q)
+            for (int e = 0; e < ne; ++e) apod[q * ne + e] = ((e / d->pattern_m) % n_apod == q) ? 1.0f : 0.0f;
+    }
+    return PAM_OK;
+}
+
+namespace {
+
+pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
+{
+    pam_status s = pam::check_desc_ranges(d);
+    if (s != PAM_OK) return s;
     const bool up2 = (d->flags & PAM_LATERAL_UPSAMPLE2X) != 0;
     const bool pad2 = (d->flags & PAM_LATERAL_PAD2X) != 0;
     if (up2 && pad2) return fail(PAM_ERR_INVALID_ARG, "PAM_LATERAL_UPSAMPLE2X and PAM_LATERAL_PAD2X exclude each other");
@@ -123,11 +180,7 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     if (nev != 16 && nev != 32 && nev != 64 && nev != 128)
         return fail(PAM_ERR_UNSUPPORTED, "the lateral DFT length (n_elem, or 2 n_elem with PAM_LATERAL_UPSAMPLE2X "
                                          "or PAM_LATERAL_PAD2X) must be 16, 32, 64 or 128");
-    if (d->nz < 1 || d->nz > 65535) return fail(PAM_ERR_INVALID_ARG, "nz must be in [1, 65535]");
-    if (!std::isfinite(d->z0_m) || d->z0_m < 0.0) return fail(PAM_ERR_INVALID_ARG, "z0_m must be finite and >= 0");
-    if (!finite_pos(d->dz_m)) return fail(PAM_ERR_INVALID_ARG, "dz_m must be finite and > 0");
     if (d->n_apod < 1 || d->n_apod > 3) return fail(PAM_ERR_INVALID_ARG, "n_apod must be 1, 2 or 3");
-    if (!(d->eps > 0.0f) || !(d->eps <= 1.0f)) return fail(PAM_ERR_INVALID_ARG, "eps must be in (0, 1]");
     if (d->max_frames < 1 || d->max_frames > 65535) return fail(PAM_ERR_INVALID_ARG, "max_frames must be in [1, 65535]");
     const unsigned form_bits =
         PAM_FORM_GEMM_BF16 | PAM_FORM_GEMM_FP16 | PAM_FORM_GEMM_BF16_SPLIT | PAM_FORM_GEMM_FP16_SPLIT;
@@ -139,39 +192,14 @@ pam_status validate_and_fill(const pam_plan_desc *d, pam_plan_s *p)
     if (form && pad2) return fail(PAM_ERR_UNSUPPORTED, "PAM_LATERAL_PAD2X runs on the plain FP32 path only");
 
     const int nt = d->n_samples;
-    p->bins.clear();
-    if (d->bins) {
-        if (d->n_bins < 1 || d->n_bins > 8192) return fail(PAM_ERR_INVALID_ARG, "n_bins must be in [1, 8192]");
-        for (int b = 0; b < d->n_bins; ++b) {
-            int k = d->bins[b];
-            if (k <= 0 || 2 * k >= nt) return fail(PAM_ERR_INVALID_ARG, "every bin must satisfy 0 < k < n_samples/2");
-            if (b > 0 && k <= d->bins[b - 1]) return fail(PAM_ERR_INVALID_ARG, "bins must be strictly increasing");
-            p->bins.push_back(k);
-        }
-    } else {
-        if (!std::isfinite(d->f_lo_hz) || !std::isfinite(d->f_hi_hz) || d->f_hi_hz < d->f_lo_hz)
-            return fail(PAM_ERR_INVALID_ARG, "band must satisfy f_lo_hz <= f_hi_hz (finite)");
-        for (int k = 1; 2 * k < nt; ++k) {
-            double f = (double)k * d->fs_hz / (double)nt;
-            if (f >= d->f_lo_hz && f <= d->f_hi_hz) p->bins.push_back(k);
-        }
-        if (p->bins.empty()) return fail(PAM_ERR_INVALID_ARG, "the band holds no DFT bin");
-        if (p->bins.size() > 8192) return fail(PAM_ERR_INVALID_ARG, "the band holds more than 8192 bins");
-    }
+    int nb = 0;
+    p->bins.assign(pam::kMaxBins, 0);
+    if ((s = pam::desc_bins(d, p->bins.data(), &nb)) != PAM_OK) return s;
+    p->bins.resize(nb);
 
     const int ne = d->n_elem, na = d->n_apod;
     p->apod.assign((size_t)na * ne, 0.0f);
-    if (d->apod) {
-        for (int x = 0; x < na * ne; ++x) {
-            if (!std::isfinite(d->apod[x])) return fail(PAM_ERR_INVALID_ARG, "apodization weights must be finite");
-            p->apod[x] = d->apod[x];
-        }
-    } else {
-        if (d->pattern_m < 1 || d->pattern_m > ne) return fail(PAM_ERR_INVALID_ARG, "pattern_m must be in [1, n_elem]");
-        for (int q = 0; q < na; ++q)
-            for (int e = 0; e < ne; ++e)
-                p->apod[(size_t)q * ne + e] = ((e / d->pattern_m) % na == q) ? 1.0f : 0.0f;
-    }
+    if ((s = pam::desc_apod(d, na, p->apod.data())) != PAM_OK) return s;
 
     p->d = *d;
     p->d.bins = nullptr;

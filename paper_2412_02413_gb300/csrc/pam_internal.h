@@ -194,4 +194,19 @@ cudaError_t launch_prec_bands(const pam_plan_s &p, const float2 *S, int n_frames
 pam_status set_error(pam_status s, const char *msg);
 int choose_split(const pam_plan_s &p, int n_frames);
 
+// Descriptor checks shared by pam_plan_create and pam_as_tax_static, writing
+// only to caller-provided fixed arrays (no allocation). kMaxBins bounds every
+// valid bin list: bins are strictly increasing in (0, n_samples/2) and
+// n_samples <= 8192.
+constexpr int kMaxBins = 4096;
+// Ranges of the geometry fields common to every entry point: n_elem, pitch,
+// fs, c, n_samples (a power of two in [64, 8192]), nz, z0, dz and eps.
+pam_status check_desc_ranges(const pam_plan_desc *d);
+// The bins of Omega (Sec. II-E band, or the explicit list) into bins[kMaxBins];
+// *n_out gets their count.
+pam_status desc_bins(const pam_plan_desc *d, int *bins, int *n_out);
+// The n_apod apodizations (explicit, or Pattern-m of Sec. II-A/C) into
+// apod[n_apod * n_elem].
+pam_status desc_apod(const pam_plan_desc *d, int n_apod, float *apod);
+
 }  // namespace pam

@@ -710,6 +710,12 @@ struct pam_learn_s {
     int *counters = nullptr;
     float *gate_err = nullptr;
     int *gate_pass = nullptr;
+    // ordering of the host-blocking state calls: `done` is recorded on the
+    // caller's stream at the end of every queued call, and the state copies run
+    // on the private stream `own` behind it, so they wait for this handle's work
+    // only, not for other streams of the process
+    cudaStream_t own = nullptr;
+    cudaEvent_t done = nullptr;
 };
 
 namespace {
@@ -756,8 +762,16 @@ void learn_free(pam_learn_s *l)
     fr(l->gate_err); fr(l->gate_pass);
     if (l->gemm) pam_destroy(l->gemm);
     if (l->plan) pam_destroy(l->plan);
+    if (l->done) cudaEventDestroy(l->done);
+    if (l->own) cudaStreamDestroy(l->own);
     delete l;
 }
+
+// End of a queued call on `st`: later state calls wait for this point.
+cudaError_t mark_done(pam_learn_s *l, cudaStream_t st) { return cudaEventRecord(l->done, st); }
+
+// The private stream, ordered after this handle's most recent queued call.
+cudaError_t own_after_last_call(pam_learn_s *l) { return cudaStreamWaitEvent(l->own, l->done, 0); }
 
 pam_status check_dev(const void *ptr, const char *name, bool required)
 {
@@ -1004,6 +1018,9 @@ pam_status pam_learn_create(const pam_plan_desc *d, pam_learn_t *out)
         LALLOC(cudaMemcpy(l->frames, fr.data(), sizeof(pam::BatchFrame) * F, cudaMemcpyHostToDevice));
         LALLOC(cudaMemcpy(l->items_all, all.data(), sizeof(int2) * all.size(), cudaMemcpyHostToDevice));
     }
+    LALLOC(cudaStreamCreateWithFlags(&l->own, cudaStreamNonBlocking));
+    LALLOC(cudaEventCreateWithFlags(&l->done, cudaEventDisableTiming));
+    LALLOC(cudaEventRecord(l->done, l->own));
     LALLOC(pam::prepare_learn_kernels());
     if (l->W == 128) LALLOC(pam::prepare_conv_tc());
     LALLOC(run_prep(l, nullptr));
@@ -1026,13 +1043,13 @@ pam_status pam_learn_set_params(pam_learn_t l, const float *params, size_t n)
     if (n != pam::N_PARAMS) return lfail(PAM_ERR_INVALID_ARG, "parameter count differs from pam_learn_n_params()");
     for (size_t i = 0; i < n; ++i)
         if (!std::isfinite(params[i])) return lfail(PAM_ERR_NUMERIC, "non-finite parameter");
-    LTRY(cudaDeviceSynchronize());
-    LTRY(cudaMemcpy(l->params, params, n * sizeof(float), cudaMemcpyHostToDevice));
-    LTRY(cudaMemset(l->adam_m, 0, n * sizeof(float)));
-    LTRY(cudaMemset(l->adam_v, 0, n * sizeof(float)));
+    LTRY(own_after_last_call(l));
+    LTRY(cudaMemcpyAsync(l->params, params, n * sizeof(float), cudaMemcpyHostToDevice, l->own));
+    LTRY(cudaMemsetAsync(l->adam_m, 0, n * sizeof(float), l->own));
+    LTRY(cudaMemsetAsync(l->adam_v, 0, n * sizeof(float), l->own));
     l->t = 0;
-    LTRY(run_prep(l, nullptr));
-    LTRY(cudaDeviceSynchronize());
+    LTRY(run_prep(l, l->own));
+    LTRY(cudaStreamSynchronize(l->own));
     return PAM_OK;
 }
 
@@ -1040,8 +1057,9 @@ pam_status pam_learn_get_params(pam_learn_t l, float *params, size_t n)
 {
     if (!l || !params) return lfail(PAM_ERR_INVALID_ARG, "NULL argument");
     if (n != pam::N_PARAMS) return lfail(PAM_ERR_INVALID_ARG, "parameter count differs from pam_learn_n_params()");
-    LTRY(cudaDeviceSynchronize());
-    LTRY(cudaMemcpy(params, l->params, n * sizeof(float), cudaMemcpyDeviceToHost));
+    LTRY(own_after_last_call(l));
+    LTRY(cudaMemcpyAsync(params, l->params, n * sizeof(float), cudaMemcpyDeviceToHost, l->own));
+    LTRY(cudaStreamSynchronize(l->own));
     return PAM_OK;
 }
 
@@ -1052,10 +1070,11 @@ pam_status pam_learn_get_state(pam_learn_t l, float *state, size_t n, long long 
     if (!l || !state) return lfail(PAM_ERR_INVALID_ARG, "NULL argument");
     if (n != 3 * pam::N_PARAMS) return lfail(PAM_ERR_INVALID_ARG, "state size differs from pam_learn_state_size()");
     const size_t np = pam::N_PARAMS;
-    LTRY(cudaDeviceSynchronize());
-    LTRY(cudaMemcpy(state, l->params, np * sizeof(float), cudaMemcpyDeviceToHost));
-    LTRY(cudaMemcpy(state + np, l->adam_m, np * sizeof(float), cudaMemcpyDeviceToHost));
-    LTRY(cudaMemcpy(state + 2 * np, l->adam_v, np * sizeof(float), cudaMemcpyDeviceToHost));
+    LTRY(own_after_last_call(l));
+    LTRY(cudaMemcpyAsync(state, l->params, np * sizeof(float), cudaMemcpyDeviceToHost, l->own));
+    LTRY(cudaMemcpyAsync(state + np, l->adam_m, np * sizeof(float), cudaMemcpyDeviceToHost, l->own));
+    LTRY(cudaMemcpyAsync(state + 2 * np, l->adam_v, np * sizeof(float), cudaMemcpyDeviceToHost, l->own));
+    LTRY(cudaStreamSynchronize(l->own));
     if (adam_steps) *adam_steps = l->t;
     return PAM_OK;
 }
@@ -1070,13 +1089,13 @@ pam_status pam_learn_set_state(pam_learn_t l, const float *state, size_t n, long
     for (size_t i = 2 * pam::N_PARAMS; i < n; ++i)
         if (state[i] < 0.0f) return lfail(PAM_ERR_INVALID_ARG, "Adam second moments must be >= 0");
     const size_t np = pam::N_PARAMS;
-    LTRY(cudaDeviceSynchronize());
-    LTRY(cudaMemcpy(l->params, state, np * sizeof(float), cudaMemcpyHostToDevice));
-    LTRY(cudaMemcpy(l->adam_m, state + np, np * sizeof(float), cudaMemcpyHostToDevice));
-    LTRY(cudaMemcpy(l->adam_v, state + 2 * np, np * sizeof(float), cudaMemcpyHostToDevice));
+    LTRY(own_after_last_call(l));
+    LTRY(cudaMemcpyAsync(l->params, state, np * sizeof(float), cudaMemcpyHostToDevice, l->own));
+    LTRY(cudaMemcpyAsync(l->adam_m, state + np, np * sizeof(float), cudaMemcpyHostToDevice, l->own));
+    LTRY(cudaMemcpyAsync(l->adam_v, state + 2 * np, np * sizeof(float), cudaMemcpyHostToDevice, l->own));
     l->t = adam_steps;
-    LTRY(run_prep(l, nullptr));
-    LTRY(cudaDeviceSynchronize());
+    LTRY(run_prep(l, l->own));
+    LTRY(cudaStreamSynchronize(l->own));
     return PAM_OK;
 }
 
@@ -1141,6 +1160,7 @@ pam_status pam_learn_example(pam_learn_t l, const float *rf, int n_frames, void 
                                     l->counters + 1, out, st));
         l->kernels += 3;
     }
+    LTRY(mark_done(l, st));
     return PAM_OK;
 }
 
@@ -1158,6 +1178,7 @@ pam_status pam_learn_forward(pam_learn_t l, const void *features, int n_frames, 
     pam::head_kernel<<<g, pam::EPI_THREADS, 0, st>>>(l->z, l->E, (int)l->npix, l->plan->d.eps, rho, l->rmax, l->peak);
     LTRY(cudaGetLastError());
     l->kernels += 2;
+    LTRY(mark_done(l, st));
     return PAM_OK;
 }
 
@@ -1175,6 +1196,7 @@ pam_status pam_learn_grads(pam_learn_t l, const void *features, const float *tar
     if (grads) {
         LTRY(cudaMemcpyAsync(grads, l->grads, pam::N_PARAMS * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
+    LTRY(mark_done(l, st));
     return PAM_OK;
 }
 
@@ -1199,6 +1221,7 @@ pam_status pam_learn_train_step(pam_learn_t l, const void *features, const float
     LTRY(cudaGetLastError());
     LTRY(run_prep(l, st));
     l->kernels += 1;
+    LTRY(mark_done(l, st));
     return PAM_OK;
 }
 
@@ -1254,6 +1277,7 @@ pam_status pam_learn_tax(pam_learn_t l, const float *rf, int n_frames, float *im
         LTRY(cudaGetLastError());
         l->kernels += 7;
     }
+    LTRY(mark_done(l, st));
     return PAM_OK;
 }
 

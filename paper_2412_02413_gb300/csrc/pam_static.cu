@@ -45,8 +45,6 @@ pam_status cuda_fail(cudaError_t e, const char *where)
     return pam::set_error(PAM_ERR_CUDA, m);
 }
 
-bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
-
 // One-time set-up of the current device: the device address of g_scratch and
 // the kernels' shared-memory attributes.
 pam_status setup_device(int dev, unsigned char **base)
@@ -82,6 +80,19 @@ pam_status check_dev(const void *ptr, const char *what)
 }
 
 size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Writes NaN to every output element when a kernel of this call reported an
+// expired wait in the status word; otherwise each block only reads the word.
+__global__ void static_expiry_kernel(const int *__restrict__ status, float *__restrict__ image,
+                                     float *__restrict__ rho_n, size_t n)
+{
+    if (*status == 0) return;
+    const float nan = __int_as_float(0x7fc00000);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        image[i] = nan;
+        if (rho_n) rho_n[i] = nan;
+    }
+}
 
 // Carves the plan tables and the one-frame workspace out of `base`. With
 // base == nullptr it only counts the bytes.
@@ -121,51 +132,22 @@ extern "C" pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf,
 {
     if (!d) return fail(PAM_ERR_INVALID_ARG, "descriptor is NULL");
     if (n_frames < 0) return fail(PAM_ERR_INVALID_ARG, "n_frames must be >= 0");
-    // Descriptor checks (the same ranges as pam_plan_create) on stack copies only.
+    // Descriptor checks: the ranges every entry point shares, then this entry
+    // point's own limits; the bins and apodizations go to stack arrays.
+    pam_status s = pam::check_desc_ranges(d);
+    if (s != PAM_OK) return s;
     const int ne = d->n_elem, nt = d->n_samples, nz = d->nz;
     const int nx = d->nx == 0 ? ne : d->nx;
-    if (ne < 8 || ne > 256) return fail(PAM_ERR_INVALID_ARG, "n_elem must be in [8, 256]");
     if (nx != ne || (nx != 16 && nx != 32 && nx != 64 && nx != 128))
         return fail(PAM_ERR_UNSUPPORTED, "nx must equal n_elem and be 16, 32, 64 or 128");
-    if (nt < 64 || nt > 8192 || (nt & (nt - 1))) return fail(PAM_ERR_UNSUPPORTED, "n_samples must be a power of two in [64, 8192]");
-    if (nz < 1 || nz > 65535) return fail(PAM_ERR_INVALID_ARG, "nz must be in [1, 65535]");
-    if (!finite_pos(d->pitch_m) || !finite_pos(d->fs_hz) || !finite_pos(d->c_mps) || !finite_pos(d->dz_m) ||
-        !std::isfinite(d->z0_m) || d->z0_m < 0.0)
-        return fail(PAM_ERR_INVALID_ARG, "pitch, fs, c, dz must be finite and > 0; z0 finite and >= 0");
     if (d->n_apod != 3) return fail(PAM_ERR_INVALID_ARG, "pam_as_tax_static needs n_apod == 3");
-    if (!(d->eps > 0.0f) || !(d->eps <= 1.0f)) return fail(PAM_ERR_INVALID_ARG, "eps must be in (0, 1]");
-    if (d->flags & ~PAM_EVANESCENT_ZERO) return fail(PAM_ERR_INVALID_ARG, "unknown flag bits");
-
-    int bins_h[4096];  // every valid bin is below nt/2 <= 4096
+    if (d->flags & ~PAM_EVANESCENT_ZERO)
+        return fail(PAM_ERR_INVALID_ARG, "pam_as_tax_static takes no flag but PAM_EVANESCENT_ZERO");
+    int bins_h[pam::kMaxBins];
     int nb = 0;
-    if (d->bins) {
-        if (d->n_bins < 1 || d->n_bins > nt / 2) return fail(PAM_ERR_INVALID_ARG, "n_bins out of range");
-        for (int b = 0; b < d->n_bins; ++b) {
-            int k = d->bins[b];
-            if (k <= 0 || 2 * k >= nt || (b > 0 && k <= d->bins[b - 1]))
-                return fail(PAM_ERR_INVALID_ARG, "bins must be strictly increasing with 0 < k < n_samples/2");
-            bins_h[nb++] = k;
-        }
-    } else {
-        if (!std::isfinite(d->f_lo_hz) || !std::isfinite(d->f_hi_hz) || d->f_hi_hz < d->f_lo_hz)
-            return fail(PAM_ERR_INVALID_ARG, "band must satisfy f_lo_hz <= f_hi_hz");
-        for (int k = 1; 2 * k < nt; ++k) {
-            double f = (double)k * d->fs_hz / (double)nt;
-            if (f >= d->f_lo_hz && f <= d->f_hi_hz) bins_h[nb++] = k;
-        }
-        if (nb == 0) return fail(PAM_ERR_INVALID_ARG, "the band holds no DFT bin");
-    }
+    if ((s = pam::desc_bins(d, bins_h, &nb)) != PAM_OK) return s;
     float apod_h[3 * 256];
-    if (d->apod) {
-        for (int x = 0; x < 3 * ne; ++x) {
-            if (!std::isfinite(d->apod[x])) return fail(PAM_ERR_INVALID_ARG, "apodization weights must be finite");
-            apod_h[x] = d->apod[x];
-        }
-    } else {
-        if (d->pattern_m < 1 || d->pattern_m > ne) return fail(PAM_ERR_INVALID_ARG, "pattern_m must be in [1, n_elem]");
-        for (int q = 0; q < 3; ++q)
-            for (int e = 0; e < ne; ++e) apod_h[q * ne + e] = ((e / d->pattern_m) % 3 == q) ? 1.0f : 0.0f;
-    }
+    if ((s = pam::desc_apod(d, 3, apod_h)) != PAM_OK) return s;
 
     // Geometry of a one-frame plan whose memory is g_scratch (no vectors are filled).
     pam_plan_s p;
@@ -204,7 +186,14 @@ extern "C" pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf,
         return fail(PAM_ERR_INVALID_ARG, m);
     }
     if (n_frames == 0) return PAM_OK;
-    pam_status s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // The uploads below come from pageable stack memory, which stream capture
+    // does not allow; refuse before anything is queued, so that the caller's
+    // capture stays valid.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess) return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(PAM_ERR_UNSUPPORTED, "pam_as_tax_static cannot run on a capturing stream");
     if ((s = check_dev(rf, "rf must be 16-byte aligned device memory")) != PAM_OK) return s;
     if ((s = check_dev(image_tax, "image_tax must be 16-byte aligned device memory")) != PAM_OK) return s;
     if (rho_n && (s = check_dev(rho_n, "rho_n must be 16-byte aligned device memory")) != PAM_OK) return s;
@@ -213,7 +202,6 @@ extern "C" pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf,
     if ((s = setup_device(dev, &base)) != PAM_OK) return s;
     carve(p, ns, base);
 
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     // Pageable copies: each returns once the source has been staged, so the
     // stack arrays may go out of scope afterwards.
     if ((e = cudaMemcpyAsync(p.t.bins, bins_h, nb * sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -240,5 +228,14 @@ extern "C" pam_status pam_as_tax_static(const pam_plan_desc *d, const float *rf,
             return cuda_fail(e, "propagate/correlate");
         if ((e = pam::launch_epilogue(p, 1, 3, ns, out, st)) != cudaSuccess) return cuda_fail(e, "epilogue");
     }
+    // Host-side injection for the tests of the expiry report: a wait that
+    // nothing completes gives up after about a second and sets the status word.
+    if (pam::fault_injected("static_wait") && (e = pam::launch_expire_wait(p.w.status, st)) != cudaSuccess)
+        return cuda_fail(e, "injected wait");
+    // No plan means no pam_sync to read the device status word, so an expired
+    // bounded wait (a row tile that stopped early) shows in the outputs: every
+    // element of image_tax and rho_n becomes NaN.
+    static_expiry_kernel<<<2 * p.num_sms, 256, 0, st>>>(p.w.status, image_tax, rho_n, (size_t)n_frames * npix);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "expiry report");
     return PAM_OK;
 }

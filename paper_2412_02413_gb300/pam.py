@@ -88,7 +88,6 @@ _SIGS = {
     "pam_as3": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP]),
     "pam_image_metrics": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_float, _VP, _VP]),
-    "pam_fp32_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "pam_learn_n_params": (ctypes.c_size_t, []),
     "pam_learn_create": (ctypes.c_int, [ctypes.POINTER(PlanDesc), ctypes.POINTER(_VP)]),
     "pam_learn_destroy": (None, [_VP]),
@@ -645,13 +644,6 @@ def image_metrics(maps, x0: float, dx: float, z0: float, dz: float, alpha: float
     n_in = raw[:, 5].copy().view(np.int32)
     return [dict(zip(METRIC_FIELDS, [float(v) for v in r[:5]] + [int(n)])) for r, n in zip(raw, n_in)]
 
-
-def fp32_fma_rate(iters: int = 2048) -> float:
-    """Measured FP32 FMA rate of the current device in TFLOP/s (``pam_fp32_fma_rate``)."""
-    _require_cuda()
-    v = ctypes.c_double(0.0)
-    _check(load().pam_fp32_fma_rate(int(iters), ctypes.byref(v)))
-    return float(v.value)
 
 
 def unpack_features(features, nz: int, nx: int):

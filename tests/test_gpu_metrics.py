@@ -70,10 +70,26 @@ def test_measures_match_oracle(alpha):
     plan.close()
 
 
+def _probe_rate(packed):
+    import ctypes
+    import os
+
+    from paper_2412_02413_gb300 import build
+    lib = ctypes.CDLL(build.PROBE_LIB)
+    lib.pam_probe_fp32_fma_rate.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.pam_probe_fp32_fma_rate.restype = ctypes.c_int
+    v = ctypes.c_double(0.0)
+    assert os.path.exists(build.PROBE_LIB)
+    assert lib.pam_probe_fp32_fma_rate(1024, int(packed), ctypes.byref(v)) == 0
+    return v.value
+
+
 def test_fp32_fma_rate_is_plausible():
-    """The FMA probe's rate lies between a quarter of the unit-count peak at
-    1 GHz and that peak at 2.2 GHz (128 FP32 lanes per SM, 2 flops per FMA)."""
-    from paper_2412_02413_gb300 import pam
+    """The benchmark's FMA probe (its own library, not libpam): the scalar and
+    the packed two-wide rates lie between a quarter of the unit-count peak at
+    1 GHz and twice that peak at 2.2 GHz (128 FP32 lanes per SM, 2 flops per
+    FMA)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    rate = pam.fp32_fma_rate(1024)
-    assert 0.25 * sms * 128 * 2 * 1.0e9 / 1e12 < rate < sms * 128 * 2 * 2.2e9 / 1e12, rate
+    for packed in (0, 1):
+        rate = _probe_rate(packed)
+        assert 0.25 * sms * 128 * 2 * 1.0e9 / 1e12 < rate < 2 * sms * 128 * 2 * 2.2e9 / 1e12, (packed, rate)
