@@ -278,7 +278,7 @@ pam_status alloc_plan(pam_plan_s *p)
     PAM_TRY(dalloc(&p->t.live, nb * nx));
     PAM_TRY(dalloc(&p->t.bin_evan, nb));
     PAM_TRY(dalloc(&p->w.S, F * nb * ne));
-    PAM_TRY(dalloc(&p->w.Q, F * nb * (size_t)p->n_apod * nx));
+    PAM_TRY(dalloc(&p->w.Q, F * nb * pam::q_per_bin(p->n_apod, nx)));
     if (pam::fault_injected("alloc")) return fail(PAM_ERR_OOM, "injected allocation failure (PAM_FAULT=alloc)");
     int rows = pam::prop_rows_per_cta(p->nx);
     int row_tiles = (p->nz + rows - 1) / rows;

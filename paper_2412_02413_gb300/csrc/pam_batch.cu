@@ -452,7 +452,7 @@ pam_status pam_batch_create(const pam_plan_desc *common, const pam_frame_desc *f
         dh[f].nt = b->nt[f];
         dh[f].n_bins = b->nbf[f];
         pam::BatchFrame &x = fh[f];
-        x.Q = p.w.Q + (size_t)f * b->n_bins * b->napq * b->nx;
+        x.Q = p.w.Q + (size_t)f * b->n_bins * pam::q_per_bin(b->napq, b->nx);
         x.phase = b->phase + (size_t)f * b->n_bins * b->nx;
         x.bin_evan = b->bin_evan + (size_t)f * b->n_bins;
         x.n_bins = b->nbf[f];

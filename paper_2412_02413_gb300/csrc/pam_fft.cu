@@ -167,11 +167,21 @@ time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const 
 }
 
 // -------------------------------------------------------- lateral FFT ----
-// Q[f][b][q][u] = live[b][u] / nx * sum_e apod_q[e] S[f][b][e] exp(-2 pi i u e / nx).
-// live_fs is the frame stride of the mask (0: one mask for all frames).
-// One CTA per (bin, frame): the napq apodized rows are transformed together
-// by the shared-memory FFT. The 1/nx of the inverse lateral transform is
-// applied here.
+// V_q[u] = live[b][u] / nx * sum_e apod_q[e] S[f][b][e] exp(-2 pi i u e / nx),
+// the propagator's input (Eq. 1-2); live_fs is the frame stride of the mask
+// (0: one mask for all frames). One CTA per (bin, frame): the napq apodized
+// rows are transformed together by the shared-memory FFT. The 1/nx of the
+// inverse lateral transform is applied here.
+//
+// Output layout, for the fused kernel's radix-2 decimation-in-frequency split
+// of the inverse lateral DFT: half g of the output pixels needs
+//   x_g[u0] = W^(g u0) (P[u0] + (-1)^g P[u0 + H]),  H = nx/2, W = exp(2 pi i/nx),
+// with P[u] = V[u] exp(i kz_u z). Writing u0 = L2 n1 + n2 (L2 = nx/16), the
+// lane (g, n2) reads per (q, n1) one pair of complex values that it multiplies
+// with its own phasor (u = g H + u0) and its partner lane's (u = (1-g) H + u0):
+//   g = 0: ( V[u0],                V[u0 + H]          )
+//   g = 1: ( -W^u0 V[u0 + H],      W^u0 V[u0]         )
+// stored at Q[f][b][q][n1][g][n2][2] (q_per_bin = 2 napq nx complex values).
 constexpr int LAT_THREADS = 128;
 
 __global__ void __launch_bounds__(LAT_THREADS)
@@ -193,11 +203,20 @@ lateral_kernel(const float2 *__restrict__ S, int ne, int nx, int log2nx, int n_b
     __syncthreads();
     const float2 *X = stockham(x, y, nx, log2nx, napq, tws, threadIdx.x, LAT_THREADS);
     const float inv_nx = 1.0f / (float)nx;
-    float2 *dst = Q + ((size_t)f * n_bins + b) * napq * nx;
+    float2 *dst = Q + ((size_t)f * n_bins + b) * (2 * napq * nx);
+    const int H = nx / 2, L2 = nx / 16;
     for (int i = threadIdx.x; i < napq * nx; i += LAT_THREADS) {
-        const int u = i & (nx - 1);
+        const int q = i / nx, u = i & (nx - 1);
         const float l = live[(size_t)f * live_fs + (size_t)b * nx + u] * inv_nx;
-        dst[i] = make_float2(X[i].x * l, X[i].y * l);
+        const float2 v = make_float2(X[i].x * l, X[i].y * l);
+        const int hi = u >= H ? 1 : 0, u0 = u - hi * H, n1 = u0 / L2, n2 = u0 - n1 * L2;
+        float ws, wc;
+        sincospif(2.0f * (float)u0 / (float)nx, &ws, &wc);   // W^u0, exact argument
+        const float sg = hi ? -1.0f : 1.0f;
+        const float2 vw = make_float2(sg * (wc * v.x - ws * v.y), sg * (wc * v.y + ws * v.x));
+        const size_t base = (size_t)(q * 8 + n1) * 2;
+        dst[((base + 0) * L2 + n2) * 2 + hi] = v;
+        dst[((base + 1) * L2 + n2) * 2 + (1 - hi)] = vw;
     }
 }
 

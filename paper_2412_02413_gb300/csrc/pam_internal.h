@@ -23,6 +23,11 @@ int prop_rows_per_cta(int nx);
 // Bin splits up to this size reduce inside a thread-block cluster (portable limit).
 constexpr int kMaxClusterSplit = 8;
 
+// Complex entries of the staged spectra per (frame, bin): the fused kernel's
+// paired layout holds every aperture's nx values twice, once per half of its
+// radix-2 split (see lateral_kernel).
+inline size_t q_per_bin(int napq, int nx) { return (size_t)2 * napq * nx; }
+
 // Destination of the per-pixel epilogue (maps of one call, [F][nz][nx]).
 struct EpiOut {
     float eps = 1e-3f;

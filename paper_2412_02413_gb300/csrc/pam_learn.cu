@@ -1003,7 +1003,7 @@ pam_status pam_learn_create(const pam_plan_desc *d, pam_learn_t *out)
         std::vector<int2> all(F * l->tiles);
         for (size_t f = 0; f < F; ++f) {
             pam::BatchFrame &b = fr[f];
-            b.Q = p.w.Q + f * p.n_bins * 3 * p.nx;
+            b.Q = p.w.Q + f * p.n_bins * pam::q_per_bin(3, p.nx);
             b.phase = p.t.phase;
             b.bin_evan = p.t.bin_evan;
             b.n_bins = p.n_bins;

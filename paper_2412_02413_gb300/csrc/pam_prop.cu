@@ -127,7 +127,7 @@ constexpr size_t prop_smem_bytes()
 {
     using S = Shape<NX>;
     return (size_t)128                                    // full / empty mbarriers
-           + (size_t)NSTAGE * NAP * NX * sizeof(float2)   // spectra, one per stage
+           + (size_t)NSTAGE * 2 * NAP * NX * sizeof(float2)   // paired spectra, one per stage
            + (size_t)NSTAGE * NX * sizeof(uint4)          // phase words + evanescent coefficients
            + (size_t)(NX / 2) * sizeof(float2)            // exp(+2 pi i m / (nx/2))
            + (size_t)PROP_WARPS * NAP * S::RPW * 2 * S::RS * sizeof(float2);  // transposes
@@ -205,7 +205,7 @@ template <int NAP, int NX>
 struct PropSmem {
     uint64_t *full;   // [NSTAGE] data of a stage has landed
     uint64_t *empty;  // [NSTAGE] all warps are done with a stage
-    float2 *sQ;       // [NSTAGE][NAP][NX] spectra
+    float4 *sQ;       // [NSTAGE][NAP][8][2][NX/16] paired spectra (lateral_kernel's layout)
     uint4 *sD;        // [NSTAGE][NX] phase words
     float2 *sW;       // [NX/2] exp(+2 pi i m / (nx/2))
     float2 *sT;       // per-warp transpose regions
@@ -213,7 +213,7 @@ struct PropSmem {
     {
         full = reinterpret_cast<uint64_t *>(raw);
         empty = full + NSTAGE;
-        sQ = reinterpret_cast<float2 *>(raw + 128);
+        sQ = reinterpret_cast<float4 *>(raw + 128);
         sD = reinterpret_cast<uint4 *>(sQ + NSTAGE * NAP * NX);
         sW = reinterpret_cast<float2 *>(sD + NSTAGE * NX);
         sT = sW + NX / 2;
@@ -239,7 +239,8 @@ struct PropSmem {
 
 // The bin loop of one row tile: Eq. 2 phasors, the inverse lateral DFT and
 // the per-pixel sums over bins [b_begin, b_begin + nb) of one frame. Qf is the
-// frame's [n_bins][NAP][NX] spectra; row jj (clamped into the frame) at depth
+// frame's [n_bins][NAP][8][2][NX/16] paired spectra (lateral_kernel's layout,
+// 2 NAP NX complex values per bin); row jj (clamped into the frame) at depth
 // zj. `seq` counts the bins this CTA staged before this call: the staging
 // ring's stage and phase continue from it. With FIELDS, lanes of valid rows
 // also write bin b's fields to fields_row + b * bin_stride. Returns false if a
@@ -260,10 +261,9 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
     float2 *myT = sm.sT + (size_t)warp * (NAP * RPW * 2 * RS);
     const float2 *sW = sm.sW;
 
-    // Radix-2 DIF split folded into the phase: lanes of half g take
-    // x_g[n'] = exp(2 pi i g n'/nx) (P[n'] + (-1)^g P[n'+H]).
-    const unsigned g_unit = g ? (1u << (32 - S::LOG2NX)) : 0u;
-    const unsigned g_half = g ? 0x80000000u : 0u;
+    // Radix-2 DIF split: lanes of half g take
+    // x_g[n'] = exp(2 pi i g n'/nx) (P[n'] + (-1)^g P[n'+H]); the twiddle and
+    // the sign are in the paired spectra, so both halves use the same phasors.
     const unsigned jw = (unsigned)jj;
 
     // Staging pipeline: thread 0 keeps NSTAGE-1 bins in flight with TMA bulk
@@ -271,7 +271,7 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
     // barrier. Every warp arrives on the stage's `empty` barrier once it has
     // finished with the stage. Warps can therefore run up to NSTAGE-1 bins
     // apart, with no CTA-wide barrier per bin.
-    constexpr unsigned BYTES_Q = NAP * NX * sizeof(float2), BYTES_D = NX * sizeof(uint4);
+    constexpr unsigned BYTES_Q = NAP * NX * sizeof(float4), BYTES_D = NX * sizeof(uint4);
     int issued = 0;    // producer (thread 0): bins whose copies have been issued
     bool ok = true;    // false once a bounded wait expired
     auto issue_next = [&]() -> bool {
@@ -280,7 +280,7 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
         if (n >= NSTAGE && !mbar_wait(&sm.empty[st], ((n / NSTAGE) - 1) & 1)) return false;
         const int b = b_begin + issued;
         mbar_expect_tx(&sm.full[st], BYTES_Q + BYTES_D);
-        bulk_g2s(sm.sQ + st * NAP * NX, Qf + (size_t)b * NAP * NX, BYTES_Q, &sm.full[st]);
+        bulk_g2s(sm.sQ + st * NAP * NX, Qf + (size_t)b * 2 * NAP * NX, BYTES_Q, &sm.full[st]);
         bulk_g2s(sm.sD + st * NX, phase + (size_t)b * NX, BYTES_D, &sm.full[st]);
         ++issued;
         return true;
@@ -299,27 +299,29 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
             break;
         }
         const int b = b_begin + i;
-        const float2 *cQ = sm.sQ + stage * NAP * NX;
+        const float4 *cQ = sm.sQ + stage * NAP * NX;
         const uint4 *cD = sm.sD + stage * NX;
         const bool evan = bin_evan[b] != 0;
 
-        // Eq. 2 phasors of this lane's 16 lateral bins at depth z_j. The row's
-        // phase word is anchor + j*step_hi + hi32(j*step_lo); dropping the
-        // carry out of the low word costs at most 2^-32 turn.
+        // Eq. 2 phasors at depth z_j: this lane computes those of the lateral
+        // bins u = g H + L2 n1 + n2 (ph0) and takes the other half's from its
+        // partner lane, lane ^ L2 (ph1). The row's phase word is
+        // anchor + j*step_hi + hi32(j*step_lo); dropping the carry out of the
+        // low word costs at most 2^-32 turn.
         float2 ph0[8], ph1[8];
 #pragma unroll
         for (int n1 = 0; n1 < 8; ++n1) {
-            const int u0 = L2 * n1 + n2;
-            const uint4 d0 = cD[u0], d1 = cD[u0 + H];
-            const unsigned off = g_unit * (unsigned)u0;
-            ph0[n1] = phase_cis(d0.x + jw * d0.y + __umulhi(jw, d0.z) + off);
-            ph1[n1] = phase_cis(d1.x + jw * d1.y + __umulhi(jw, d1.z) + off + g_half);
+            const uint4 d = cD[g * H + L2 * n1 + n2];
+            ph0[n1] = phase_cis(d.x + jw * d.y + __umulhi(jw, d.z));
             if (evan) {
-                const float a0 = exp2f(__uint_as_float(d0.w) * zj), a1 = exp2f(__uint_as_float(d1.w) * zj);
-                ph0[n1] = make_float2(ph0[n1].x * a0, ph0[n1].y * a0);
-                ph1[n1] = make_float2(ph1[n1].x * a1, ph1[n1].y * a1);
+                const float a = exp2f(__uint_as_float(d.w) * zj);
+                ph0[n1] = make_float2(ph0[n1].x * a, ph0[n1].y * a);
             }
         }
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1)
+            ph1[n1] = make_float2(__shfl_xor_sync(0xffffffffu, ph0[n1].x, L2),
+                                  __shfl_xor_sync(0xffffffffu, ph0[n1].y, L2));
 
         // first factor: 8-point DFT over n1, twiddle, into the transpose region.
         // The lane's twiddles are loaded once for all apertures (the compiler
@@ -332,10 +334,10 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
             float2 x[8];
 #pragma unroll
             for (int n1 = 0; n1 < 8; ++n1) {
-                const int u0 = L2 * n1 + n2;
-                // Q0 ph0 + Q1 ph1 as two chains of one multiply and three FMAs: 8 FMA-pipe
+                // a ph0 + c ph1 as two chains of one multiply and three FMAs: 8 FMA-pipe
                 // instructions where two complex products and a packed add take 9
-                const float2 a = cQ[q * NX + u0], c = cQ[q * NX + u0 + H], p = ph0[n1], r = ph1[n1];
+                const float4 qq = cQ[((q * 8 + n1) * 2 + g) * L2 + n2];
+                const float2 a = make_float2(qq.x, qq.y), c = make_float2(qq.z, qq.w), p = ph0[n1], r = ph1[n1];
                 x[n1] = make_float2(fmaf(a.x, p.x, fmaf(-a.y, p.y, fmaf(c.x, r.x, -c.y * r.y))),
                                     fmaf(a.x, p.y, fmaf(a.y, p.x, fmaf(c.x, r.y, c.y * r.x))));
             }
@@ -444,7 +446,7 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[o][a] = 0.0f;
     const bool ok = prop_bins<NAP, NX, FIELDS>(
-        sm, Q + (size_t)f * n_bins * NAP * NX, phase, bin_evan, b_begin, b_end - b_begin, jj,
+        sm, Q + (size_t)f * n_bins * 2 * NAP * NX, phase, bin_evan, b_begin, b_end - b_begin, jj,
         z0f + (float)jj * dzf, 0u, acc, FIELDS ? fields + ((size_t)f * n_bins * nz + j) * NX : nullptr, row_ok,
         (size_t)nz * NX);
     if (!ok && lane == 0) atomicOr(out.status, 1);

@@ -113,7 +113,7 @@ size_t carve(pam_plan_s &p, int n_split, unsigned char *base)
     p.t.live = static_cast<float *>(take(nb * nx * sizeof(float)));
     p.t.bin_evan = static_cast<int *>(take(nb * sizeof(int)));
     p.w.S = static_cast<float2 *>(take(nb * ne * sizeof(float2)));
-    p.w.Q = static_cast<float2 *>(take(nb * 3 * nx * sizeof(float2)));
+    p.w.Q = static_cast<float2 *>(take(nb * pam::q_per_bin(3, (int)nx) * sizeof(float2)));
     // split reductions up to the cluster size stay on chip; larger ones need partials
     const size_t units = pam::prop_uses_cluster(n_split) ? 0 : (size_t)n_split;
     p.w.part = static_cast<float *>(take(units * 6 * npix * sizeof(float)));
