@@ -282,7 +282,7 @@ pam_status alloc_plan(pam_plan_s *p)
     if (pam::fault_injected("alloc")) return fail(PAM_ERR_OOM, "injected allocation failure (PAM_FAULT=alloc)");
     int rows = pam::prop_rows_per_cta(p->nx);
     int row_tiles = (p->nz + rows - 1) / rows;
-    size_t target = 2 * (size_t)p->num_sms;
+    size_t target = (size_t)pam::prop_ctas_per_sm() * p->num_sms;
     size_t split_units = (target + row_tiles - 1) / row_tiles;
     p->w.part_units = std::max(F, split_units);
     PAM_TRY(dalloc(&p->w.part, p->w.part_units * (size_t)pam::n_acc(p->n_apod) * npix));

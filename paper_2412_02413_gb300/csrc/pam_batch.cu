@@ -427,7 +427,7 @@ pam_status pam_batch_create(const pam_plan_desc *common, const pam_frame_desc *f
     for (int f = 0; f < n_frames; ++f)
         for (int t = 0; t * rpc < b->nz[f]; ++t) items.push_back(make_int2(f, t));
     b->n_items = (int)items.size();
-    b->grid = std::min(b->n_items, 2 * p.num_sms);
+    b->grid = std::min(b->n_items, pam::prop_ctas_per_sm() * p.num_sms);
     const size_t FB = (size_t)n_frames * b->n_bins;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = dalloc(&b->bins, FB);

@@ -18,6 +18,7 @@ constexpr int kMaxGemmK = 384;     // GEMM depth of the tensor-core form: 16 per
 
 // Rows of the depth grid handled by one CTA of the fused propagate-and-correlate
 // kernel for a lateral length nx (8 warps; 2*nx/16 lanes per row).
+int prop_ctas_per_sm();   // resident CTAs per SM of the fused kernels (their register limit)
 int prop_rows_per_cta(int nx);
 
 // Bin splits up to this size reduce inside a thread-block cluster (portable limit).

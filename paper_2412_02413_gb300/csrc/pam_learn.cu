@@ -1156,7 +1156,7 @@ pam_status pam_learn_example(pam_learn_t l, const float *rf, int n_frames, void 
         out.fmax = l->fmax_x;
         out.status = p.w.status;
         const int n_items = n_frames * l->tiles;
-        LTRY(pam::launch_prop_batch(l->W, 3, std::min(2 * l->n_sms, n_items), l->frames, l->items_all, n_items,
+        LTRY(pam::launch_prop_batch(l->W, 3, std::min(pam::prop_ctas_per_sm() * l->n_sms, n_items), l->frames, l->items_all, n_items,
                                     l->counters + 1, out, st));
         l->kernels += 3;
     }
@@ -1259,7 +1259,7 @@ pam_status pam_learn_tax(pam_learn_t l, const float *rf, int n_frames, float *im
         out.e_tmp = p.w.e_tmp;
         out.fmax = l->fmax_g;
         out.status = p.w.status;
-        LTRY(pam::launch_prop_batch(l->W, 3, std::min(2 * l->n_sms, n), l->frames, l->items_gate, n, l->counters,
+        LTRY(pam::launch_prop_batch(l->W, 3, std::min(pam::prop_ctas_per_sm() * l->n_sms, n), l->frames, l->items_gate, n, l->counters,
                                     out, st));
         float *gerr = gate_err ? gate_err + f0 : l->gate_err;
         int *gpass = gate_pass ? gate_pass + f0 : l->gate_pass;
@@ -1269,7 +1269,7 @@ pam_status pam_learn_tax(pam_learn_t l, const float *rf, int n_frames, float *im
         LTRY(cudaGetLastError());
         // fallback: the plain method on every row tile of the frames that missed the gate
         out.fmax = l->fmax_x;
-        LTRY(pam::launch_prop_batch(l->W, 3, 2 * l->n_sms, l->frames, l->items_fb, n * l->tiles, l->counters + 1, out,
+        LTRY(pam::launch_prop_batch(l->W, 3, pam::prop_ctas_per_sm() * l->n_sms, l->frames, l->items_fb, n * l->tiles, l->counters + 1, out,
                                     st, l->counters + 2));
         pam::learn_finalize_kernel<<<g, pam::EPI_THREADS, 0, st>>>(
             gpass, l->rho, l->rmax, l->E, p.w.rho_tmp, p.w.e_tmp, l->fmax_x, (int)l->npix, image + (size_t)f0 * l->npix,

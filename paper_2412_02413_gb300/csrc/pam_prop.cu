@@ -105,7 +105,8 @@ __device__ __forceinline__ float2 phase_cis(unsigned w)
 
 using namespace ptx;
 
-constexpr int NSTAGE = 4;  // bins in flight per CTA
+constexpr int NSTAGE = 2;       // bins in flight per CTA
+constexpr int PROP_CTAS = 3;    // resident CTAs per SM: 24 warps (80 registers, 74 KB of shared memory each at nx = 128)
 
 template <int NX> struct Shape {
     static constexpr int H = NX / 2;               // half length
@@ -114,13 +115,33 @@ template <int NX> struct Shape {
     static constexpr int RPW = 32 / LPR;           // rows per warp
     static constexpr int RPC = PROP_WARPS * RPW;   // rows per CTA
     static constexpr int KPL = 8 / L2;             // second-stage DFTs per lane
-    static constexpr int TS = L2 + 1;              // padded transpose row (float2)
-    static constexpr int RS = 8 * TS;              // transpose region per (aperture, row, half)
-    static constexpr int LOG2NX = NX == 16 ? 4 : NX == 32 ? 5 : NX == 64 ? 6 : 7;
+    // Transpose regions per (aperture, row, half): 8 rows k1 x L2 columns. At
+    // nx = 128 the rows are unpadded and swizzled (see tpos); below it each
+    // row carries one float2 of padding.
+    static constexpr bool SWZ = false;
+    static constexpr int TS = SWZ ? L2 : L2 + 1;   // transpose row (float2)
+    static constexpr int RS = 8 * TS;              // transpose region (float2)
+    // Position of element (k1, col) in region rho = 2 r + g of a warp. Swizzled:
+    // row k1 goes to row (k1 + rho) mod 8 and column col to col ^ k1, so that
+    // the 32 lanes' stores (one k1, 8 columns per region) and loads (one
+    // column, 8 rows per region) each touch every bank exactly twice, the
+    // minimum for 256 bytes, with no padding.
+    static __device__ __forceinline__ int tpos(int k1, int col, int rho)
+    {
+        if constexpr (SWZ) return ((k1 + rho) & 7) * TS + (col ^ k1);
+        else return k1 * TS + col;
+    }
     static_assert(NX == 16 || NX == 32 || NX == 64 || NX == 128, "built lateral lengths");
 };
 
 template <int NAP> struct Acc { static constexpr int N = NAP == 1 ? 1 : (NAP == 2 ? 3 : 6); };
+
+// Tensor-memory columns of one CTA: the two warps of each lane quadrant (w and
+// w + 4) hold 8 pixels x NACC sums per lane each, at columns [a][o].
+template <int NAP> constexpr unsigned tmem_cols()
+{
+    return Acc<NAP>::N == 6 ? 128u : (Acc<NAP>::N == 3 ? 64u : 32u);
+}
 
 template <int NAP, int NX>
 constexpr size_t prop_smem_bytes()
@@ -200,11 +221,110 @@ __device__ __forceinline__ void block_max_to(float v, unsigned *dst, float *scra
     }
 }
 
+// The per-pixel sums over the bins (Eq. 3, Eq. 4 + Appendix A) live in tensor
+// memory, not in registers: 48 accumulators per thread would hold the fused
+// kernel to 2 CTAs per SM. A thread's 8 NACC sums are the columns
+// tcol + a * 8 + o (sum a, pixel o) of its own lane.
+__device__ __forceinline__ unsigned acc_tcol(unsigned tbase, int warp, int nacc)
+{
+    return tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)((warp >> 2) * 8 * nacc);
+}
+
+template <int NAP>
+__device__ __forceinline__ void acc_zero(unsigned tcol)
+{
+    const float z[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if constexpr (NAP == 1) {
+        tmem_st8(tcol, z);
+    } else if constexpr (NAP == 2) {
+        tmem_st16(tcol, z);
+        tmem_st8(tcol + 16, z);
+    } else {
+        tmem_st16(tcol, z);
+        tmem_st16(tcol + 16, z);
+        tmem_st16(tcol + 32, z);
+    }
+    tmem_wait_st();
+}
+
+// |a|^2 and Re(conj(a) b), accumulated into s
+__device__ __forceinline__ float add_norm(float s, float2 a) { return fmaf(a.x, a.x, fmaf(a.y, a.y, s)); }
+__device__ __forceinline__ float add_dot(float s, float2 a, float2 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, s)); }
+
+// Adds one bin's fields p[q][o] to the sums: A_qq += |p_q|^2, C_qr += Re conj(p_q) p_r.
+template <int NAP>
+__device__ __forceinline__ void acc_update(unsigned tcol, const float2 (&p)[NAP][8])
+{
+    tmem_wait_st();   // the previous bin's stores have landed
+    if constexpr (NAP == 1) {
+        float v[8];
+        tmem_ld8(tcol, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int o = 0; o < 8; ++o) v[o] = add_norm(v[o], p[0][o]);
+        tmem_st8(tcol, v);
+    } else {
+        float v[16];
+        tmem_ld16(tcol, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            v[o] = add_norm(v[o], p[0][o]);
+            v[8 + o] = add_norm(v[8 + o], p[1][o]);
+        }
+        tmem_st16(tcol, v);
+        if constexpr (NAP == 2) {
+            float w[8];
+            tmem_ld8(tcol + 16, w);
+            tmem_wait_ld();
+#pragma unroll
+            for (int o = 0; o < 8; ++o) w[o] = add_dot(w[o], p[0][o], p[1][o]);
+            tmem_st8(tcol + 16, w);
+        } else {
+            float w[16];
+            tmem_ld16(tcol + 16, w);
+            tmem_wait_ld();
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                w[o] = add_norm(w[o], p[2][o]);
+                w[8 + o] = add_dot(w[8 + o], p[0][o], p[1][o]);
+            }
+            tmem_st16(tcol + 16, w);
+            float y[16];
+            tmem_ld16(tcol + 32, y);
+            tmem_wait_ld();
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                y[o] = add_dot(y[o], p[1][o], p[2][o]);
+                y[8 + o] = add_dot(y[8 + o], p[2][o], p[0][o]);
+            }
+            tmem_st16(tcol + 32, y);
+        }
+    }
+}
+
+// The sums of the thread's 8 pixels, acc[o][a], back in registers.
+template <int NAP>
+__device__ __forceinline__ void acc_read(unsigned tcol, float (&acc)[8][Acc<NAP>::N])
+{
+    constexpr int NACC = Acc<NAP>::N;
+    tmem_wait_st();
+    float v[8 * NACC];
+#pragma unroll
+    for (int c = 0; c < NACC; ++c) tmem_ld8(tcol + 8 * c, v + 8 * c);
+    tmem_wait_ld();
+#pragma unroll
+    for (int o = 0; o < 8; ++o)
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[o][a] = v[a * 8 + o];
+}
+
 // Shared-memory regions of the fused kernel (layout of prop_smem_bytes).
 template <int NAP, int NX>
 struct PropSmem {
     uint64_t *full;   // [NSTAGE] data of a stage has landed
     uint64_t *empty;  // [NSTAGE] all warps are done with a stage
+    unsigned *tslot;  // tensor-memory base address of the CTA's sums
     float4 *sQ;       // [NSTAGE][NAP][8][2][NX/16] paired spectra (lateral_kernel's layout)
     uint4 *sD;        // [NSTAGE][NX] phase words
     float2 *sW;       // [NX/2] exp(+2 pi i m / (nx/2))
@@ -213,14 +333,19 @@ struct PropSmem {
     {
         full = reinterpret_cast<uint64_t *>(raw);
         empty = full + NSTAGE;
+        tslot = reinterpret_cast<unsigned *>(raw + 120);
         sQ = reinterpret_cast<float4 *>(raw + 128);
         sD = reinterpret_cast<uint4 *>(sQ + NSTAGE * NAP * NX);
         sW = reinterpret_cast<float2 *>(sD + NSTAGE * NX);
         sT = sW + NX / 2;
     }
-    // second-factor twiddles and the staging barriers; every thread calls this once
-    __device__ void init() const
+    // second-factor twiddles, the staging barriers and the tensor memory of
+    // the sums (warp 0 allocates `tcols` columns); every thread calls this
+    // once and gets the CTA's tensor-memory base address
+    __device__ unsigned init(unsigned tcols) const
     {
+        static_assert(2 * NSTAGE * sizeof(uint64_t) <= 120, "barriers overlap the tensor-memory slot");
+        if (threadIdx.x < 32) tmem_alloc(tslot, tcols);
         for (int m = threadIdx.x; m < NX / 2; m += PROP_THREADS) {
             float s, c;
             sincospif(2.0f * (float)m / (float)(NX / 2), &s, &c);
@@ -233,7 +358,18 @@ struct PropSmem {
             }
             mbar_fence_init();
         }
+        tc_fence_before();
         __syncthreads();
+        tc_fence_after();
+        return *tslot;
+    }
+    // every thread calls this once after its last tensor-memory access
+    __device__ void release(unsigned tbase, unsigned tcols) const
+    {
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x < 32) tmem_dealloc(tbase, tcols);
     }
 };
 
@@ -242,19 +378,19 @@ struct PropSmem {
 // frame's [n_bins][NAP][8][2][NX/16] paired spectra (lateral_kernel's layout,
 // 2 NAP NX complex values per bin); row jj (clamped into the frame) at depth
 // zj. `seq` counts the bins this CTA staged before this call: the staging
-// ring's stage and phase continue from it. With FIELDS, lanes of valid rows
+// ring's stage and phase continue from it. The sums accumulate in the
+// thread's tensor-memory columns from tcol. With FIELDS, lanes of valid rows
 // also write bin b's fields to fields_row + b * bin_stride. Returns false if a
 // bounded wait expired; the copies still in flight have landed by then.
 template <int NAP, int NX, bool FIELDS>
 __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const float2 *__restrict__ Qf,
                                           const uint4 *__restrict__ phase, const int *__restrict__ bin_evan,
-                                          int b_begin, int nb, int jj, float zj, unsigned seq,
-                                          float (&acc)[8][Acc<NAP>::N], float2 *__restrict__ fields_row,
-                                          bool row_ok, size_t bin_stride)
+                                          int b_begin, int nb, int jj, float zj, unsigned seq, unsigned tcol,
+                                          float2 *__restrict__ fields_row, bool row_ok, size_t bin_stride)
 {
     using S = Shape<NX>;
     constexpr int H = S::H, L2 = S::L2, LPR = S::LPR, RPW = S::RPW, KPL = S::KPL;
-    constexpr int TS = S::TS, RS = S::RS;
+    constexpr int RS = S::RS;
     constexpr int NOUT = KPL * L2;  // 8 pixels per lane
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
@@ -345,7 +481,7 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
             float2 *reg = myT + ((q * RPW + r) * 2 + g) * RS;
 #pragma unroll
             for (int k1 = 0; k1 < 8; ++k1)
-                reg[k1 * TS + n2] = k1 ? cmul(x[k1], twk[k1]) : x[k1];
+                reg[S::tpos(k1, n2, r * 2 + g)] = k1 ? cmul(x[k1], twk[k1]) : x[k1];
         }
         __syncwarp();
 
@@ -359,7 +495,7 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
                 const int k1 = n2 * KPL + s;
                 float2 v[L2];
 #pragma unroll
-                for (int t = 0; t < L2; ++t) v[t] = reg[k1 * TS + t];
+                for (int t = 0; t < L2; ++t) v[t] = reg[S::tpos(k1, t, r * 2 + g)];
                 IDft<L2>::run(v);
 #pragma unroll
                 for (int k2 = 0; k2 < L2; ++k2) p[q][s * L2 + k2] = v[k2];
@@ -367,24 +503,7 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
         }
 
         // per-pixel sums over the bins
-#pragma unroll
-        for (int o = 0; o < NOUT; ++o) {
-            const float2 a = p[0][o];
-            acc[o][0] = fmaf(a.x, a.x, fmaf(a.y, a.y, acc[o][0]));
-            if constexpr (NAP >= 2) {
-                const float2 bb = p[1][o];
-                acc[o][1] = fmaf(bb.x, bb.x, fmaf(bb.y, bb.y, acc[o][1]));
-                if constexpr (NAP == 2) {
-                    acc[o][2] = fmaf(a.x, bb.x, fmaf(a.y, bb.y, acc[o][2]));
-                } else {
-                    const float2 cc = p[2][o];
-                    acc[o][2] = fmaf(cc.x, cc.x, fmaf(cc.y, cc.y, acc[o][2]));
-                    acc[o][3] = fmaf(a.x, bb.x, fmaf(a.y, bb.y, acc[o][3]));
-                    acc[o][4] = fmaf(bb.x, cc.x, fmaf(bb.y, cc.y, acc[o][4]));
-                    acc[o][5] = fmaf(cc.x, a.x, fmaf(cc.y, a.y, acc[o][5]));
-                }
-            }
-        }
+        acc_update<NAP>(tcol, p);
         if constexpr (FIELDS) {
             if (row_ok) {  // fields of bin b
                 float2 *dst = fields_row + (size_t)b * bin_stride;
@@ -415,7 +534,7 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
 // epilogue themselves. Otherwise each CTA writes its partial sums to `part`
 // for epi_reduce_kernel.
 template <int NAP, int NX, bool FIELDS, bool CLUSTER>
-__global__ void __launch_bounds__(PROP_THREADS, 2)
+__global__ void __launch_bounds__(PROP_THREADS, PROP_CTAS)
 prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
                  const int *__restrict__ bin_evan, int n_bins, int nz,
                  float z0f, float dzf, int n_split, float *__restrict__ part, float2 *__restrict__ fields,
@@ -439,18 +558,17 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
     const int b_begin = (int)(((long long)n_bins * split) / n_split);
     const int b_end = (int)(((long long)n_bins * (split + 1)) / n_split);
 
-    sm.init();
-    float acc[NOUT][NACC];
-#pragma unroll
-    for (int o = 0; o < NOUT; ++o)
-#pragma unroll
-        for (int a = 0; a < NACC; ++a) acc[o][a] = 0.0f;
+    const unsigned tbase = sm.init(tmem_cols<NAP>());
+    const unsigned tcol = acc_tcol(tbase, warp, NACC);
+    acc_zero<NAP>(tcol);
     const bool ok = prop_bins<NAP, NX, FIELDS>(
         sm, Q + (size_t)f * n_bins * 2 * NAP * NX, phase, bin_evan, b_begin, b_end - b_begin, jj,
-        z0f + (float)jj * dzf, 0u, acc, FIELDS ? fields + ((size_t)f * n_bins * nz + j) * NX : nullptr, row_ok,
+        z0f + (float)jj * dzf, 0u, tcol, FIELDS ? fields + ((size_t)f * n_bins * nz + j) * NX : nullptr, row_ok,
         (size_t)nz * NX);
     if (!ok && lane == 0) atomicOr(out.status, 1);
     const bool aborted = __syncthreads_or(!ok) != 0;
+    float acc[NOUT][NACC];
+    acc_read<NAP>(tcol, acc);
 
     if constexpr (CLUSTER) {
         namespace cg = cooperative_groups;
@@ -502,6 +620,7 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
             }
         }
     }
+    sm.release(tbase, tmem_cols<NAP>());
 }
 
 // --------------------------------------------------------- epilogue ----
@@ -571,7 +690,7 @@ epi_normalize_kernel(const float4 *__restrict__ rho_tmp, const float4 *__restric
 // its per-pixel epilogue follows directly from the registers. The staging
 // ring's position carries over from item to item.
 template <int NAP, int NX>
-__global__ void __launch_bounds__(PROP_THREADS, 2)
+__global__ void __launch_bounds__(PROP_THREADS, PROP_CTAS)
 prop_batch_kernel(const BatchFrame *__restrict__ frames, const int2 *__restrict__ items, int n_items,
                   const int *__restrict__ n_items_dev, int *__restrict__ counter, EpiOut out)
 {
@@ -586,7 +705,8 @@ prop_batch_kernel(const BatchFrame *__restrict__ frames, const int2 *__restrict_
     __shared__ float wmax[PROP_THREADS / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
-    sm.init();
+    const unsigned tbase = sm.init(tmem_cols<NAP>());
+    const unsigned tcol = acc_tcol(tbase, warp, NACC);
     unsigned seq = 0;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -599,16 +719,14 @@ prop_batch_kernel(const BatchFrame *__restrict__ frames, const int2 *__restrict_
         const int j = w.y * RPC + warp * RPW + r;
         const bool row_ok = j < fr.nz;
         const int jj = row_ok ? j : fr.nz - 1;
-        float acc[NOUT][NACC];
-#pragma unroll
-        for (int o = 0; o < NOUT; ++o)
-#pragma unroll
-            for (int a = 0; a < NACC; ++a) acc[o][a] = 0.0f;
+        acc_zero<NAP>(tcol);
         const bool ok = prop_bins<NAP, NX, false>(sm, fr.Q, fr.phase, fr.bin_evan, 0, fr.n_bins, jj,
-                                                  fr.z0f + (float)jj * fr.dzf, seq, acc, nullptr, row_ok, 0);
+                                                  fr.z0f + (float)jj * fr.dzf, seq, tcol, nullptr, row_ok, 0);
         seq += (unsigned)fr.n_bins;
         if (!ok && lane == 0) atomicOr(out.status, 1);
         if (__syncthreads_or(!ok)) break;
+        float acc[NOUT][NACC];
+        acc_read<NAP>(tcol, acc);
         float rmax = 0.0f;
         if (row_ok) {
 #pragma unroll
@@ -620,6 +738,7 @@ prop_batch_kernel(const BatchFrame *__restrict__ frames, const int2 *__restrict_
         }
         block_max_to(rmax, out.fmax + w.x, wmax, PROP_THREADS);
     }
+    sm.release(tbase, tmem_cols<NAP>());
 }
 
 // Per-frame rho_n and image for a batch packed by per-frame pixel offsets.
@@ -685,11 +804,21 @@ cudaError_t launch_prop_nx(const pam_plan_s &p, int n_frames, int napq, int n_sp
                                       : launch_prop_nc<NX, false>(p, n_frames, napq, n_split, fields, out, st);
 }
 
+// Dynamic shared memory of a fused kernel, and the largest shared-memory
+// carveout, so that PROP_CTAS CTAs fit on an SM.
+template <class K>
+cudaError_t set_smem_of(K kernel, size_t bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 template <int NAP, int NX, bool FIELDS, bool CLUSTER>
 cudaError_t set_smem()
 {
-    return cudaFuncSetAttribute(prop_corr_kernel<NAP, NX, FIELDS, CLUSTER>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)prop_smem_bytes<NAP, NX>());
+    return set_smem_of(prop_corr_kernel<NAP, NX, FIELDS, CLUSTER>, prop_smem_bytes<NAP, NX>());
 }
 
 template <int NX, bool CLUSTER>
@@ -707,12 +836,8 @@ cudaError_t prepare_nx()
 {
     cudaError_t e = prepare_nc<NX, true>();
     if (e == cudaSuccess) e = prepare_nc<NX, false>();
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(prop_batch_kernel<2, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)prop_smem_bytes<2, NX>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(prop_batch_kernel<3, NX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)prop_smem_bytes<3, NX>());
+    if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<2, NX>, prop_smem_bytes<2, NX>());
+    if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<3, NX>, prop_smem_bytes<3, NX>());
     return e;
 }
 
@@ -763,6 +888,8 @@ cudaError_t launch_expire_wait(int *status, cudaStream_t st)
 
 int prop_rows_per_cta(int nx) { return PROP_WARPS * (32 / (nx / 8)); }
 
+int prop_ctas_per_sm() { return PROP_CTAS; }
+
 bool prop_uses_cluster(int n_split) { return n_split <= kMaxClusterSplit; }
 
 int choose_split(const pam_plan_s &p, int n_frames)
@@ -773,12 +900,12 @@ int choose_split(const pam_plan_s &p, int n_frames)
     if (p.split_override > 0) {
         ns = p.split_override;
     } else {
-        // About two CTAs per SM (the register limit) over the whole grid. The
+        // About PROP_CTAS CTAs per SM (the register limit) over the whole grid. The
         // cluster reduction is used when this split is small enough anyway:
         // capping a larger split at the cluster size loses more to load
         // imbalance than the partial sums cost (128 x 512 frame: 9 -> 8 splits
         // measured 135 us against 108 + 11 us).
-        const long long target = 2LL * p.num_sms;
+        const long long target = (long long)PROP_CTAS * p.num_sms;
         ns = target / (row_tiles * n_frames);
     }
     if (ns < 1) ns = 1;

@@ -66,6 +66,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
     return true;
 }
 
+// As mbar_wait, but each poll lets the hardware suspend the thread until the
+// phase completes (or about 10 us pass), so a waiting warp issues no
+// instructions in the meantime. Bounded at about one second like mbar_wait.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, unsigned parity)
+{
+    if (mbar_try_wait_sleep(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait_sleep(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+
 // ---- bulk copies ----
 // One bulk global -> shared copy that completes `bytes` of transaction on `bar`
 // (both addresses 16-byte aligned, bytes a multiple of 16).
@@ -124,6 +136,48 @@ __device__ __forceinline__ void umma_commit_elect(uint64_t *bar)
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
+// Tensor-memory allocation by one whole warp: `ncols` (a power of 2, >= 32)
+// columns of all 128 lanes; the base address is written to shared memory at
+// `slot`. The CTA then gives up its right to allocate again, so that other
+// CTAs on the SM are not held back. The same warp frees the columns with
+// tmem_dealloc before the CTA exits.
+__device__ __forceinline__ void tmem_alloc(unsigned *slot, unsigned ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Tensor-memory stores of the warp's 32 lanes (32x32b shape): 8 or 16
+// consecutive columns per lane. tmem_wait_st() orders them before later
+// loads of the same columns.
+__device__ __forceinline__ void tmem_st8(unsigned taddr, const float *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st16(unsigned taddr, const float *v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                 "%15,%16};\n" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+                 "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                 "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                 "r"(__float_as_uint(v[15]))
+                 : "memory");
+}
 
 // Tensor-memory loads of the warp's 32 lanes (32x32b shape): 8, 16 or 32
 // consecutive columns per lane. tmem_wait_ld() must follow before use.
