@@ -285,7 +285,12 @@ pam_status alloc_plan(pam_plan_s *p)
     size_t target = (size_t)pam::prop_ctas_per_sm() * p->num_sms;
     size_t split_units = (target + row_tiles - 1) / row_tiles;
     p->w.part_units = std::max(F, split_units);
-    PAM_TRY(dalloc(&p->w.part, p->w.part_units * (size_t)pam::n_acc(p->n_apod) * npix));
+    // segment sums of the even division (batches of fewer than `target` row tiles)
+    const size_t seg_frames = std::min(F, (target + row_tiles - 1) / row_tiles);
+    const size_t part_floats = std::max(p->w.part_units * (size_t)pam::n_acc(p->n_apod) * npix,
+                                        pam::prop_seg_part_floats(*p, (int)seg_frames));
+    PAM_TRY(dalloc(&p->w.part, part_floats));
+    p->seg_ok = true;
     PAM_TRY(dalloc(&p->w.rho_tmp, F * npix));
     PAM_TRY(dalloc(&p->w.e_tmp, F * npix));
     PAM_TRY(dalloc(&p->w.fmax, F));
@@ -411,7 +416,7 @@ pam_status run_xcorr(pam_plan_t p, const float *rf, int n_frames, float *image, 
         if ((e = prof_end(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
         e = pam::launch_epilogue(*p, Fc, p->n_apod, ns, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "epilogue launch");
-        p->kernels += 3 + pam::epilogue_kernels(p->n_apod, ns);
+        p->kernels += 3 + pam::epilogue_kernels(*p, p->n_apod, ns);
         if (crop) {
             e = pam::launch_pad_crop(p->w.pad_rho, p->w.pad_as, p->w.pad_pairs, npairs, Fc, p->nz, p->nx, p->nx_out,
                                      c_img, c_rho, c_pairs, c_as, st);
@@ -529,9 +534,9 @@ pam_status pam_as_backprop(pam_plan_t p, const float *rf, int n_frames, int apod
         e = pam::launch_prop(*p, Fc, 1, ns, fl, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "propagate launch");
         if ((e = prof_end(p, st)) != cudaSuccess) return cuda_fail(e, "profile event");
-        e = pam::launch_epilogue(*p, Fc, 1, ns, out, st);
+        e = pam::launch_epilogue(*p, Fc, 1, ns, out, st, false, fl != nullptr);
         if (e != cudaSuccess) return cuda_fail(e, "epilogue launch");
-        p->kernels += 3 + pam::epilogue_kernels(1, ns);
+        p->kernels += 3 + pam::epilogue_kernels(*p, 1, ns, fl != nullptr);
         if (crop) {   // element columns of the padded energy map
             const size_t w_out = (size_t)p->nx_out * sizeof(float), w_in = (size_t)p->nx * sizeof(float);
             e = cudaMemcpy2DAsync(energy + (size_t)f0 * npix, w_out, p->w.pad_img, w_in, w_out, (size_t)Fc * p->nz,

@@ -118,6 +118,7 @@ struct pam_plan_s {
     size_t prof_used = 0;              // events recorded since the last read
     long long kernels = 0;             // libpam kernel launches since the last read
     int split_override = 0;            // pam_plan_set_split (0 = automatic)
+    bool seg_ok = false;               // Workspace::part holds prop_seg_part_floats (even division of small batches)
     // tensor-core form (PAM_FORM_GEMM_*): 0 = plain FP32 path
     int form = 0;
     int K = 0;                         // GEMM depth: 16 per (aperture, 8-element block) pair
@@ -144,8 +145,15 @@ cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split
 // The rest of the epilogue: the partial reduction (no cluster) and the rho
 // normalisation (DAX / TAX).
 cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, const EpiOut &out,
-                            cudaStream_t st, bool from_partials = false);
-int epilogue_kernels(int napq, int n_split);   // kernels launch_epilogue launches
+                            cudaStream_t st, bool from_partials = false, bool fields = false);
+int epilogue_kernels(const pam_plan_s &p, int napq, int n_split, bool fields = false);   // kernels launch_epilogue launches
+// Even division of small batches (the automatic split above 1, no fields,
+// plan memory for the segment sums): one wave of prop_seg_ctas CTAs over the
+// linearized (frame, tile, bin) sequence; the segment sums need
+// prop_seg_part_floats floats of Workspace::part.
+bool prop_seg_mode(const pam_plan_s &p, int n_split, bool fields);
+int prop_seg_ctas(const pam_plan_s &p, int n_frames);
+size_t prop_seg_part_floats(const pam_plan_s &p, int n_frames);
 // Batch (pam_batch.cu): the persistent propagate-and-correlate kernel over
 // (frame, row tile) items and the per-frame normalisation.
 // n_items_dev (optional): a device int that caps n_items when the kernel starts.

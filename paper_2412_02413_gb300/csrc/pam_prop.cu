@@ -80,13 +80,14 @@ template <> struct IDft<8> {
         float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
         idft4(e0, e1, e2, e3);
         idft4(o0, o1, o2, o3);
-        // o_k *= exp(+2 pi i k / 8)
-        o1 = make_float2(r * (o1.x - o1.y), r * (o1.x + o1.y));
-        o3 = make_float2(-r * (o3.x + o3.y), r * (o3.x - o3.y));
+        // o_k *= exp(+2 pi i k / 8): (1 + i) o1 and (-1 + i) o3 here, the 1/sqrt(2) in the FMAs below
+        o1 = make_float2(o1.x - o1.y, o1.x + o1.y);
+        o3 = make_float2(-(o3.x + o3.y), o3.x - o3.y);
+        const float2 rp = make_float2(r, r), rn = make_float2(-r, -r);
         v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
-        v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+        v[1] = __ffma2_rn(rp, o1, e1); v[5] = __ffma2_rn(rn, o1, e1);
         v[2] = cadd_i(e2, o2); v[6] = csub_i(e2, o2);   // o2 times i
-        v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+        v[3] = __ffma2_rn(rp, o3, e3); v[7] = __ffma2_rn(rn, o3, e3);
     }
 };
 
@@ -105,8 +106,8 @@ __device__ __forceinline__ float2 phase_cis(unsigned w)
 
 using namespace ptx;
 
-constexpr int NSTAGE = 2;       // bins in flight per CTA
-constexpr int PROP_CTAS = 3;    // resident CTAs per SM: 24 warps (80 registers, 74 KB of shared memory each at nx = 128)
+constexpr int NSTAGE = 4;       // bins in flight per CTA
+constexpr int PROP_CTAS = 2;    // resident CTAs per SM: 16 warps (up to 128 registers each)
 
 template <int NX> struct Shape {
     static constexpr int H = NX / 2;               // half length
@@ -115,22 +116,13 @@ template <int NX> struct Shape {
     static constexpr int RPW = 32 / LPR;           // rows per warp
     static constexpr int RPC = PROP_WARPS * RPW;   // rows per CTA
     static constexpr int KPL = 8 / L2;             // second-stage DFTs per lane
-    // Transpose regions per (aperture, row, half): 8 rows k1 x L2 columns. At
-    // nx = 128 the rows are unpadded and swizzled (see tpos); below it each
-    // row carries one float2 of padding.
-    static constexpr bool SWZ = false;
-    static constexpr int TS = SWZ ? L2 : L2 + 1;   // transpose row (float2)
-    static constexpr int RS = 8 * TS;              // transpose region (float2)
-    // Position of element (k1, col) in region rho = 2 r + g of a warp. Swizzled:
-    // row k1 goes to row (k1 + rho) mod 8 and column col to col ^ k1, so that
-    // the 32 lanes' stores (one k1, 8 columns per region) and loads (one
-    // column, 8 rows per region) each touch every bank exactly twice, the
-    // minimum for 256 bytes, with no padding.
-    static __device__ __forceinline__ int tpos(int k1, int col, int rho)
-    {
-        if constexpr (SWZ) return ((k1 + rho) & 7) * TS + (col ^ k1);
-        else return k1 * TS + col;
-    }
+    // Transpose regions per (aperture, row, half): 8 rows k1 x L2 columns, each
+    // row padded by one float2 so that the stores of one k1 and the loads of
+    // one column are free of bank conflicts.
+    static constexpr bool V4 = NX == 128;          // second-stage reads as float4 pairs
+    static constexpr int TS = V4 ? L2 + 2 : L2 + 1;   // transpose row (float2)
+    static constexpr int RS = V4 ? 8 * TS + 8 : 8 * TS;   // transpose region (float2), 16 mod 32 words
+    static __device__ __forceinline__ int tpos(int k1, int col) { return k1 * TS + col; }
     static_assert(NX == 16 || NX == 32 || NX == 64 || NX == 128, "built lateral lengths");
 };
 
@@ -424,6 +416,9 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
     if (tid == 0)
         while (issued < nb && issued < NSTAGE - 1) issue_next();
 
+    float2 twk[8];     // the lane's second-factor twiddles, for every bin
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) twk[k1] = sW[(n2 * k1) & (H - 1)];
     int done = 0;      // bins this warp has finished
     for (int i = 0; i < nb; ++i) {
         if (tid == 0 && issued < nb) ok = issue_next();
@@ -445,13 +440,19 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
         // anchor + j*step_hi + hi32(j*step_lo); dropping the carry out of the
         // low word costs at most 2^-32 turn.
         float2 ph0[8], ph1[8];
+        if (evan) {
 #pragma unroll
-        for (int n1 = 0; n1 < 8; ++n1) {
-            const uint4 d = cD[g * H + L2 * n1 + n2];
-            ph0[n1] = phase_cis(d.x + jw * d.y + __umulhi(jw, d.z));
-            if (evan) {
+            for (int n1 = 0; n1 < 8; ++n1) {
+                const uint4 d = cD[g * H + L2 * n1 + n2];
+                const float2 c = phase_cis(d.x + jw * d.y + __umulhi(jw, d.z));
                 const float a = exp2f(__uint_as_float(d.w) * zj);
-                ph0[n1] = make_float2(ph0[n1].x * a, ph0[n1].y * a);
+                ph0[n1] = make_float2(c.x * a, c.y * a);
+            }
+        } else {
+#pragma unroll
+            for (int n1 = 0; n1 < 8; ++n1) {
+                const uint4 d = cD[g * H + L2 * n1 + n2];
+                ph0[n1] = phase_cis(d.x + jw * d.y + __umulhi(jw, d.z));
             }
         }
 #pragma unroll
@@ -462,9 +463,6 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
         // first factor: 8-point DFT over n1, twiddle, into the transpose region.
         // The lane's twiddles are loaded once for all apertures (the compiler
         // reloads them per aperture otherwise; measured 2% faster).
-        float2 twk[8];
-#pragma unroll
-        for (int k1 = 1; k1 < 8; ++k1) twk[k1] = sW[(n2 * k1) & (H - 1)];
 #pragma unroll
         for (int q = 0; q < NAP; ++q) {
             float2 x[8];
@@ -481,7 +479,7 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
             float2 *reg = myT + ((q * RPW + r) * 2 + g) * RS;
 #pragma unroll
             for (int k1 = 0; k1 < 8; ++k1)
-                reg[S::tpos(k1, n2, r * 2 + g)] = k1 ? cmul(x[k1], twk[k1]) : x[k1];
+                reg[S::tpos(k1, n2)] = k1 ? cmul(x[k1], twk[k1]) : x[k1];
         }
         __syncwarp();
 
@@ -494,8 +492,18 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
             for (int s = 0; s < KPL; ++s) {
                 const int k1 = n2 * KPL + s;
                 float2 v[L2];
+                if constexpr (S::V4) {
+                    const float4 *reg4 = reinterpret_cast<const float4 *>(reg + k1 * S::TS);
 #pragma unroll
-                for (int t = 0; t < L2; ++t) v[t] = reg[S::tpos(k1, t, r * 2 + g)];
+                    for (int t = 0; t < L2; t += 2) {
+                        const float4 w4 = reg4[t / 2];
+                        v[t] = make_float2(w4.x, w4.y);
+                        v[t + 1] = make_float2(w4.z, w4.w);
+                    }
+                } else {
+#pragma unroll
+                    for (int t = 0; t < L2; ++t) v[t] = reg[S::tpos(k1, t)];
+                }
                 IDft<L2>::run(v);
 #pragma unroll
                 for (int k2 = 0; k2 < L2; ++k2) p[q][s * L2 + k2] = v[k2];
@@ -623,6 +631,73 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
     sm.release(tbase, tmem_cols<NAP>());
 }
 
+// CTA holding tile-bin w of the linearized (frame, row tile, bin) sequence of
+// W tile-bins when G CTAs take equal contiguous shares [c W / G, (c+1) W / G).
+__host__ __device__ __forceinline__ int seg_cta_of(long long w, long long W, int G)
+{
+    return (int)(((w + 1) * (long long)G - 1) / W);
+}
+
+// Even division of a small batch: gridDim.x CTAs (one wave) each take an
+// equal contiguous share of the W = frames x tiles x n_bins tile-bins, in
+// (frame, tile, bin) order. A share spans the end of one tile's bins and the
+// start of the next one's; for each such segment the CTA writes its sums to
+// its own slot c + tt (tt = frame x tiles + tile) of part[slot][NACC][RPC][NX],
+// and epi_reduce_seg_kernel adds a tile's slots in CTA order. The staging
+// ring carries over from segment to segment.
+template <int NAP, int NX>
+__global__ void __launch_bounds__(PROP_THREADS, PROP_CTAS)
+prop_seg_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase, const int *__restrict__ bin_evan,
+                int n_bins, int nz, int tiles, float z0f, float dzf, long long W, float *__restrict__ part,
+                EpiOut out)
+{
+    using S = Shape<NX>;
+    constexpr int L2 = S::L2, LPR = S::LPR, RPW = S::RPW, RPC = S::RPC, KPL = S::KPL;
+    constexpr int NACC = Acc<NAP>::N;
+    constexpr int NOUT = KPL * L2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const PropSmem<NAP, NX> sm(smem_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
+    const unsigned tbase = sm.init(tmem_cols<NAP>());
+    const unsigned tcol = acc_tcol(tbase, warp, NACC);
+    const long long G = gridDim.x, c = blockIdx.x;
+    long long w = c * W / G;
+    const long long w1 = (c + 1) * W / G;
+    unsigned seq = 0;
+    while (w < w1) {
+        const long long tt = w / n_bins;
+        const int b0 = (int)(w - tt * n_bins);
+        const int nb = (int)min((long long)(n_bins - b0), w1 - w);
+        const int f = (int)(tt / tiles), tile = (int)(tt - (long long)f * tiles);
+        const int rowl = warp * RPW + r;
+        const int j = tile * RPC + rowl;
+        const bool row_ok = j < nz;
+        const int jj = row_ok ? j : nz - 1;
+        acc_zero<NAP>(tcol);
+        const bool ok = prop_bins<NAP, NX, false>(sm, Q + (size_t)f * n_bins * 2 * NAP * NX, phase, bin_evan, b0, nb,
+                                                  jj, z0f + (float)jj * dzf, seq, tcol, nullptr, row_ok, 0);
+        seq += (unsigned)nb;
+        if (!ok && lane == 0) atomicOr(out.status, 1);
+        if (__syncthreads_or(!ok)) break;
+        float acc[NOUT][NACC];
+        acc_read<NAP>(tcol, acc);
+        if (row_ok) {
+            constexpr size_t plane = (size_t)RPC * NX;
+            float *dst = part + (size_t)(c + tt) * NACC * plane + (size_t)rowl * NX;
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) {
+                const int k1 = n2 * KPL + o / L2, k2 = o % L2;
+                const int i = 2 * (k1 + 8 * k2) + g;
+#pragma unroll
+                for (int a = 0; a < NACC; ++a) dst[a * plane + i] = acc[o][a];
+            }
+        }
+        w += nb;
+    }
+    sm.release(tbase, tmem_cols<NAP>());
+}
+
 // --------------------------------------------------------- epilogue ----
 
 // Sums the per-split partials in split order (deterministic) and finishes
@@ -646,6 +721,48 @@ epi_reduce_kernel(const float4 *__restrict__ part, int n_split, int npix4, EpiOu
 #pragma unroll 4
         for (int s = 0; s < n_split; ++s) {
             const float4 v = src[s * stride];
+            a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+        }
+    }
+    sA[c][lane] = a;
+    __syncthreads();
+    float rmax = 0.0f;
+    if (c == 0 && x4 < npix4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float acc[NACC];
+#pragma unroll
+            for (int k = 0; k < NACC; ++k) acc[k] = reinterpret_cast<const float *>(&sA[k][lane])[i];
+            rmax = fmaxf(rmax, pixel_epilogue<NAP>(acc, out, f, (size_t)x4 * 4 + i));
+        }
+    }
+    if constexpr (NAP > 1) block_max_to(rmax, out.fmax + f, wmax, 32 * NACC);
+}
+
+// The segment sums of prop_seg_kernel: for each pixel, its tile's slots
+// added in CTA order (deterministic), then the per-pixel epilogue. Layout as
+// epi_reduce_kernel: one warp per accumulator over 32 groups of four pixels.
+template <int NAP>
+__global__ void __launch_bounds__(32 * Acc<NAP>::N)
+epi_reduce_seg_kernel(const float4 *__restrict__ part, int npix4, int nx, int rpc, int n_bins, int tiles, long long W,
+                      int G, EpiOut out)
+{
+    constexpr int NACC = Acc<NAP>::N;
+    __shared__ float4 sA[NACC][32];
+    __shared__ float wmax[NACC];
+    const int f = blockIdx.y;
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x4 = blockIdx.x * 32 + lane;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (x4 < npix4) {
+        const int tile4 = rpc * nx / 4;             // float4 groups per tile
+        const int tile = x4 / tile4;
+        const long long tt = (long long)f * tiles + tile;
+        const int cf = seg_cta_of(tt * n_bins, W, G), cl = seg_cta_of((tt + 1) * n_bins - 1, W, G);
+        const float4 *src = part + ((size_t)(cf + tt) * NACC + c) * tile4 + (x4 - tile * tile4);
+        const size_t stride = (size_t)NACC * tile4;
+        for (int sgm = 0; sgm <= cl - cf; ++sgm) {
+            const float4 v = src[sgm * stride];
             a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
         }
     }
@@ -784,6 +901,18 @@ cudaError_t launch_prop_t(const pam_plan_s &p, int n_frames, int n_split, float 
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+template <int NAP, int NX>
+cudaError_t launch_seg_t(const pam_plan_s &p, int n_frames, const EpiOut &out, cudaStream_t st)
+{
+    using S = Shape<NX>;
+    const int tiles = (p.nz + S::RPC - 1) / S::RPC;
+    const long long W = (long long)n_frames * tiles * p.n_bins;
+    const int G = prop_seg_ctas(p, n_frames);
+    prop_seg_kernel<NAP, NX><<<G, PROP_THREADS, prop_smem_bytes<NAP, NX>(), st>>>(
+        p.w.Q, p.t.phase, p.t.bin_evan, p.n_bins, p.nz, tiles, (float)p.d.z0_m, (float)p.d.dz_m, W, p.w.part, out);
+    return cudaGetLastError();
+}
+
 template <int NX, bool CLUSTER>
 cudaError_t launch_prop_nc(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields,
                            const EpiOut &out, cudaStream_t st)
@@ -800,6 +929,11 @@ template <int NX>
 cudaError_t launch_prop_nx(const pam_plan_s &p, int n_frames, int napq, int n_split, float *fields,
                            const EpiOut &out, cudaStream_t st)
 {
+    if (prop_seg_mode(p, n_split, fields != nullptr)) {
+        if (napq == 1) return launch_seg_t<1, NX>(p, n_frames, out, st);
+        if (napq == 2) return launch_seg_t<2, NX>(p, n_frames, out, st);
+        return launch_seg_t<3, NX>(p, n_frames, out, st);
+    }
     return prop_uses_cluster(n_split) ? launch_prop_nc<NX, true>(p, n_frames, napq, n_split, fields, out, st)
                                       : launch_prop_nc<NX, false>(p, n_frames, napq, n_split, fields, out, st);
 }
@@ -838,6 +972,9 @@ cudaError_t prepare_nx()
     if (e == cudaSuccess) e = prepare_nc<NX, false>();
     if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<2, NX>, prop_smem_bytes<2, NX>());
     if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<3, NX>, prop_smem_bytes<3, NX>());
+    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<1, NX>, prop_smem_bytes<1, NX>());
+    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<2, NX>, prop_smem_bytes<2, NX>());
+    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<3, NX>, prop_smem_bytes<3, NX>());
     return e;
 }
 
@@ -892,6 +1029,26 @@ int prop_ctas_per_sm() { return PROP_CTAS; }
 
 bool prop_uses_cluster(int n_split) { return n_split <= kMaxClusterSplit; }
 
+bool prop_seg_mode(const pam_plan_s &p, int n_split, bool fields)
+{
+    return p.seg_ok && p.split_override == 0 && n_split > 1 && !fields;
+}
+
+int prop_seg_ctas(const pam_plan_s &p, int n_frames)
+{
+    const int rows = prop_rows_per_cta(p.nx);
+    const long long W = (long long)n_frames * ((p.nz + rows - 1) / rows) * p.n_bins;
+    const long long G = (long long)PROP_CTAS * p.num_sms;
+    return (int)(W < G ? W : G);
+}
+
+size_t prop_seg_part_floats(const pam_plan_s &p, int n_frames)
+{
+    const int rows = prop_rows_per_cta(p.nx);
+    const size_t tiles = (size_t)(p.nz + rows - 1) / rows;
+    return ((size_t)PROP_CTAS * p.num_sms + (size_t)n_frames * tiles) * n_acc(p.n_apod) * rows * p.nx;
+}
+
 int choose_split(const pam_plan_s &p, int n_frames)
 {
     const int rows = prop_rows_per_cta(p.nx);
@@ -929,12 +1086,27 @@ cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split
 }
 
 cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, const EpiOut &out,
-                            cudaStream_t st, bool from_partials)
+                            cudaStream_t st, bool from_partials, bool fields)
 {
     const int npix4 = p.nz * p.nx / 4;  // nx is a multiple of 16
     dim3 grid((npix4 + EPI_THREADS - 1) / EPI_THREADS, n_frames);
     auto v4 = [](float *q) { return reinterpret_cast<float4 *>(q); };
-    if (from_partials || !prop_uses_cluster(n_split)) {
+    if (!from_partials && prop_seg_mode(p, n_split, fields)) {
+        const int rows = prop_rows_per_cta(p.nx);
+        const int tiles = (p.nz + rows - 1) / rows;
+        const long long W = (long long)n_frames * tiles * p.n_bins;
+        const int G = prop_seg_ctas(p, n_frames);
+        const float4 *part = reinterpret_cast<const float4 *>(p.w.part);
+        dim3 rgrid((npix4 + 31) / 32, n_frames);
+        if (napq == 1)
+            epi_reduce_seg_kernel<1><<<rgrid, 32 * Acc<1>::N, 0, st>>>(part, npix4, p.nx, rows, p.n_bins, tiles, W, G, out);
+        else if (napq == 2)
+            epi_reduce_seg_kernel<2><<<rgrid, 32 * Acc<2>::N, 0, st>>>(part, npix4, p.nx, rows, p.n_bins, tiles, W, G, out);
+        else
+            epi_reduce_seg_kernel<3><<<rgrid, 32 * Acc<3>::N, 0, st>>>(part, npix4, p.nx, rows, p.n_bins, tiles, W, G, out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    } else if (from_partials || !prop_uses_cluster(n_split)) {
         const float4 *part = reinterpret_cast<const float4 *>(p.w.part);
         dim3 rgrid((npix4 + 31) / 32, n_frames);
         if (napq == 1)
@@ -986,9 +1158,10 @@ cudaError_t launch_normalize_batch(int n_frames, int max_npix, const BatchFrame 
     return cudaGetLastError();
 }
 
-int epilogue_kernels(int napq, int n_split)
+int epilogue_kernels(const pam_plan_s &p, int napq, int n_split, bool fields)
 {
-    return (prop_uses_cluster(n_split) ? 0 : 1) + (napq > 1 ? 1 : 0);
+    const bool reduce = prop_seg_mode(p, n_split, fields) || !prop_uses_cluster(n_split);
+    return (reduce ? 1 : 0) + (napq > 1 ? 1 : 0);
 }
 
 cudaError_t prepare_kernels(const pam_plan_s &p)
