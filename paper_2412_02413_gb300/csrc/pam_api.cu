@@ -285,10 +285,9 @@ pam_status alloc_plan(pam_plan_s *p)
     size_t target = (size_t)pam::prop_ctas_per_sm() * p->num_sms;
     size_t split_units = (target + row_tiles - 1) / row_tiles;
     p->w.part_units = std::max(F, split_units);
-    // segment sums of the even division (batches of fewer than `target` row tiles)
-    const size_t seg_frames = std::min(F, (target + row_tiles - 1) / row_tiles);
+    // sums of the split tiles of the even division
     const size_t part_floats = std::max(p->w.part_units * (size_t)pam::n_acc(p->n_apod) * npix,
-                                        pam::prop_seg_part_floats(*p, (int)seg_frames));
+                                        pam::prop_seg_part_floats(*p));
     PAM_TRY(dalloc(&p->w.part, part_floats));
     p->seg_ok = true;
     PAM_TRY(dalloc(&p->w.rho_tmp, F * npix));

@@ -147,13 +147,13 @@ cudaError_t launch_prop(const pam_plan_s &p, int n_frames, int napq, int n_split
 cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_split, const EpiOut &out,
                             cudaStream_t st, bool from_partials = false, bool fields = false);
 int epilogue_kernels(const pam_plan_s &p, int napq, int n_split, bool fields = false);   // kernels launch_epilogue launches
-// Even division of small batches (the automatic split above 1, no fields,
-// plan memory for the segment sums): one wave of prop_seg_ctas CTAs over the
-// linearized (frame, tile, bin) sequence; the segment sums need
-// prop_seg_part_floats floats of Workspace::part.
+// Even division (automatic split, no fields, plan memory for the segment
+// sums): one wave of prop_seg_ctas CTAs over the linearized (frame, tile, bin)
+// sequence; the sums of split tiles need prop_seg_part_floats floats of
+// Workspace::part, whatever the number of frames. n_split is then unused.
 bool prop_seg_mode(const pam_plan_s &p, int n_split, bool fields);
 int prop_seg_ctas(const pam_plan_s &p, int n_frames);
-size_t prop_seg_part_floats(const pam_plan_s &p, int n_frames);
+size_t prop_seg_part_floats(const pam_plan_s &p);
 // Batch (pam_batch.cu): the persistent propagate-and-correlate kernel over
 // (frame, row tile) items and the per-frame normalisation.
 // n_items_dev (optional): a device int that caps n_items when the kernel starts.

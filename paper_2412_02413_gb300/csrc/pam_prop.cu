@@ -31,7 +31,7 @@ cudaError_t prepare_fft_kernels(const pam_plan_s &p);
 
 namespace {
 
-constexpr int PROP_WARPS = 8;
+constexpr int PROP_WARPS = 16;
 constexpr int PROP_THREADS = 32 * PROP_WARPS;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -107,7 +107,10 @@ __device__ __forceinline__ float2 phase_cis(unsigned w)
 using namespace ptx;
 
 constexpr int NSTAGE = 4;       // bins in flight per CTA
-constexpr int PROP_CTAS = 2;    // resident CTAs per SM: 16 warps (up to 128 registers each)
+// One CTA per SM (16 warps, up to 128 registers each): with two, the warp
+// scheduler favours the older CTA, which then finishes its share early and
+// leaves the other running at half occupancy.
+constexpr int PROP_CTAS = 1;
 
 template <int NX> struct Shape {
     static constexpr int H = NX / 2;               // half length
@@ -128,11 +131,13 @@ template <int NX> struct Shape {
 
 template <int NAP> struct Acc { static constexpr int N = NAP == 1 ? 1 : (NAP == 2 ? 3 : 6); };
 
-// Tensor-memory columns of one CTA: the two warps of each lane quadrant (w and
-// w + 4) hold 8 pixels x NACC sums per lane each, at columns [a][o].
+// Tensor-memory columns of one CTA: the PROP_WARPS / 4 warps of each lane
+// quadrant (w, w + 4, ...) hold 8 pixels x NACC sums per lane each, at columns
+// [a][o] (a power of 2 of at least 32 columns is allocated).
 template <int NAP> constexpr unsigned tmem_cols()
 {
-    return Acc<NAP>::N == 6 ? 128u : (Acc<NAP>::N == 3 ? 64u : 32u);
+    constexpr unsigned need = (unsigned)(PROP_WARPS / 4) * 8u * (unsigned)Acc<NAP>::N;
+    return need <= 32u ? 32u : need <= 64u ? 64u : need <= 128u ? 128u : need <= 256u ? 256u : 512u;
 }
 
 template <int NAP, int NX>
@@ -638,12 +643,22 @@ __host__ __device__ __forceinline__ int seg_cta_of(long long w, long long W, int
     return (int)(((w + 1) * (long long)G - 1) / W);
 }
 
-// Even division of a small batch: gridDim.x CTAs (one wave) each take an
-// equal contiguous share of the W = frames x tiles x n_bins tile-bins, in
-// (frame, tile, bin) order. A share spans the end of one tile's bins and the
-// start of the next one's; for each such segment the CTA writes its sums to
-// its own slot c + tt (tt = frame x tiles + tile) of part[slot][NACC][RPC][NX],
-// and epi_reduce_seg_kernel adds a tile's slots in CTA order. The staging
+// Slot of CTA c's sums for tile tt when the tile is split between CTAs: a
+// share has at most two partial segments, its first (slot 2c) and its last
+// (slot 2c + 1).
+__host__ __device__ __forceinline__ long long seg_slot(int c, long long tt, long long W, int G, int n_bins)
+{
+    const long long first_tt = ((long long)c * W / G) / n_bins;
+    return 2LL * c + (first_tt < tt ? 1 : 0);
+}
+
+// Even division of the work: gridDim.x CTAs (one wave) each take an equal
+// contiguous share of the W = frames x tiles x n_bins tile-bins, in (frame,
+// tile, bin) order. A share is a run of segments, one per row tile it
+// touches. A segment that covers all bins of its tile finishes the per-pixel
+// epilogue itself; a partial one (only the first and the last of a share can
+// be) writes its sums to slot seg_slot of part[slot][NACC][RPC][NX], and
+// epi_reduce_seg_kernel adds a split tile's slots in CTA order. The staging
 // ring carries over from segment to segment.
 template <int NAP, int NX>
 __global__ void __launch_bounds__(PROP_THREADS, PROP_CTAS)
@@ -657,13 +672,14 @@ prop_seg_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase, c
     constexpr int NOUT = KPL * L2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const PropSmem<NAP, NX> sm(smem_raw);
+    __shared__ float wmax[PROP_THREADS / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
     const unsigned tbase = sm.init(tmem_cols<NAP>());
     const unsigned tcol = acc_tcol(tbase, warp, NACC);
-    const long long G = gridDim.x, c = blockIdx.x;
-    long long w = c * W / G;
-    const long long w1 = (c + 1) * W / G;
+    const int G = gridDim.x, c = blockIdx.x;
+    long long w = (long long)c * W / G;
+    const long long w1 = (long long)(c + 1) * W / G;
     unsigned seq = 0;
     while (w < w1) {
         const long long tt = w / n_bins;
@@ -682,9 +698,21 @@ prop_seg_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase, c
         if (__syncthreads_or(!ok)) break;
         float acc[NOUT][NACC];
         acc_read<NAP>(tcol, acc);
-        if (row_ok) {
+        if (nb == n_bins) {
+            // the whole tile: per-pixel epilogue from the registers
+            float rmax = 0.0f;
+            if (row_ok) {
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    const int k1 = n2 * KPL + o / L2, k2 = o % L2;
+                    const int i = 2 * (k1 + 8 * k2) + g;
+                    rmax = fmaxf(rmax, pixel_epilogue<NAP>(acc[o], out, f, (size_t)j * NX + i));
+                }
+            }
+            if constexpr (NAP > 1) block_max_to(rmax, out.fmax + f, wmax, PROP_THREADS);
+        } else if (row_ok) {
             constexpr size_t plane = (size_t)RPC * NX;
-            float *dst = part + (size_t)(c + tt) * NACC * plane + (size_t)rowl * NX;
+            float *dst = part + (size_t)seg_slot(c, tt, W, G, n_bins) * NACC * plane + (size_t)rowl * NX;
 #pragma unroll
             for (int o = 0; o < NOUT; ++o) {
                 const int k1 = n2 * KPL + o / L2, k2 = o % L2;
@@ -739,9 +767,12 @@ epi_reduce_kernel(const float4 *__restrict__ part, int n_split, int npix4, EpiOu
     if constexpr (NAP > 1) block_max_to(rmax, out.fmax + f, wmax, 32 * NACC);
 }
 
-// The segment sums of prop_seg_kernel: for each pixel, its tile's slots
-// added in CTA order (deterministic), then the per-pixel epilogue. Layout as
-// epi_reduce_kernel: one warp per accumulator over 32 groups of four pixels.
+// The split tiles of prop_seg_kernel: for each pixel of a tile that two or
+// more CTAs share, its slots added in CTA order (deterministic), then the
+// per-pixel epilogue. A tile inside one CTA's share was finished by that CTA;
+// its blocks return at once (a block's 128 pixels never straddle tiles).
+// Layout as epi_reduce_kernel: one warp per accumulator over 32 groups of four
+// pixels.
 template <int NAP>
 __global__ void __launch_bounds__(32 * Acc<NAP>::N)
 epi_reduce_seg_kernel(const float4 *__restrict__ part, int npix4, int nx, int rpc, int n_bins, int tiles, long long W,
@@ -752,17 +783,17 @@ epi_reduce_seg_kernel(const float4 *__restrict__ part, int npix4, int nx, int rp
     __shared__ float wmax[NACC];
     const int f = blockIdx.y;
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile4 = rpc * nx / 4;                    // float4 groups per tile
+    const int tile = (blockIdx.x * 32) / tile4;
+    const long long tt = (long long)f * tiles + tile;
+    const int cf = seg_cta_of(tt * n_bins, W, G), cl = seg_cta_of((tt + 1) * n_bins - 1, W, G);
+    if (cf == cl) return;                              // block-uniform
     const int x4 = blockIdx.x * 32 + lane;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
     if (x4 < npix4) {
-        const int tile4 = rpc * nx / 4;             // float4 groups per tile
-        const int tile = x4 / tile4;
-        const long long tt = (long long)f * tiles + tile;
-        const int cf = seg_cta_of(tt * n_bins, W, G), cl = seg_cta_of((tt + 1) * n_bins - 1, W, G);
-        const float4 *src = part + ((size_t)(cf + tt) * NACC + c) * tile4 + (x4 - tile * tile4);
-        const size_t stride = (size_t)NACC * tile4;
-        for (int sgm = 0; sgm <= cl - cf; ++sgm) {
-            const float4 v = src[sgm * stride];
+        const size_t off = (size_t)c * tile4 + (x4 - tile * tile4);
+        for (int cc = cf; cc <= cl; ++cc) {
+            const float4 v = part[(size_t)seg_slot(cc, tt, W, G, n_bins) * NACC * tile4 + off];
             a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
         }
     }
@@ -1031,7 +1062,8 @@ bool prop_uses_cluster(int n_split) { return n_split <= kMaxClusterSplit; }
 
 bool prop_seg_mode(const pam_plan_s &p, int n_split, bool fields)
 {
-    return p.seg_ok && p.split_override == 0 && n_split > 1 && !fields;
+    (void)n_split;
+    return p.seg_ok && p.split_override == 0 && !fields;
 }
 
 int prop_seg_ctas(const pam_plan_s &p, int n_frames)
@@ -1042,11 +1074,10 @@ int prop_seg_ctas(const pam_plan_s &p, int n_frames)
     return (int)(W < G ? W : G);
 }
 
-size_t prop_seg_part_floats(const pam_plan_s &p, int n_frames)
+size_t prop_seg_part_floats(const pam_plan_s &p)
 {
     const int rows = prop_rows_per_cta(p.nx);
-    const size_t tiles = (size_t)(p.nz + rows - 1) / rows;
-    return ((size_t)PROP_CTAS * p.num_sms + (size_t)n_frames * tiles) * n_acc(p.n_apod) * rows * p.nx;
+    return (size_t)2 * PROP_CTAS * p.num_sms * n_acc(p.n_apod) * rows * p.nx;
 }
 
 int choose_split(const pam_plan_s &p, int n_frames)
