@@ -791,10 +791,27 @@ epi_reduce_seg_kernel(const float4 *__restrict__ part, int npix4, int nx, int rp
     const int x4 = blockIdx.x * 32 + lane;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
     if (x4 < npix4) {
+        // CTAs cf < cc <= cl start inside this tile (their first segment, slot
+        // 2 cc); cf's segment is its last unless its share starts at this tile.
+        // The slots' loads are all issued before the sums (in CTA order), in
+        // batches of 16, so that their latencies overlap.
+        constexpr int MAXS = 16;
+        const int cf_slot = 2 * cf + ((tt > 0 && seg_cta_of(tt * n_bins - 1, W, G) == cf) ? 1 : 0);
         const size_t off = (size_t)c * tile4 + (x4 - tile * tile4);
-        for (int cc = cf; cc <= cl; ++cc) {
-            const float4 v = part[(size_t)seg_slot(cc, tt, W, G, n_bins) * NACC * tile4 + off];
-            a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+        const int ns = cl - cf + 1;
+        for (int base = 0; base < ns; base += MAXS) {
+            float4 v[MAXS];
+#pragma unroll
+            for (int k = 0; k < MAXS; ++k) {
+                const int cc = cf + base + k;
+                const size_t slot = cc == cf ? (size_t)cf_slot : 2 * (size_t)cc;
+                if (base + k < ns) v[k] = part[slot * NACC * tile4 + off];
+            }
+#pragma unroll
+            for (int k = 0; k < MAXS; ++k)
+                if (base + k < ns) {
+                    a.x += v[k].x; a.y += v[k].y; a.z += v[k].z; a.w += v[k].w;
+                }
         }
     }
     sA[c][lane] = a;
