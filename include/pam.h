@@ -155,13 +155,29 @@ int pam_plan_bins(pam_plan_t p, int *bins_out);
 int pam_plan_apod(pam_plan_t p, float *apod_out);
 
 /* Pins the number of bin chunks that the fused propagate-and-correlate
- * kernel splits Omega into for one row tile: 0 = automatic (about two CTAs
- * per SM), n >= 1 = n chunks, capped at n_bins and at what the workspace
- * holds. Splits of up to 8 are reduced on chip inside a thread-block cluster,
+ * kernel splits Omega into for one row tile: 0 = automatic (the even
+ * division described at pam_plan_set_grid), n >= 1 = n chunks, capped at
+ * n_bins and at what the workspace holds. Splits of up to 8 are reduced on chip inside a thread-block cluster,
  * larger ones through global partial sums. Results are deterministic for a
  * given split. Different splits round differently, by the order of the sums
  * over bins. */
 pam_status pam_plan_set_split(pam_plan_t p, int n_split);
+
+/* Number of CTAs of the fused propagate-and-correlate kernel when the split
+ * is automatic (pam_plan_set_split(p, 0)): the launch is one wave of one CTA
+ * per SM, each taking an equal contiguous share of the (frame, row tile, bin)
+ * work. n_ctas = 0 uses every SM; 1 <= n_ctas < the SM count leaves SMs free
+ * for kernels of other streams (several plans on several streams). Errors:
+ * PAM_ERR_INVALID_ARG for n_ctas < 0. Larger values are capped at the SM
+ * count. Different counts divide the sums over bins differently, so results
+ * differ at the rounding level. */
+pam_status pam_plan_set_grid(pam_plan_t p, int n_ctas);
+
+/* Largest radix of the stages of the time FFT (Eq. 1, F_t): 8 (the default:
+ * radix-8 stages while they fit, then radix 4 and 2) or 4 (radix-4 stages,
+ * then radix 2). Fewer stages mean fewer passes through shared memory; the
+ * two round differently. PAM_ERR_INVALID_ARG for other values. */
+pam_status pam_plan_set_fft_radix(pam_plan_t p, int radix);
 
 /* AS back-propagation energy map, Eq. 3, for one apodization.
  *   rf          device float32 [n_frames][n_elem][n_samples]

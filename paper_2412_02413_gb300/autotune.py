@@ -137,3 +137,50 @@ def tune_batch_grid(tuner: Autotuner, batch, rf, num_sms: int, force: bool = Fal
     best = tuner.tune(key, cands, run, force=force)
     batch.configure(use_graph=True, persistent_ctas=int(best))
     return best
+
+
+def stream_grid_candidates(num_sms: int):
+    """CTA counts of the fused kernel tried for several plans on several
+    streams: every SM (0), or a few SMs left free for the other streams' small
+    kernels."""
+    return [0] + [num_sms - k for k in (4, 8, 12, 16, 24) if num_sms - k >= num_sms // 2]
+
+
+def _streams_timer(step, streams, n: int = 200, warmup: int = 12) -> float:
+    """Seconds per step of ``step(i)`` (which enqueues step i on its own
+    stream) over n steps, from CUDA events that span every stream."""
+    import torch
+    for i in range(warmup):
+        step(i)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(streams[0])
+    for st in streams[1:]:
+        st.wait_event(e0)
+    for i in range(n):
+        step(i)
+    for st in streams[1:]:
+        e = torch.cuda.Event()
+        e.record(st)
+        streams[0].wait_event(e)
+    e1.record(streams[0])
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / n
+
+
+def tune_stream_grid(tuner: Autotuner, plans, step, num_sms: int, n_streams: int, w, frames: int, streams,
+                     force: bool = False):
+    """Best CTA count of the fused kernel when ``step`` alternates over
+    ``plans`` on ``streams``; applied to every plan. 0 means one CTA per SM."""
+    key = make_key(f"stream_grid_S{int(n_streams)}", w.n_elem, w.nt, w.nz, frames)
+
+    def run(c):
+        for p in plans:
+            p.set_grid(int(c))
+        return _streams_timer(step, streams)
+
+    best = tuner.tune(key, stream_grid_candidates(num_sms), run, force=force)
+    for p in plans:
+        p.set_grid(int(best))
+    return best

@@ -656,6 +656,22 @@ pam_status pam_sync(pam_plan_t p, void *stream)
     return PAM_OK;
 }
 
+pam_status pam_plan_set_grid(pam_plan_t p, int n_ctas)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (n_ctas < 0) return fail(PAM_ERR_INVALID_ARG, "n_ctas must be >= 0");
+    p->grid_override = n_ctas;
+    return PAM_OK;
+}
+
+pam_status pam_plan_set_fft_radix(pam_plan_t p, int radix)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (radix != 4 && radix != 8) return fail(PAM_ERR_INVALID_ARG, "radix must be 4 or 8");
+    p->fft_radix = radix;
+    return PAM_OK;
+}
+
 pam_status pam_plan_set_split(pam_plan_t p, int n_split)
 {
     if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");

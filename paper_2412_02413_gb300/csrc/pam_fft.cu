@@ -79,16 +79,77 @@ __global__ void tables_kernel(const int *__restrict__ bins, int n_bins, int nx, 
 }
 
 // ------------------------------------------------------ Stockham FFT ----
+// Forward 8-point DFT (exp(-2 pi i m r / 8)) in registers: two 4-point DFTs
+// of the even and odd inputs, the odd ones turned by exp(-2 pi i r / 8).
+__device__ __forceinline__ void fdft8(float2 (&v)[8])
+{
+    const float h = 0.70710678118654752440f;
+    float2 e[4], o[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        e[r] = v[2 * r];
+        o[r] = v[2 * r + 1];
+    }
+    auto dft4 = [](float2 (&a)[4]) {
+        const float2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+        const float2 s13 = cadd(a[1], a[3]), d13 = csub(a[1], a[3]);
+        const float2 md13 = make_float2(d13.y, -d13.x);   // -i * d13
+        a[0] = cadd(s02, s13);
+        a[2] = csub(s02, s13);
+        a[1] = cadd(d02, md13);
+        a[3] = csub(d02, md13);
+    };
+    dft4(e);
+    dft4(o);
+    o[1] = make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));    // (1 - i) / sqrt 2
+    o[2] = make_float2(o[2].y, -o[2].x);                                 // -i
+    o[3] = make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));   // (-1 - i) / sqrt 2
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        v[r] = cadd(e[r], o[r]);
+        v[r + 4] = csub(e[r], o[r]);
+    }
+}
+
 // Forward FFTs (exp(-2 pi i m / n)) of `batch` contiguous n-point sequences in
-// shared memory. Radix-4 stages, then one radix-2 stage when log2 n is odd.
-// Auto-sort ordering, so the output is in natural order. tw[m] holds
-// exp(-2 pi i m / n) for m < n. x and y are ping-pong buffers; the return
-// value is the buffer with the result. Every thread of the CTA must call it.
+// shared memory. With MAXR = 8: radix-8 stages while they fit, then radix-4;
+// with MAXR = 4: radix-4 stages. Then one radix-2 stage if a factor 2 is left.
+// Auto-sort ordering (a stage of radix R takes sub-transforms of length Ns to
+// R Ns), so the output is in natural order. tw[m] holds exp(-2 pi i m / n)
+// for m < n. x and y are ping-pong buffers; the return value is the buffer
+// with the result. Every thread of the CTA must call it.
+template <int MAXR>
 __device__ float2 *stockham(float2 *x, float2 *y, int n, int log2n, int batch, const float2 *tw, int tid, int nth)
 {
+    int Ns = 1;
+    if constexpr (MAXR == 8) {
+        const int q8 = n >> 3;
+        const int lq8 = log2n - 3;
+        for (; 8 * Ns <= n; Ns <<= 3) {
+            const int ts = n / (8 * Ns);
+            for (int t = tid; t < batch * q8; t += nth) {
+                const int bt = t >> lq8, j = t & (q8 - 1);
+                const float2 *xb = x + bt * n;
+                float2 *yb = y + bt * n;
+                const int k = j & (Ns - 1);
+                float2 v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) v[r] = xb[j + r * q8];
+                if (Ns > 1) {
+#pragma unroll
+                    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw[r * k * ts]);
+                }
+                fdft8(v);
+                const int base = (j - k) * 8 + k;
+#pragma unroll
+                for (int r = 0; r < 8; ++r) yb[base + r * Ns] = v[r];
+            }
+            __syncthreads();
+            float2 *tmp = x; x = y; y = tmp;
+        }
+    }
     const int q4 = n >> 2;
     const int lq4 = log2n - 2;
-    int Ns = 1;
     for (; 4 * Ns <= n; Ns <<= 2) {
         const int ts = n / (4 * Ns);
         for (int t = tid; t < batch * q4; t += nth) {
@@ -141,6 +202,7 @@ __device__ float2 *stockham(float2 *x, float2 *y, int n, int log2n, int batch, c
 // Block (0, f) also clears the frame's rho maximum for the epilogue.
 constexpr int TFFT_THREADS = 256;
 
+template <int MAXR>
 __global__ void __launch_bounds__(TFFT_THREADS)
 time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const float2 *__restrict__ tw,
                 const int *__restrict__ bins, int n_bins, float2 *__restrict__ S, int nev, int cstep,
@@ -156,7 +218,7 @@ time_fft_kernel(const float *__restrict__ rf, int ne, int nt, int log2nt, const 
     for (int i = threadIdx.x; i < nt / 4; i += TFFT_THREADS) x4[i] = src[i];  // (x0,x1),(x2,x3) pairs
     for (int m = threadIdx.x; m < M; m += TFFT_THREADS) tws[m] = tw[2 * m];    // exp(-2 pi i m / M)
     __syncthreads();
-    float2 *Z = stockham(x, y, M, log2nt - 1, 1, tws, threadIdx.x, TFFT_THREADS);
+    float2 *Z = stockham<MAXR>(x, y, M, log2nt - 1, 1, tws, threadIdx.x, TFFT_THREADS);
     for (int b = threadIdx.x; b < n_bins; b += TFFT_THREADS) {
         const int k = bins[b];                                 // 0 < k < M
         const float2 zk = Z[k], zm = Z[M - k];
@@ -201,7 +263,7 @@ lateral_kernel(const float2 *__restrict__ S, int ne, int nx, int log2nx, int n_b
     }
     for (int i = threadIdx.x; i < nx; i += LAT_THREADS) tws[i] = twx[i];
     __syncthreads();
-    const float2 *X = stockham(x, y, nx, log2nx, napq, tws, threadIdx.x, LAT_THREADS);
+    const float2 *X = stockham<4>(x, y, nx, log2nx, napq, tws, threadIdx.x, LAT_THREADS);
     const float inv_nx = 1.0f / (float)nx;
     float2 *dst = Q + ((size_t)f * n_bins + b) * (2 * napq * nx);
     const int H = nx / 2, L2 = nx / 16;
@@ -249,9 +311,9 @@ cudaError_t launch_tables(const pam_plan_s &p, cudaStream_t st)
 cudaError_t launch_time_fft(const pam_plan_s &p, const float *rf, int n_frames, cudaStream_t st)
 {
     dim3 grid(p.ne, n_frames);
-    time_fft_kernel<<<grid, TFFT_THREADS, time_fft_smem(p.nt), st>>>(rf, p.ne, p.nt, ilog2i(p.nt), p.t.tw_t,
-                                                                      p.t.bins, p.n_bins, p.w.S, p.nev, p.chan_step,
-                                                                      p.w.fmax);
+    auto kern = p.fft_radix == 8 ? time_fft_kernel<8> : time_fft_kernel<4>;
+    kern<<<grid, TFFT_THREADS, time_fft_smem(p.nt), st>>>(rf, p.ne, p.nt, ilog2i(p.nt), p.t.tw_t, p.t.bins,
+                                                          p.n_bins, p.w.S, p.nev, p.chan_step, p.w.fmax);
     return cudaGetLastError();
 }
 
@@ -289,7 +351,10 @@ cudaError_t launch_tables_frame(const pam_plan_s &p, const int *bins, int n_bins
 // supported nt so that plans of different sizes can coexist.
 cudaError_t prepare_fft_kernels(const pam_plan_s &)
 {
-    return cudaFuncSetAttribute(time_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(time_fft_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)time_fft_smem(8192));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(time_fft_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)time_fft_smem(8192));
 }
 

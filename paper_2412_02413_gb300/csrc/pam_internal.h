@@ -118,6 +118,8 @@ struct pam_plan_s {
     size_t prof_used = 0;              // events recorded since the last read
     long long kernels = 0;             // libpam kernel launches since the last read
     int split_override = 0;            // pam_plan_set_split (0 = automatic)
+    int grid_override = 0;             // pam_plan_set_grid (0 = every SM)
+    int fft_radix = 8;                 // pam_plan_set_fft_radix: largest radix of the time FFT's stages (4 or 8)
     bool seg_ok = false;               // Workspace::part holds prop_seg_part_floats (even division of small batches)
     // tensor-core form (PAM_FORM_GEMM_*): 0 = plain FP32 path
     int form = 0;

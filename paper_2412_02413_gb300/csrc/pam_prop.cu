@@ -1087,7 +1087,8 @@ int prop_seg_ctas(const pam_plan_s &p, int n_frames)
 {
     const int rows = prop_rows_per_cta(p.nx);
     const long long W = (long long)n_frames * ((p.nz + rows - 1) / rows) * p.n_bins;
-    const long long G = (long long)PROP_CTAS * p.num_sms;
+    long long G = (long long)PROP_CTAS * p.num_sms;
+    if (p.grid_override > 0 && p.grid_override < G) G = p.grid_override;
     return (int)(W < G ? W : G);
 }
 

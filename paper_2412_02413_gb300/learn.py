@@ -89,91 +89,64 @@ def mix_frames(bank, n: int, gen, max_sources: int = 6, snr_db: float = 20.0):
     return rf
 
 
-def isnr_esa(img: np.ndarray, pix_area_mm2: float):
-    """Eq. 12 ISNR (dB) and the energy spread area A_0.5 (mm^2)."""
-    m = img > 0.5 * img.max()
-    inside, outside = img[m].mean(), img[~m].mean()
-    return 10.0 * math.log10(inside / outside), float(m.sum() * pix_area_mm2)
-
-
-def save_checkpoint(path: str, params: np.ndarray, meta: dict):
-    os.makedirs(os.path.dirname(path), exist_ok=True)
-    np.savez(path, params=np.asarray(params, np.float32), meta=np.array(json.dumps(meta)))
-
-
-def load_checkpoint(path: str = CHECKPOINT):
-    d = np.load(path)
-    return d["params"], json.loads(str(d["meta"]))
-
-
-def save_training_state(path: str, learned, step: int, meta: dict):
-    """Parameters, Adam moments and the step reached (written atomically)."""
-    state, adam_steps = learned.get_state()
-    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
-    tmp = path + ".tmp.npz"
-    np.savez(tmp, state=state, adam_steps=np.int64(adam_steps), step=np.int64(step), meta=np.array(json.dumps(meta)))
-    os.replace(tmp, path)
-
-
-def load_training_state(path: str):
-    d = np.load(path)
-    return d["state"], int(d["adam_steps"]), int(d["step"]), json.loads(str(d["meta"]))
-
-
-def batch_schedule(n_batches: int, epochs: int, seed: int):
-    """Batch index of every step: a seeded permutation per epoch."""
-    import torch
-    gen = torch.Generator().manual_seed(seed)
-    return [b for _ in range(epochs) for b in torch.randperm(n_batches, generator=gen).tolist()]
-
-
-def lr_at(step: int, steps: int, lr: float, lr_min: float) -> float:
-    """Cosine decay from lr to lr_min over the run."""
-    return lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * step / steps))
-
-
-def held_out_frames(w, n: int, first: int = HELD_OUT_FIRST, workers: int = 0) -> np.ndarray:
-    jobs = [(w, first + i) for i in range(n)]
-    workers = workers or max(1, min(16, os.cpu_count() or 1))
-    with mp.get_context("spawn").Pool(workers) as pool:
-        return np.stack(pool.map(_frame, jobs))
-
-
 def _frame(args):
     w, f = args
     return synth.make_frame(w, f)[0]
 
 
+STRICT_REL_L2 = 1e-2   # accuracy bar of a chosen form: rel L2 of the normalised image, peak pixel exact
+
+
+def accuracy_rows(img_l, img_t, img_as, gate_err, gate_pass, w):
+    """Per-frame accuracy of learned images img_l against exact AS-TAX img_t
+    (device [F][nz][nx]): relative L2 of the max-normalised images over every
+    pixel, brightest-pixel agreement, whether the frame meets the strict bar
+    (rel L2 <= 1e-2 with the exact peak), and the Eq. 12 ISNR / A_0.5 of the
+    learned, exact and plain AS images from pam_image_metrics (GPU)."""
+    import torch
+    from . import pam
+    x0 = -(w.nx - 1) / 2 * w.pitch
+    m = {k: pam.image_metrics(v, x0, w.pitch, w.z0, w.dz) for k, v in
+         (("learned", img_l), ("tax", img_t), ("as", img_as))}
+    nl = img_l / img_l.amax(dim=(1, 2), keepdim=True)
+    nt = img_t / img_t.amax(dim=(1, 2), keepdim=True)
+    rel = (torch.linalg.vector_norm(nl - nt, dim=(1, 2)) / torch.linalg.vector_norm(nt, dim=(1, 2))).cpu().numpy()
+    pl = img_l.flatten(1).argmax(1).cpu().numpy()
+    pt = img_t.flatten(1).argmax(1).cpu().numpy()
+    ge, gp = gate_err.cpu().numpy(), gate_pass.cpu().numpy()
+    rows = []
+    for f in range(img_l.shape[0]):
+        rows.append({
+            "gate_err": float(ge[f]), "gate_pass": int(gp[f]), "rel_l2": float(rel[f]),
+            "peak_match": bool(pl[f] == pt[f]),
+            "meets_bar": bool(rel[f] <= STRICT_REL_L2 and pl[f] == pt[f]),
+            "isnr_learned": m["learned"][f]["isnr_db"], "isnr_tax": m["tax"][f]["isnr_db"],
+            "isnr_as": m["as"][f]["isnr_db"], "esa_learned": 1e6 * m["learned"][f]["esa_m2"],
+            "esa_tax": 1e6 * m["tax"][f]["esa_m2"], "esa_as": 1e6 * m["as"][f]["esa_m2"],
+        })
+    return rows
+
+
 def evaluate(learned, plan, rf_t, w, gate_tol: float):
-    """Learned vs plain AS-TAX on frames rf_t: per-frame gate error and pass,
-    relative L2 of the normalised images, peak match, ISNR of learned, exact
-    and plain AS images."""
+    """Learned vs plain AS-TAX on frames rf_t (accuracy_rows per frame)."""
     import torch
     learned.configure(gate_tol=gate_tol, tensor_cores=True)
     out = learned.as_tax(rf_t)
     ref = plan.as_tax(rf_t, rho_n=True, image_as=True)
     torch.cuda.synchronize()
-    pix = w.pitch * w.dz * 1e6
-    rows = []
-    for f in range(rf_t.shape[0]):
-        il = out["image"][f].cpu().numpy().astype(np.float64)
-        it = ref["image"][f].cpu().numpy().astype(np.float64)
-        ia = ref["image_as"][f].cpu().numpy().astype(np.float64)
-        rows.append({
-            "gate_err": float(out["gate_err"][f].item()),
-            "gate_pass": int(out["gate_pass"][f].item()),
-            "rel_l2": float(np.linalg.norm(il / il.max() - it / it.max()) / np.linalg.norm(it / it.max())),
-            "peak_match": bool(np.argmax(il) == np.argmax(it)),
-            "isnr_learned": isnr_esa(il, pix)[0], "isnr_tax": isnr_esa(it, pix)[0], "isnr_as": isnr_esa(ia, pix)[0],
-            "esa_learned": isnr_esa(il, pix)[1], "esa_tax": isnr_esa(it, pix)[1], "esa_as": isnr_esa(ia, pix)[1],
-        })
-    return rows
+    return accuracy_rows(out["image"], ref["image"], ref["image_as"], out["gate_err"], out["gate_pass"], w)
 
 
 def summarize(rows):
-    a = lambda k: float(np.mean([r[k] for r in rows]))
+    """Means over the frames; the accepted_* entries cover the frames that
+    passed the gate, the only ones whose learned image is returned."""
+    a = lambda k, rs=rows: float(np.mean([r[k] for r in rs])) if rs else float("nan")
+    acc = [r for r in rows if r["gate_pass"]]
     return {"frames": len(rows), "gate_pass_rate": a("gate_pass"), "gate_err_median": float(np.median(
         [r["gate_err"] for r in rows])), "rel_l2_mean": a("rel_l2"), "peak_match_rate": a("peak_match"),
+        "meets_bar_rate": a("meets_bar"),
+        "accepted_rel_l2_max": float(max([r["rel_l2"] for r in acc], default=float("nan"))),
+        "accepted_meet_bar": bool(all(r["meets_bar"] for r in acc)),
         "isnr_learned_db": a("isnr_learned"), "isnr_tax_db": a("isnr_tax"), "isnr_as_db": a("isnr_as"),
         "esa_learned_mm2": a("esa_learned"), "esa_tax_mm2": a("esa_tax"), "esa_as_mm2": a("esa_as")}
 

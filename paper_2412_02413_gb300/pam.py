@@ -63,6 +63,8 @@ _SIGS = {
     "pam_plan_bins": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
     "pam_plan_apod": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_float)]),
     "pam_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pam_plan_set_grid": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pam_plan_set_fft_radix": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_as_backprop": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
     "pam_as_tax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pam_as_dax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
@@ -356,6 +358,14 @@ class Plan:
     def set_split(self, n_split: int = 0):
         """Bin chunks per row tile of the fused kernel (0 = automatic)."""
         _check(load().pam_plan_set_split(self._h, int(n_split)))
+
+    def set_grid(self, n_ctas: int = 0):
+        """CTAs of the fused kernel's even division (0 = one per SM)."""
+        _check(load().pam_plan_set_grid(self._h, int(n_ctas)))
+
+    def set_fft_radix(self, radix: int = 8):
+        """Largest radix of the time FFT's stages (4 or 8)."""
+        _check(load().pam_plan_set_fft_radix(self._h, int(radix)))
 
     def profile_enable(self, on: bool = True):
         """Record CUDA events around each propagate-and-correlate launch."""

@@ -42,3 +42,30 @@ def test_corrupt_cache_is_ignored(tmp_path):
     t = autotune.Autotuner(str(p))
     assert t.lookup("k") is None
     assert t.tune("k", [1], lambda c: 1.0) == 1
+
+
+def test_stream_grid_candidates():
+    assert autotune.stream_grid_candidates(152) == [0, 148, 144, 140, 136, 128]
+    assert autotune.stream_grid_candidates(16) == [0, 12, 8]
+
+
+def test_tune_stream_grid_applies_the_fastest_to_every_plan(tmp_path, monkeypatch):
+    class FakePlan:
+        def __init__(self):
+            self.grid = None
+
+        def set_grid(self, n):
+            self.grid = n
+
+    plans = [FakePlan(), FakePlan(), FakePlan()]
+    # seconds per step as a function of the grid the plans carry: fastest at 136
+    cost = {0: 1.00, 148: 0.98, 144: 0.97, 140: 0.96, 136: 0.95, 128: 0.99}
+    monkeypatch.setattr(autotune, "_streams_timer", lambda step, streams: cost[plans[0].grid])
+
+    class W:
+        n_elem, nt, nz = 128, 4096, 512
+
+    t = autotune.Autotuner(str(tmp_path / "db.json"))
+    best = autotune.tune_stream_grid(t, plans, None, 152, 3, W, 1, [None])
+    assert best == 136 and all(p.grid == 136 for p in plans)
+    assert t.lookup("stream_grid_S3:ne128:nt4096:nz512:F1") == 136

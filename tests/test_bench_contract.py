@@ -53,4 +53,16 @@ def test_reference_arm_line():
     assert d["config"]["workload"] == synth.workload(2).name
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["extrapolated"] is True and 0 < cb["sampled_fraction"] < 1
     assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_oracle_runs_mean_sd_and_extrapolation_label():
+    """The CPU baseline's unit: runs of the oracle on a (bins x rows) sample,
+    each scaled to a whole frame by the sampled fraction; mean and sd."""
+    b = _bench()
+    w = synth.workload(1)
+    rf, _ = synth.make_frame(w, 0)
+    r = b.oracle_runs(w, rf, 2, 4, 2, 3)
+    assert r["runs"] == 3 and r["threads"] == 2 and r["value"] > 0 and r["sd"] >= 0
+    assert r["extrapolated"] is True and r["sampled_fraction"] == 2 * 4 / (len(w.bins()) * w.nz)

@@ -53,10 +53,11 @@ def _run_tax(plan, rf):
 
 # ------------------------------------------------------------- small grids --
 @pytest.mark.parametrize("ne,nt,nz,nbins", [
-    (16, 128, 7, None),     # one CTA tile (128 rows) with a short tail
-    (32, 256, 70, None),    # 64 rows per CTA: two tiles, ragged
-    (64, 512, 45, None),    # 32 rows per CTA: two tiles, ragged
-    (128, 256, 37, 10),     # 16 rows per CTA: three tiles, ragged
+    (16, 128, 7, None),     # one CTA tile (256 rows) with a short tail
+    (16, 128, 300, None),   # 256 rows per CTA: two tiles, ragged
+    (32, 256, 150, None),   # 128 rows per CTA: two tiles, ragged
+    (64, 512, 90, None),    # 64 rows per CTA: two tiles, ragged
+    (128, 256, 77, 10),     # 32 rows per CTA: three tiles, ragged
 ])
 def test_small_tax_parity(ne, nt, nz, nbins):
     w = _tiny(ne, nt, nz, bins=nbins)
@@ -138,6 +139,33 @@ def test_split_paths_match_oracle(w1_frames, split):
     compare_xcorr(_run_tax(plan, frames[0][0]), orc[0])
     e = plan.as_backprop(torch.from_numpy(frames[0][0]).cuda())
     assert rel_l2(e[0].cpu().numpy(), orc[0]["image_as"]) < REL_L2_TOL
+
+
+@pytest.mark.parametrize("radix", [4, 8])
+@pytest.mark.parametrize("nt", [64, 128, 256, 1024])
+def test_time_fft_radix_matches_oracle(radix, nt):
+    """The time FFT with radix-8 stages (then radix 4 and 2) and with radix-4
+    stages (then radix 2), over sequence lengths nt/2 = 32 ... 512 that end in
+    each kind of last stage."""
+    w = _tiny(16, nt, 9, fs=20e6 * nt / 128)
+    rf = synth.random_rf(w.n_elem, w.nt, 40 + nt)
+    plan = _plan(w)
+    plan.set_fft_radix(radix)
+    orc = oracle.as_tax(_geom(w), rf, oracle.pattern(w.n_elem, 3, w.pattern_m))
+    compare_xcorr(_run_tax(plan, rf), orc, check_peak=False)
+
+
+@pytest.mark.parametrize("grid", [0, 1, 37, 100, 151])
+def test_fused_grid_matches_oracle_and_is_deterministic(w2_frame, grid):
+    """The even division over any number of CTAs (one per SM, down to one)
+    agrees with the oracle, and a given count reproduces its bits."""
+    w, rf, src, orc = w2_frame
+    plan = _pam().Plan.from_workload(w, max_frames=1)
+    plan.set_grid(grid)
+    a = _run_tax(plan, rf)
+    compare_xcorr(a, orc)
+    b = _run_tax(plan, rf)
+    assert torch.equal(a["image"], b["image"]) and torch.equal(a["rho_pairs"], b["rho_pairs"])
 
 
 def test_workload1_batched_frames(w1_frames):
