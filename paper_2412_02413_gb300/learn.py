@@ -89,6 +89,49 @@ def mix_frames(bank, n: int, gen, max_sources: int = 6, snr_db: float = 20.0):
     return rf
 
 
+def save_checkpoint(path: str, params: np.ndarray, meta: dict):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.savez(path, params=np.asarray(params, np.float32), meta=np.array(json.dumps(meta)))
+
+
+def load_checkpoint(path: str = CHECKPOINT):
+    d = np.load(path)
+    return d["params"], json.loads(str(d["meta"]))
+
+
+def save_training_state(path: str, learned, step: int, meta: dict):
+    """Parameters, Adam moments and the step reached (written atomically)."""
+    state, adam_steps = learned.get_state()
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, state=state, adam_steps=np.int64(adam_steps), step=np.int64(step), meta=np.array(json.dumps(meta)))
+    os.replace(tmp, path)
+
+
+def load_training_state(path: str):
+    d = np.load(path)
+    return d["state"], int(d["adam_steps"]), int(d["step"]), json.loads(str(d["meta"]))
+
+
+def batch_schedule(n_batches: int, epochs: int, seed: int):
+    """Batch index of every step: a seeded permutation per epoch."""
+    import torch
+    gen = torch.Generator().manual_seed(seed)
+    return [b for _ in range(epochs) for b in torch.randperm(n_batches, generator=gen).tolist()]
+
+
+def lr_at(step: int, steps: int, lr: float, lr_min: float) -> float:
+    """Cosine decay from lr to lr_min over the run."""
+    return lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * step / steps))
+
+
+def held_out_frames(w, n: int, first: int = HELD_OUT_FIRST, workers: int = 0) -> np.ndarray:
+    jobs = [(w, first + i) for i in range(n)]
+    workers = workers or max(1, min(16, os.cpu_count() or 1))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return np.stack(pool.map(_frame, jobs))
+
+
 def _frame(args):
     w, f = args
     return synth.make_frame(w, f)[0]
