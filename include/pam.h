@@ -341,8 +341,8 @@ pam_status pam_batch_as_tax(pam_batch_t b, const float *rf, float *image, float 
 pam_status pam_batch_sync(pam_batch_t b, void *stream);
 
 /* Tuning knobs. use_graph 0 launches the kernels directly (no graph);
- * persistent_ctas > 0 sets the grid of the persistent kernel (0: two per SM,
- * at most one per work item). */
+ * persistent_ctas > 0 sets the grid of the persistent kernel (0: one per SM,
+ * the most that fit; at most one per work item). */
 pam_status pam_batch_configure(pam_batch_t b, int use_graph, int persistent_ctas);
 
 /* Work items (frame, row tile), the persistent grid in use, and the libpam

@@ -1,13 +1,18 @@
 """Measured choice of launch parameters, cached as JSON.
 
-Two knobs have no closed-form best value on a given GPU: the bin split of
-the single-frame fused kernel (how many CTAs share a row tile's bins; set by
-``Plan.set_split``) and the persistent grid of a batch
-(``Batch.configure(persistent_ctas=...)``). The tuner times each candidate
-through the library's own calls, keeps the fastest, and caches it under a key
-made of the problem's shape: (kind, n_elem, nt bucket, nz bucket, frames). nt
-and nz are bucketed to the next power of 2 so that frames of similar size
-share an entry.
+Knobs with no closed-form best value on a given GPU:
+* the largest radix of the time FFT's Stockham stages, 8 or 4
+  (``Plan.set_fft_radix``);
+* the number of CTAs of the fused kernel when several plans run on several
+  streams (``Plan.set_grid``): fewer than one per SM leaves room for the other
+  streams' small kernels;
+* the bin split of the fused kernel (``Plan.set_split``; 0 is the even
+  division);
+* the persistent grid of a batch (``Batch.configure(persistent_ctas=...)``).
+The tuner times each candidate through the library's own calls, keeps the
+fastest, and caches it under a key made of the problem's shape: (kind,
+n_elem, nt bucket, nz bucket, frames). nt and nz are bucketed to the next
+power of 2 so that frames of similar size share an entry.
 
 The selection and caching logic is plain Python and takes any timing
 function, so it is tested without a GPU.
@@ -122,10 +127,34 @@ def tune_plan_split(tuner: Autotuner, plan, rf, candidates=(0, 1, 2, 4, 8, 9, 12
     return best
 
 
+def tune_time_fft_radix(tuner: Autotuner, plans, rf, force: bool = False):
+    """Best largest radix (8 or 4) of the time FFT for ``plans[0].as_tax(rf)``;
+    applied to every plan of ``plans``."""
+    plan = plans[0]
+    F = rf.shape[0] if rf.dim() == 3 else 1
+    key = make_key("fft_radix", plan.n_elem, plan.n_samples, plan.nz, F)
+    outs = {}
+
+    def run(c):
+        plan.set_fft_radix(int(c))
+        return _event_timer(lambda: plan.as_tax(rf, outs=outs), warmup=2, iters=20)
+
+    best = tuner.tune(key, (8, 4), run, force=force)
+    for p in plans:
+        p.set_fft_radix(int(best))
+    return best
+
+
+def batch_grid_candidates(n_items: int, num_sms: int):
+    """Persistent grids tried for a batch: one CTA per SM (the most that fit),
+    three quarters and half of that, each capped at the number of work items."""
+    return sorted({min(n_items, c) for c in (num_sms // 2, (3 * num_sms) // 4, num_sms)})
+
+
 def tune_batch_grid(tuner: Autotuner, batch, rf, num_sms: int, force: bool = False):
     """Best persistent grid for ``batch.as_tax(rf)``; applied to the batch."""
     n_items, _, _ = batch.info()
-    cands = sorted({min(n_items, c) for c in (num_sms, (3 * num_sms) // 2, 2 * num_sms)})
+    cands = batch_grid_candidates(n_items, num_sms)
     key = make_key("batch_grid", batch.n_elem, max(batch.n_samples), max(batch.nz), batch.n_frames)
     img = None
 

@@ -69,3 +69,35 @@ def test_tune_stream_grid_applies_the_fastest_to_every_plan(tmp_path, monkeypatc
     best = autotune.tune_stream_grid(t, plans, None, 152, 3, W, 1, [None])
     assert best == 136 and all(p.grid == 136 for p in plans)
     assert t.lookup("stream_grid_S3:ne128:nt4096:nz512:F1") == 136
+
+
+def test_batch_grid_candidates():
+    assert autotune.batch_grid_candidates(2000, 152) == [76, 114, 152]
+    assert autotune.batch_grid_candidates(100, 152) == [76, 100]
+
+
+def test_tune_time_fft_radix_applies_to_every_plan(tmp_path, monkeypatch):
+    class FakePlan:
+        n_elem, n_samples, nz = 128, 4096, 512
+
+        def __init__(self):
+            self.radix = None
+
+        def set_fft_radix(self, r):
+            self.radix = r
+
+        def as_tax(self, rf, outs=None):
+            pass
+
+    class RF:
+        def dim(self):
+            return 3
+
+        shape = (1, 128, 4096)
+
+    plans = [FakePlan(), FakePlan()]
+    monkeypatch.setattr(autotune, "_event_timer", lambda call, warmup=1, iters=3: {8: 1.0, 4: 2.0}[plans[0].radix])
+    t = autotune.Autotuner(str(tmp_path / "db.json"))
+    assert autotune.tune_time_fft_radix(t, plans, RF()) == 8
+    assert [p.radix for p in plans] == [8, 8]
+    assert t.lookup("fft_radix:ne128:nt4096:nz512:F1") == 8

@@ -159,7 +159,7 @@ def test_batch_workload3_sampled_rows():
     the coherent energy E = image / rho_n^2 must match its Eq. 3 energy, and
     rho_n along the row must match up to the frame's normalisation."""
     ws = synth.batch_workload(6)
-    pick = [0, 2, 5]
+    pick = range(6)
     frames = [(w.nt, w.nz) for w in ws]
     b = _pam().Batch(n_elem=128, pitch=PITCH, fs=40e6, c=C, frames=frames, z0=5e-3, dz=synth.BATCH_DZ,
                      n_bins=300, f_lo=0.5e6, f_hi=8e6, n_apod=3, pattern_m=16)
@@ -174,9 +174,10 @@ def test_batch_workload3_sampled_rows():
             g = oracle.Geometry(128, ws[i].nt, 40e6, C, PITCH, 1, 5e-3 + j * synth.BATCH_DZ, 1e-4, b.bins[i])
             orc = oracle.as_xcorr(g, rfs[i], apod)
             e_gpu = gi[j] / gr[j] ** 2
-            assert rel_l2(e_gpu, orc["image_as"][0]) <= 2e-5, (i, j)
+            # measured on GB300: E rel L2 <= 6e-7, ratio max |d| <= 3.3e-6
+            assert rel_l2(e_gpu, orc["image_as"][0]) <= REL_L2_TOL, (i, j)
             ratio = gr[j] / gr[j].max()
-            assert np.max(np.abs(ratio - orc["rho_n"][0])) <= 2e-5, (i, j)
+            assert np.max(np.abs(ratio - orc["rho_n"][0])) <= NCC_TOL, (i, j)
 
 
 def test_autotuned_batch_grid_keeps_results(tmp_path):

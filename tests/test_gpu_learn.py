@@ -359,7 +359,7 @@ def test_gate_error_is_the_tile_distance():
     g = oracle.Geometry(w.n_elem, w.nt, w.fs, w.c, w.pitch, w.nz, w.z0, w.dz, w.bins())
     orc = oracle.as_tax(g, rf, oracle.pattern(w.n_elem, 3, w.pattern_m))
     rho_x = np.cbrt(np.prod(orc["rho_pairs"], axis=0))
-    rows = 2048 // w.n_elem                         # row tile of the persistent kernel
+    rows = 4096 // w.n_elem                         # row tile of the persistent kernel: 16 warps x 256 / nx rows
     i_pred = rho ** 2 * e
     r0 = (int(np.argmax(i_pred)) // w.n_elem) // rows * rows
     sl = slice(r0, min(w.nz, r0 + rows))
