@@ -290,11 +290,16 @@ def run_forms(args, w, pool, stream, dev):
     if names and names[0] != "fp32" and "fp32" in names:
         names.remove("fp32")
         names.insert(0, "fp32")
+    from paper_2412_02413_gb300 import autotune
+    tuner = autotune.Autotuner()
     for form in names:
         fp = pam.Plan.from_workload(w, max_frames=args.batch, form=form)
         fo = {"image": torch.empty(args.batch, w.nz, w.nx, device=dev),
               "rho_n": torch.empty(args.batch, w.nz, w.nx, device=dev)}
         nb = max(1, P // args.batch)
+        tile = None
+        if form != "fp32":   # the GEMM's M tile (one CTA per row, or CTA pairs), autotuned
+            tile = autotune.tune_gemm_tile(tuner, fp, pool[0:args.batch], form)
 
         def bstep(i):
             s0 = (i % nb) * args.batch
@@ -316,7 +321,8 @@ def run_forms(args, w, pool, stream, dev):
         bstep(0)
         torch.cuda.synchronize()
         img = fo["image"].double()
-        entry = {"frames_per_call": args.batch, "value": args.batch * args.batch_steps / (fms / 1000.0),
+        entry = {"frames_per_call": args.batch, "gemm_tile_m": tile,
+                 "value": args.batch * args.batch_steps / (fms / 1000.0),
                  "unit": "frames/s", "ms_per_frame": fms / (args.batch * args.batch_steps),
                  "main_kernel_us_per_frame": 1000.0 * kms / max(kn, 1) / args.batch}
         if form != "fp32":

@@ -179,6 +179,15 @@ pam_status pam_plan_set_grid(pam_plan_t p, int n_ctas);
  * two round differently. PAM_ERR_INVALID_ARG for other values. */
 pam_status pam_plan_set_fft_radix(pam_plan_t p, int radix);
 
+/* M tile of the tensor-core form's MMAs (PAM_FORM_GEMM_*; no effect on the
+ * plain path): 128 (the default) runs one CTA per depth row; 256 runs each
+ * pair of rows on a 2-CTA cluster whose MMAs (tcgen05 cta_group::2) compute
+ * both rows at once, so that each SM stages and reads half of the spectra
+ * operand, while the pair's even CTA issues every MMA. Results are identical
+ * (the same products summed in the same order). PAM_ERR_INVALID_ARG for other
+ * values. */
+pam_status pam_plan_set_gemm_tile(pam_plan_t p, int m);
+
 /* AS back-propagation energy map, Eq. 3, for one apodization.
  *   rf          device float32 [n_frames][n_elem][n_samples]
  *   apod_index  -1 = full aperture (all ones); 0..n_apod-1 = plan aperture q

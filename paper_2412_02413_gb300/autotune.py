@@ -8,7 +8,9 @@ Knobs with no closed-form best value on a given GPU:
   streams' small kernels;
 * the bin split of the fused kernel (``Plan.set_split``; 0 is the even
   division);
-* the persistent grid of a batch (``Batch.configure(persistent_ctas=...)``).
+* the persistent grid of a batch (``Batch.configure(persistent_ctas=...)``);
+* the M tile of the tensor-core form's MMAs, 128 (one CTA per row) or 256
+  (CTA pairs, ``Plan.set_gemm_tile``).
 The tuner times each candidate through the library's own calls, keeps the
 fastest, and caches it under a key made of the problem's shape: (kind,
 n_elem, nt bucket, nz bucket, frames). nt and nz are bucketed to the next
@@ -212,4 +214,20 @@ def tune_stream_grid(tuner: Autotuner, plans, step, num_sms: int, n_streams: int
     best = tuner.tune(key, stream_grid_candidates(num_sms), run, force=force)
     for p in plans:
         p.set_grid(int(best))
+    return best
+
+
+def tune_gemm_tile(tuner: Autotuner, plan, rf, form: str, force: bool = False):
+    """Best M tile (128 or 256) of the tensor-core form for ``plan.as_tax(rf)``;
+    applied to the plan. The two give identical results."""
+    F = rf.shape[0] if rf.dim() == 3 else 1
+    key = make_key(f"gemm_tile_{form}", plan.n_elem, plan.n_samples, plan.nz, F)
+    outs = {}
+
+    def run(c):
+        plan.set_gemm_tile(int(c))
+        return _event_timer(lambda: plan.as_tax(rf, outs=outs), warmup=2, iters=5)
+
+    best = tuner.tune(key, (128, 256), run, force=force)
+    plan.set_gemm_tile(int(best))
     return best

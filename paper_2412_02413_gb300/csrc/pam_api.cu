@@ -672,6 +672,14 @@ pam_status pam_plan_set_fft_radix(pam_plan_t p, int radix)
     return PAM_OK;
 }
 
+pam_status pam_plan_set_gemm_tile(pam_plan_t p, int m)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (m != 128 && m != 256) return fail(PAM_ERR_INVALID_ARG, "the GEMM tile M must be 128 or 256");
+    p->gemm_m = m;
+    return PAM_OK;
+}
+
 pam_status pam_plan_set_split(pam_plan_t p, int n_split)
 {
     if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");

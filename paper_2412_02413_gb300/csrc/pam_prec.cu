@@ -124,7 +124,10 @@ __device__ __forceinline__ int frame_exp(unsigned bits)
 // holds a_q S[e] (scaled) for the real half of the K range, and the values
 // that pair with Im c for the imaginary half:
 //   Re p = sum Re c Re s - Im c Im s,   Im p = sum Re c Im s + Im c Re s.
-template <bool FP16, bool SPLIT>
+// PAIR: the tile is stored as its two halves of N / 2 columns (the Re
+// columns, then the Im columns), each in the same canonical layout, so that
+// each CTA of a pair copies its half with one bulk copy.
+template <bool FP16, bool SPLIT, bool PAIR>
 __global__ void __launch_bounds__(256)
 prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, const float *__restrict__ kwgt,
                   int K, int n_bins, int ne, int F, const unsigned *__restrict__ smax, uint8_t *__restrict__ Bhi,
@@ -147,7 +150,13 @@ prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, 
             v = imag == 0 ? (kind == 0 ? sr : si) : (kind == 0 ? -si : sr);
         }
         const unsigned short h = to16<FP16>(v);
-        const size_t off = (size_t)(k / 8) * CS_B + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+        size_t off;
+        if constexpr (PAIR) {
+            const int half = n / FG, nn = n % FG;
+            off = (size_t)half * K * FG * 2 + (size_t)(k / 8) * (CS_B / 2) + (nn / 8) * 128 + (nn % 8) * 16 + (k % 8) * 2;
+        } else {
+            off = (size_t)(k / 8) * CS_B + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+        }
         *reinterpret_cast<unsigned short *>(dh + off) = h;
         if (SPLIT) *reinterpret_cast<unsigned short *>(dl + off) = to16<FP16>(v - from16<FP16>(h));
     }
@@ -197,20 +206,21 @@ constexpr int gemm_threads() { return 384; }   // 8 build/fold warps, 1 copy war
 constexpr int REG_LAUNCH = 168, REG_CTRL = 96, REG_FOLD = 200;
 static_assert(2 * 128 * REG_FOLD + 128 * REG_CTRL <= 384 * REG_LAUNCH, "register split exceeds the launch budget");
 
-// Shared memory of one pipeline stage: NPART x (A blocks, B tile, c words).
-__host__ __device__ constexpr size_t gemm_stage_bytes(int K, int npart)
+// Shared memory of one pipeline stage: NPART x (A blocks, B tile, c words);
+// a CTA of a pair holds half of the B tile.
+__host__ __device__ constexpr size_t gemm_stage_bytes(int K, int npart, bool pair = false)
 {
-    return (size_t)npart * (A_BYTES + (size_t)K * NG * 2 + NXP * 4);
+    return (size_t)npart * (A_BYTES + (size_t)K * (pair ? NG / 2 : NG) * 2 + NXP * 4);
 }
-int gemm_stages(int K, bool split)
+int gemm_stages(int K, bool split, bool pair = false)
 {
-    const size_t st = gemm_stage_bytes(K, split ? 2 : 1);
+    const size_t st = gemm_stage_bytes(K, split ? 2 : 1, pair);
     const size_t n = (GEMM_SMEM_LIMIT - GEMM_SMEM_EXTRA) / st;
     return (int)(n < MAX_NST ? n : MAX_NST);
 }
-size_t gemm_smem(int K, bool split)
+size_t gemm_smem(int K, bool split, bool pair = false)
 {
-    return gemm_stages(K, split) * gemm_stage_bytes(K, split ? 2 : 1) + GEMM_SMEM_EXTRA;
+    return gemm_stages(K, split, pair) * gemm_stage_bytes(K, split ? 2 : 1, pair) + GEMM_SMEM_EXTRA;
 }
 
 // steps: element block of K step st in bits 4 (st % 16) of steps[st / 16].
@@ -218,21 +228,31 @@ size_t gemm_smem(int K, bool split)
 // |p_1 + p_2 + p_3|^2 (Eq. 3 with apodizations that sum to one) and write it
 // out per band of bins: band k = bins [n_bins k / n_bands, n_bins (k+1) / n_bands),
 // to part[frame][k][nz][nx].
-template <int NAP, bool FP16, bool SPLIT, bool BANDS = false>
+// PAIR: the CTAs of a 2-CTA cluster take depth rows j (even rank 0) and j + 1
+// of the same frame group. Each builds its own row's A blocks and copies half
+// of the B tile (rank 0 the Re columns, rank 1 the Im columns); rank 0's MMA
+// warps issue cta_group::2 MMAs with M = 256 that write each CTA's own tensor
+// memory. Both CTAs' build and fold warps arrive on rank 0's go barriers; the
+// MMA commits arrive on the stage and accumulator barriers of both CTAs. Each
+// SM thus stages and reads half of B.
+template <int NAP, bool FP16, bool SPLIT, bool BANDS = false, bool PAIR = false>
 __global__ void __launch_bounds__(gemm_threads<NAP>(), 1)
 prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ clo, const uint8_t *__restrict__ Bhi,
                  const uint8_t *__restrict__ Blo, ulonglong2 steps, int4 kq, int n_bins, int nz, int F, int NST,
                  const unsigned *__restrict__ smax, float *__restrict__ part, int *__restrict__ status, int n_bands)
 {
     static_assert(!BANDS || NAP == 3, "band energies fold three apertures");
+    static_assert(!(BANDS && PAIR), "the band form runs unpaired");
     constexpr int NACC = BANDS ? 1 : (NAP == 2 ? 3 : 6);
     constexpr int NPART = SPLIT ? 2 : 1;
     constexpr int ACC_COLS = NAP * NG;
+    constexpr int NGC = PAIR ? NG / 2 : NG;      // B columns in this CTA's shared memory
+    constexpr int CS_BC = NGC / 8 * 128;         // bytes between K chunks of this CTA's B
     constexpr unsigned TMEM_ALLOC = 2 * ACC_COLS <= 256 ? 256u : 512u;
     static_assert(2 * ACC_COLS <= 512, "two accumulator sets must fit in tensor memory");
     extern __shared__ __align__(1024) uint8_t sm[];
-    const size_t bytesB = (size_t)K_of(kq) * NG * 2;
-    const size_t stage = gemm_stage_bytes(K_of(kq), NPART);
+    const size_t bytesB = (size_t)K_of(kq) * NGC * 2;   // this CTA's part of one B tile
+    const size_t stage = gemm_stage_bytes(K_of(kq), NPART, PAIR);
     auto sA = [&](int s) { return sm + s * stage; };
     auto sB = [&](int s) { return sm + s * stage + NPART * A_BYTES; };
     auto sC = [&](int s) { return reinterpret_cast<uint32_t *>(sm + s * stage + NPART * (A_BYTES + bytesB)); };
@@ -245,11 +265,21 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int j = blockIdx.x, grp = blockIdx.y;
+    const unsigned rank = PAIR ? cluster_ctarank() : 0u;
+    const bool row_ok = j < nz;               // a pair's second row may lie past the grid
+    const int jl = row_ok ? j : nz - 1;       // row whose c words are loaded
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
-                     "r"(TMEM_ALLOC)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                         "r"(TMEM_ALLOC)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;\n" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                         "r"(TMEM_ALLOC)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+        }
     }
     if (tid == 0) {
         for (int s = 0; s < MAX_NST; ++s) {
@@ -257,7 +287,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
             mbar_init(&sfree[s], NAP);
         }
         for (int t = 0; t < 2; ++t) {
-            mbar_init(&go[t], 16);
+            mbar_init(&go[t], PAIR ? 32 : 16);
             mbar_init(&afull[t], NAP);
         }
         for (int q = 0; q < 4; ++q) mbar_init(&dbar[q], 1);
@@ -265,9 +295,15 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync_all();   // the peer's barriers exist before any remote arrival
+    else __syncthreads();
     tc_fence_after();
     const unsigned tmem = *tslot;
+    // arrival on go[t] of the pair's rank-0 CTA (or this CTA's when unpaired)
+    auto go_arrive = [&](int t) {
+        if constexpr (PAIR) mbar_arrive_cluster(mapa_rank(smem_u32(&go[t]), 0u));
+        else mbar_arrive(&go[t]);
+    };
     // Register split between the warpgroups (launch: 384 x 168 = 64512): the
     // copy / MMA warpgroup (warps 0-3) drops to REG_CTRL, the two build/fold warpgroups rise
     // to REG_FOLD (2 x 128 x REG_FOLD + 128 x REG_CTRL <= 64512). The host checks
@@ -281,10 +317,18 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
     }
 
     // Bounded wait that also gives up when another thread has aborted.
+    auto try1 = [&](uint64_t *bar, unsigned parity) -> bool {
+        if constexpr (PAIR) return mbar_try_wait_cluster(bar, parity);
+        else return mbar_try_wait(bar, parity);
+    };
+    auto try2 = [&](uint64_t *bar, unsigned parity) -> bool {
+        if constexpr (PAIR) return mbar_try_wait_cluster(bar, parity);
+        else return mbar_try_wait_sleep(bar, parity);
+    };
     auto wait = [&](uint64_t *bar, unsigned parity) -> bool {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (try1(bar, parity)) return true;
         const long long t0 = clock64();
-        while (!mbar_try_wait_sleep(bar, parity)) {
+        while (!try2(bar, parity)) {
             if (*abort_flag) return false;
             if (clock64() - t0 > (1ll << 31)) {
                 *abort_flag = 1;
@@ -301,14 +345,15 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
         // -------- warp 0: bulk-copy ring; warps 1..NAP: MMA chain of aperture q --------
         const int q = warp - 1;
         const bool producer = q < 0;
-        const unsigned idesc = umma_idesc(FP16, NXP, NG);
+        const unsigned idesc = umma_idesc(FP16, PAIR ? 2 * NXP : NXP, NG);
         const int s0 = (q <= 0 ? kq.x : q == 1 ? kq.y : kq.z) / 16;
         const int s1 = (q <= 0 ? kq.y : q == 1 ? kq.z : kq.w) / 16;
         int issued = 0;
         auto load = [&](int b) {
             if (lane == 0) {
                 const int s = b % NST;
-                const size_t ob = ((size_t)grp * n_bins + b) * bytesB, oc = ((size_t)b * nz + j) * NXP;
+                const size_t ob = ((size_t)grp * n_bins + b) * (PAIR ? 2 : 1) * bytesB + rank * bytesB;
+                const size_t oc = ((size_t)b * nz + jl) * NXP;
                 mbar_expect_tx(&full[s], (unsigned)(NPART * (bytesB + NXP * 4)));
                 bulk_g2s(sB(s), Bhi + ob, (unsigned)bytesB, &full[s]);
                 bulk_g2s(sC(s), chi + oc, NXP * 4, &full[s]);
@@ -329,7 +374,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                 ok = __all_sync(0xffffffffu, wait(&sfree[b % NST], (unsigned)(b / NST - 1) & 1u));
                 if (ok) load(b);
             }
-        } else {
+        } else if (!PAIR || rank == 0) {   // a pair's MMAs are issued by its rank-0 CTA
             for (int b = 0; b < n_bins && ok; ++b) {
                 const int s = b % NST, t = b & 1;
                 // go[t]: the blocks of bin b are built (which the build warps did after
@@ -338,26 +383,39 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                 if (!ok) break;
                 tc_fence_after();
                 const uint64_t da0 = umma_desc(smem_u32(sA(s)), BLK_BYTES, 128);
-                const uint64_t db0 = umma_desc(smem_u32(sB(s)), CS_B, 128);
+                const uint64_t db0 = umma_desc(smem_u32(sB(s)), CS_BC, 128);
                 const unsigned dq = tmem + (unsigned)(t * ACC_COLS + q * NG);
+                auto mma = [&](uint64_t a, uint64_t bd, unsigned acc) {
+                    if constexpr (PAIR) umma_elect_pair(dq, a, bd, idesc, acc);
+                    else umma_elect(dq, a, bd, idesc, acc);
+                };
                 for (int st = s0; st < s1; ++st) {
                     const unsigned m = (unsigned)((st < 16 ? steps.x >> (4 * st) : steps.y >> (4 * (st - 16))) & 15u);
                     const uint64_t da = da0 + (uint64_t)((16u - m) * 8u);   // start address field: +128 B per block
-                    const uint64_t db = db0 + (uint64_t)(st * (2 * CS_B / 16));
-                    umma_elect(dq, da, db, idesc, st == s0 ? 0u : 1u);
+                    const uint64_t db = db0 + (uint64_t)(st * (2 * CS_BC / 16));
+                    mma(da, db, st == s0 ? 0u : 1u);
                     if (SPLIT) {
-                        umma_elect(dq, da, db + (uint64_t)(bytesB / 16), idesc, 1u);             // hi x lo
-                        umma_elect(dq, da + (uint64_t)(A_BYTES / 16), db, idesc, 1u);           // lo x hi
+                        mma(da, db + (uint64_t)(bytesB / 16), 1u);             // hi x lo
+                        mma(da + (uint64_t)(A_BYTES / 16), db, 1u);           // lo x hi
                     }
                 }
                 any = true;
-                umma_commit_elect(&sfree[s]);
-                umma_commit_elect(&afull[t]);
+                if constexpr (PAIR) {
+                    umma_commit_pair_elect(&sfree[s], (unsigned short)3);
+                    umma_commit_pair_elect(&afull[t], (unsigned short)3);
+                } else {
+                    umma_commit_elect(&sfree[s]);
+                    umma_commit_elect(&afull[t]);
+                }
             }
+        }
+        if constexpr (PAIR) {
+            // tracks every pair MMA this warp issued (rank 0's own dbar)
+            if (!ok && any && !producer) umma_commit_pair_elect(&dbar[q], (unsigned short)1);
         }
         if (!ok && lane == 0) {
             if (any) {
-                umma_commit(&dbar[q]);       // tracks every MMA this thread issued
+                if constexpr (!PAIR) umma_commit(&dbar[q]);   // tracks every MMA this thread issued
                 mbar_wait(&dbar[q], 0);
             }
             // at most one copy per stage can still be in flight: the last one issued there
@@ -400,7 +458,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&go[b & 1]);
+            if (lane == 0) go_arrive(b & 1);
             return true;
         };
         auto fold = [&](int b) -> bool {
@@ -409,23 +467,24 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
             tc_fence_after();
             // columns of aperture q: Re of frames 0..31, then Im of frames 0..31
             const unsigned base = tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(t * ACC_COLS + fh * FW);
+            // four frames at a time, so that the loaded values take 24 registers
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float re[NAP][8], im[NAP][8];
+            for (int h = 0; h < 4; ++h) {
+                float re[NAP][4], im[NAP][4];
 #pragma unroll
                 for (int q = 0; q < NAP; ++q) {
-                    tmem_ld8(base + (unsigned)(q * NG + 8 * h), re[q]);
-                    tmem_ld8(base + (unsigned)(q * NG + FG + 8 * h), im[q]);
+                    tmem_ld4(base + (unsigned)(q * NG + 4 * h), re[q]);
+                    tmem_ld4(base + (unsigned)(q * NG + FG + 4 * h), im[q]);
                 }
                 tmem_wait_ld();
-                if (h == 1) {
+                if (h == 3) {
                     tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&go[t]);   // set t is free for bin b + 2
+                    if (lane == 0) go_arrive(t);   // set t is free for bin b + 2
                 }
 #pragma unroll
-                for (int pp = 0; pp < 4; ++pp) {
-                    float2 *A = acc[4 * h + pp];
+                for (int pp = 0; pp < 2; ++pp) {
+                    float2 *A = acc[2 * h + pp];
                     const float2 ar = make_float2(re[0][2 * pp], re[0][2 * pp + 1]);
                     const float2 ai = make_float2(im[0][2 * pp], im[0][2 * pp + 1]);
                     const float2 br = make_float2(re[1][2 * pp], re[1][2 * pp + 1]);
@@ -456,8 +515,8 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
         };
 
         if (lane == 0) {   // accumulator sets 0 and 1 start free (bins -2 and -1)
-            mbar_arrive(&go[0]);
-            mbar_arrive(&go[1]);
+            go_arrive(0);
+            go_arrive(1);
         }
         // Blocks are built two bins ahead, so that MMA(b+1) only waits for the
         // fold of bin b-1 to release its accumulator set. Building bin b+2 reuses
@@ -494,7 +553,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
 #pragma unroll
         for (int f = 0; f < (BANDS ? 0 : FW); ++f) {
             const int fr = grp * FG + fh * FW + f;
-            if (fr < F && ok) {
+            if (fr < F && ok && row_ok) {
                 const float s2 = ldexpf(1.0f, 2 * frame_exp(smax[fr]));
 #pragma unroll
                 for (int a = 0; a < NACC; ++a) {
@@ -505,11 +564,17 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
         }
     }
     tc_fence_before();
-    __syncthreads();
+    if constexpr (PAIR) cluster_sync_all();   // the peer's MMAs, copies and arrivals are done
+    else __syncthreads();
     tc_fence_after();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_ALLOC)
-                     : "memory");
+    if (warp == 0) {
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_ALLOC)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_ALLOC)
+                         : "memory");
+    }
 }
 
 // The element block of every K step of 16 (4 bits per step, steps 0-15 in x and
@@ -525,18 +590,33 @@ ulonglong2 gemm_steps(const pam_plan_s &p)
     return steps;
 }
 
-template <int NAP, bool FP16, bool SPLIT>
+template <int NAP, bool FP16, bool SPLIT, bool PAIR>
 cudaError_t launch_gemm_t(const pam_plan_s &p, int n_frames, cudaStream_t st)
 {
     const int groups = (n_frames + FG - 1) / FG;
-    dim3 grid(p.nz, groups);
     const int4 kq = make_int4(p.kq[0], p.kq[1], p.kq[2], p.kq[3]);
-    if (gemm_stages(p.K, SPLIT) < 2 || p.K / 16 > 32) return cudaErrorInvalidConfiguration;
+    const int nst = gemm_stages(p.K, SPLIT, PAIR);
+    if (nst < 2 || p.K / 16 > 32) return cudaErrorInvalidConfiguration;
     const ulonglong2 steps = gemm_steps(p);
-    prec_gemm_kernel<NAP, FP16, SPLIT><<<grid, gemm_threads<NAP>(), gemm_smem(p.K, SPLIT), st>>>(
-        p.t.c_hi, p.t.c_lo, reinterpret_cast<const uint8_t *>(p.w.Bhi), reinterpret_cast<const uint8_t *>(p.w.Blo),
-        steps, kq, p.n_bins, p.nz, n_frames, gemm_stages(p.K, SPLIT), p.w.smax, p.w.part, p.w.status, 0);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(PAIR ? (p.nz + 1) & ~1 : p.nz, groups);   // pairs of rows: an even grid
+    cfg.blockDim = dim3(gemm_threads<NAP>());
+    cfg.dynamicSmemBytes = gemm_smem(p.K, SPLIT, PAIR);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (PAIR) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaError_t e = cudaLaunchKernelEx(&cfg, prec_gemm_kernel<NAP, FP16, SPLIT, false, PAIR>, p.t.c_hi, p.t.c_lo,
+                                       reinterpret_cast<const uint8_t *>(p.w.Bhi),
+                                       reinterpret_cast<const uint8_t *>(p.w.Blo), steps, kq, p.n_bins, p.nz, n_frames,
+                                       nst, p.w.smax, p.w.part, p.w.status, 0);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Per-band full-aperture energies of BF16 or FP16 form (no split): operand
@@ -550,7 +630,7 @@ cudaError_t launch_bands_form(const pam_plan_s &p, const float2 *S, int n_frames
     prec_smax_kernel<<<dim3(p.n_bins, n_frames), 128, 0, st>>>(S, p.n_bins, p.ne, p.w.smax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int groups = (n_frames + FG - 1) / FG;
-    prec_bprep_kernel<FP16, false><<<dim3(p.n_bins, groups), 256, 0, st>>>(
+    prec_bprep_kernel<FP16, false, false><<<dim3(p.n_bins, groups), 256, 0, st>>>(
         S, p.t.ktab, p.t.kwgt, p.K, p.n_bins, p.ne, n_frames, p.w.smax, reinterpret_cast<uint8_t *>(p.w.Bhi),
         nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -571,25 +651,39 @@ cudaError_t launch_form(const pam_plan_s &p, int n_frames, cudaStream_t st)
     prec_smax_kernel<<<dim3(p.n_bins, n_frames), 128, 0, st>>>(p.w.S, p.n_bins, p.ne, p.w.smax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int groups = (n_frames + FG - 1) / FG;
-    prec_bprep_kernel<FP16, SPLIT><<<dim3(p.n_bins, groups), 256, 0, st>>>(
-        p.w.S, p.t.ktab, p.t.kwgt, p.K, p.n_bins, p.ne, n_frames, p.w.smax, reinterpret_cast<uint8_t *>(p.w.Bhi),
-        reinterpret_cast<uint8_t *>(p.w.Blo));
+    const bool pair = p.gemm_m == 256;
+    auto bprep = pair ? prec_bprep_kernel<FP16, SPLIT, true> : prec_bprep_kernel<FP16, SPLIT, false>;
+    bprep<<<dim3(p.n_bins, groups), 256, 0, st>>>(p.w.S, p.t.ktab, p.t.kwgt, p.K, p.n_bins, p.ne, n_frames, p.w.smax,
+                                                 reinterpret_cast<uint8_t *>(p.w.Bhi),
+                                                 reinterpret_cast<uint8_t *>(p.w.Blo));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return p.n_apod == 2 ? launch_gemm_t<2, FP16, SPLIT>(p, n_frames, st) : launch_gemm_t<3, FP16, SPLIT>(p, n_frames, st);
+    if (pair)
+        return p.n_apod == 2 ? launch_gemm_t<2, FP16, SPLIT, true>(p, n_frames, st)
+                             : launch_gemm_t<3, FP16, SPLIT, true>(p, n_frames, st);
+    return p.n_apod == 2 ? launch_gemm_t<2, FP16, SPLIT, false>(p, n_frames, st)
+                         : launch_gemm_t<3, FP16, SPLIT, false>(p, n_frames, st);
 }
 
-template <int NAP, bool FP16, bool SPLIT, bool BANDS = false>
-cudaError_t set_gemm_smem()
+template <int NAP, bool FP16, bool SPLIT, bool BANDS = false, bool PAIR = false>
+cudaError_t set_gemm_smem_one()
 {
     static_assert(MAX_NST >= 2, "the copy ring needs two stages");
-    cudaError_t e = cudaFuncSetAttribute(prec_gemm_kernel<NAP, FP16, SPLIT, BANDS>,
+    cudaError_t e = cudaFuncSetAttribute(prec_gemm_kernel<NAP, FP16, SPLIT, BANDS, PAIR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM_LIMIT);
     if (e != cudaSuccess || BANDS) return e;
     // The register split (setmaxnreg) is sized for a launch of exactly REG_LAUNCH
     // registers per thread; with fewer, the increase could never be granted.
     cudaFuncAttributes a;
-    if ((e = cudaFuncGetAttributes(&a, prec_gemm_kernel<NAP, FP16, SPLIT, BANDS>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&a, prec_gemm_kernel<NAP, FP16, SPLIT, BANDS, PAIR>)) != cudaSuccess) return e;
     return a.numRegs == REG_LAUNCH ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+template <int NAP, bool FP16, bool SPLIT, bool BANDS = false>
+cudaError_t set_gemm_smem()
+{
+    cudaError_t e = set_gemm_smem_one<NAP, FP16, SPLIT, BANDS, false>();
+    if (e != cudaSuccess || BANDS) return e;
+    return set_gemm_smem_one<NAP, FP16, SPLIT, false, true>();
 }
 
 }  // namespace

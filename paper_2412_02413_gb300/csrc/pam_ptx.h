@@ -78,6 +78,45 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint64_t *bar, unsigned parity)
     return true;
 }
 
+// ---- thread-block clusters ----
+__device__ __forceinline__ unsigned cluster_ctarank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+// Shared-memory address of the same object in cluster CTA `rank`.
+__device__ __forceinline__ unsigned mapa_rank(unsigned saddr, unsigned rank)
+{
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+// Arrival on an mbarrier given by its cluster shared-memory address (this CTA
+// or a peer), with release semantics at cluster scope.
+__device__ __forceinline__ void mbar_arrive_cluster(unsigned cluster_addr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];\n" ::"r"(cluster_addr) : "memory");
+}
+// try_wait with acquire semantics at cluster scope (arrivals from peer CTAs),
+// letting the hardware suspend the thread for up to about 10 us.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(10000u)
+        : "memory");
+    return ok != 0;
+}
+// Barrier over every thread of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
 // ---- bulk copies ----
 // One bulk global -> shared copy that completes `bytes` of transaction on `bar`
 // (both addresses 16-byte aligned, bytes a multiple of 16).
@@ -135,6 +174,29 @@ __device__ __forceinline__ void umma_commit_elect(uint64_t *bar)
                  : "memory");
 }
 
+// The same for a CTA pair (cta_group::2): issued by the even CTA of a 2-CTA
+// cluster, the MMA computes M = 256 rows, 128 in each CTA's tensor memory, from
+// each CTA's own A (its 128 rows) and half of B (N / 2 columns in each CTA's
+// shared memory, at the same offsets).
+__device__ __forceinline__ void umma_elect_pair(unsigned tmem_d, uint64_t a, uint64_t b, unsigned idesc,
+                                                unsigned accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// Arrives once on the mbarrier at `bar`'s offset in every CTA of the pair
+// (mask 0b11) when every pair MMA the issuing thread launched has completed.
+__device__ __forceinline__ void umma_commit_pair_elect(uint64_t *bar, unsigned short mask)
+{
+    asm volatile("{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+                 " @e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;\n}\n"
+                 ::"r"(smem_u32(bar)), "h"(mask)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
@@ -179,8 +241,17 @@ __device__ __forceinline__ void tmem_st16(unsigned taddr, const float *v)
                  : "memory");
 }
 
-// Tensor-memory loads of the warp's 32 lanes (32x32b shape): 8, 16 or 32
+// Tensor-memory loads of the warp's 32 lanes (32x32b shape): 4, 8, 16 or 32
 // consecutive columns per lane. tmem_wait_ld() must follow before use.
+__device__ __forceinline__ void tmem_ld4(unsigned taddr, float *v)
+{
+    unsigned r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v[t] = __uint_as_float(r[t]);
+}
 __device__ __forceinline__ void tmem_ld8(unsigned taddr, float *v)
 {
     unsigned r[8];

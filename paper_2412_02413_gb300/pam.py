@@ -65,6 +65,7 @@ _SIGS = {
     "pam_plan_set_split": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_plan_set_grid": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_plan_set_fft_radix": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pam_plan_set_gemm_tile": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_as_backprop": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
     "pam_as_tax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pam_as_dax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
@@ -366,6 +367,10 @@ class Plan:
     def set_fft_radix(self, radix: int = 8):
         """Largest radix of the time FFT's stages (4 or 8)."""
         _check(load().pam_plan_set_fft_radix(self._h, int(radix)))
+
+    def set_gemm_tile(self, m: int = 128):
+        """M tile of the tensor-core form's MMAs: 128 (one CTA per row) or 256 (CTA pairs on two rows)."""
+        _check(load().pam_plan_set_gemm_tile(self._h, int(m)))
 
     def profile_enable(self, on: bool = True):
         """Record CUDA events around each propagate-and-correlate launch."""

@@ -101,3 +101,27 @@ def test_tune_time_fft_radix_applies_to_every_plan(tmp_path, monkeypatch):
     assert autotune.tune_time_fft_radix(t, plans, RF()) == 8
     assert [p.radix for p in plans] == [8, 8]
     assert t.lookup("fft_radix:ne128:nt4096:nz512:F1") == 8
+
+
+def test_tune_gemm_tile_applies_the_fastest(tmp_path, monkeypatch):
+    class FakePlan:
+        n_elem, n_samples, nz = 128, 4096, 512
+        m = None
+
+        def set_gemm_tile(self, m):
+            self.m = m
+
+        def as_tax(self, rf, outs=None):
+            pass
+
+    class RF:
+        shape = (64, 128, 4096)
+
+        def dim(self):
+            return 3
+
+    plan = FakePlan()
+    monkeypatch.setattr(autotune, "_event_timer", lambda call, warmup=1, iters=3: {128: 1.0, 256: 1.2}[plan.m])
+    t = autotune.Autotuner(str(tmp_path / "db.json"))
+    assert autotune.tune_gemm_tile(t, plan, RF(), "fp16split") == 128 and plan.m == 128
+    assert t.lookup("gemm_tile_fp16split:ne128:nt4096:nz512:F64") == 128
