@@ -297,9 +297,11 @@ def run_forms(args, w, pool, stream, dev):
         fo = {"image": torch.empty(args.batch, w.nz, w.nx, device=dev),
               "rho_n": torch.empty(args.batch, w.nz, w.nx, device=dev)}
         nb = max(1, P // args.batch)
-        tile = None
+        tile = lane_rows = None
         if form != "fp32":   # the GEMM's M tile (one CTA per row, or CTA pairs), autotuned
             tile = autotune.tune_gemm_tile(tuner, fp, pool[0:args.batch], form)
+        else:                # depth rows per lane of the fused kernel, autotuned
+            lane_rows = autotune.tune_lane_rows(tuner, [fp], pool[0:args.batch])
 
         def bstep(i):
             s0 = (i % nb) * args.batch
@@ -321,7 +323,7 @@ def run_forms(args, w, pool, stream, dev):
         bstep(0)
         torch.cuda.synchronize()
         img = fo["image"].double()
-        entry = {"frames_per_call": args.batch, "gemm_tile_m": tile,
+        entry = {"frames_per_call": args.batch, "gemm_tile_m": tile, "lane_rows": lane_rows,
                  "value": args.batch * args.batch_steps / (fms / 1000.0),
                  "unit": "frames/s", "ms_per_frame": fms / (args.batch * args.batch_steps),
                  "main_kernel_us_per_frame": 1000.0 * kms / max(kn, 1) / args.batch}
@@ -562,6 +564,7 @@ def run_ours(args):
     # on short runs of this loop (cached), before the timed region.
     from paper_2412_02413_gb300 import autotune
     radix_choice = autotune.tune_time_fft_radix(autotune.Autotuner(), plans, pool[0:F])
+    lane_rows_choice = autotune.tune_lane_rows(autotune.Autotuner(), plans, pool[0:F])
     grid_choice = None
     if NS > 1 and args.grid < 0:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -698,7 +701,7 @@ def run_ours(args):
             "data": "synthetic (seeded Green's-function point sources, 20 dB channel SNR)",
             "config": {**workload_config(w, F), "streams": NS,
                        "fused_ctas": int(grid_choice) if grid_choice else "one per SM",
-                       "time_fft_radix": int(radix_choice),
+                       "time_fft_radix": int(radix_choice), "lane_rows": int(lane_rows_choice),
                        "l2": f"rotating pool of {P} distinct input frames ({P * w.n_elem * w.nt * 4 / 1e6:.0f} MB)"
                              " > 129 MB L2", "parallelism": f"frames sharded over {world} GPU(s)"},
             "e2e": {"value": e2e_value, "unit": "frames/s",

@@ -179,6 +179,14 @@ pam_status pam_plan_set_grid(pam_plan_t p, int n_ctas);
  * two round differently. PAM_ERR_INVALID_ARG for other values. */
 pam_status pam_plan_set_fft_radix(pam_plan_t p, int radix);
 
+/* Depth rows per lane of the plain path's fused kernel when it takes the
+ * whole (frame, row tile, bin) sequence in one wave (the default split): 1
+ * (16 warps per CTA) or 2 (8 warps, each lane computing two rows of the same
+ * pixels, so that each load of the staged spectra and phase words serves
+ * both). The arithmetic of a row is the same either way, so the results are
+ * bit-identical. PAM_ERR_INVALID_ARG for other values. */
+pam_status pam_plan_set_lane_rows(pam_plan_t p, int rows);
+
 /* M tile of the tensor-core form's MMAs (PAM_FORM_GEMM_*; no effect on the
  * plain path): 128 (the default) runs one CTA per depth row; 256 runs each
  * pair of rows on a 2-CTA cluster whose MMAs (tcgen05 cta_group::2) compute

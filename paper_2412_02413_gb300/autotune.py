@@ -3,6 +3,7 @@
 Knobs with no closed-form best value on a given GPU:
 * the largest radix of the time FFT's Stockham stages, 8 or 4
   (``Plan.set_fft_radix``);
+* the depth rows per lane of the fused kernel, 1 or 2 (``Plan.set_lane_rows``);
 * the number of CTAs of the fused kernel when several plans run on several
   streams (``Plan.set_grid``): fewer than one per SM leaves room for the other
   streams' small kernels;
@@ -144,6 +145,25 @@ def tune_time_fft_radix(tuner: Autotuner, plans, rf, force: bool = False):
     best = tuner.tune(key, (8, 4), run, force=force)
     for p in plans:
         p.set_fft_radix(int(best))
+    return best
+
+
+def tune_lane_rows(tuner: Autotuner, plans, rf, force: bool = False):
+    """Best depth rows per lane (1 or 2) of the fused kernel for
+    ``plans[0].as_tax(rf)``; applied to every plan of ``plans``. The two give
+    bit-identical results."""
+    plan = plans[0]
+    F = rf.shape[0] if rf.dim() == 3 else 1
+    key = make_key("lane_rows", plan.n_elem, plan.n_samples, plan.nz, F)
+    outs = {}
+
+    def run(c):
+        plan.set_lane_rows(int(c))
+        return _event_timer(lambda: plan.as_tax(rf, outs=outs), warmup=2, iters=20)
+
+    best = tuner.tune(key, (1, 2), run, force=force)
+    for p in plans:
+        p.set_lane_rows(int(best))
     return best
 
 

@@ -672,6 +672,14 @@ pam_status pam_plan_set_fft_radix(pam_plan_t p, int radix)
     return PAM_OK;
 }
 
+pam_status pam_plan_set_lane_rows(pam_plan_t p, int rows)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (rows != 1 && rows != 2) return fail(PAM_ERR_INVALID_ARG, "rows per lane must be 1 or 2");
+    p->lane_rows = rows;
+    return PAM_OK;
+}
+
 pam_status pam_plan_set_gemm_tile(pam_plan_t p, int m)
 {
     if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");

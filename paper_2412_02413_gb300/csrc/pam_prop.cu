@@ -33,6 +33,11 @@ namespace {
 
 constexpr int PROP_WARPS = 16;
 constexpr int PROP_THREADS = 32 * PROP_WARPS;
+// Depth rows per lane (RPL) of a fused kernel: 1 with PROP_WARPS warps of up
+// to 128 registers, or 2 with half as many warps of up to 255, where a lane
+// takes two rows of the same pixels and every spectra and phase-word load
+// from shared memory serves both. A CTA covers the same rows either way.
+constexpr int prop_warps(int rpl) { return PROP_WARPS / rpl; }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
@@ -112,12 +117,12 @@ constexpr int NSTAGE = 4;       // bins in flight per CTA
 // leaves the other running at half occupancy.
 constexpr int PROP_CTAS = 1;
 
-template <int NX> struct Shape {
+template <int NX, int RPL = 1> struct Shape {
     static constexpr int H = NX / 2;               // half length
     static constexpr int L2 = H / 8;               // lanes per half row
     static constexpr int LPR = 2 * L2;             // lanes per row
-    static constexpr int RPW = 32 / LPR;           // rows per warp
-    static constexpr int RPC = PROP_WARPS * RPW;   // rows per CTA
+    static constexpr int RPW = 32 / LPR * RPL;     // rows per warp
+    static constexpr int RPC = prop_warps(RPL) * RPW;   // rows per CTA (independent of RPL)
     static constexpr int KPL = 8 / L2;             // second-stage DFTs per lane
     // Transpose regions per (aperture, row, half): 8 rows k1 x L2 columns, each
     // row padded by one float2 so that the stores of one k1 and the loads of
@@ -133,22 +138,23 @@ template <int NAP> struct Acc { static constexpr int N = NAP == 1 ? 1 : (NAP == 
 
 // Tensor-memory columns of one CTA: the PROP_WARPS / 4 warps of each lane
 // quadrant (w, w + 4, ...) hold 8 pixels x NACC sums per lane each, at columns
-// [a][o] (a power of 2 of at least 32 columns is allocated).
+// [a][o] (a power of 2 of at least 32 columns is allocated). With two rows
+// per lane, half as many warps hold twice the columns: the same total.
 template <int NAP> constexpr unsigned tmem_cols()
 {
     constexpr unsigned need = (unsigned)(PROP_WARPS / 4) * 8u * (unsigned)Acc<NAP>::N;
     return need <= 32u ? 32u : need <= 64u ? 64u : need <= 128u ? 128u : need <= 256u ? 256u : 512u;
 }
 
-template <int NAP, int NX>
+template <int NAP, int NX, int RPL = 1>
 constexpr size_t prop_smem_bytes()
 {
-    using S = Shape<NX>;
+    using S = Shape<NX, RPL>;
     return (size_t)128                                    // full / empty mbarriers
            + (size_t)NSTAGE * 2 * NAP * NX * sizeof(float2)   // paired spectra, one per stage
            + (size_t)NSTAGE * NX * sizeof(uint4)          // phase words + evanescent coefficients
            + (size_t)(NX / 2) * sizeof(float2)            // exp(+2 pi i m / (nx/2))
-           + (size_t)PROP_WARPS * NAP * S::RPW * 2 * S::RS * sizeof(float2);  // transposes
+           + (size_t)prop_warps(RPL) * NAP * S::RPW * 2 * S::RS * sizeof(float2);  // transposes
 }
 
 // Eq. 4 (with the Appendix A completion) for one pixel and one pair:
@@ -221,10 +227,11 @@ __device__ __forceinline__ void block_max_to(float v, unsigned *dst, float *scra
 // The per-pixel sums over the bins (Eq. 3, Eq. 4 + Appendix A) live in tensor
 // memory, not in registers: 48 accumulators per thread would hold the fused
 // kernel to 2 CTAs per SM. A thread's 8 NACC sums are the columns
-// tcol + a * 8 + o (sum a, pixel o) of its own lane.
-__device__ __forceinline__ unsigned acc_tcol(unsigned tbase, int warp, int nacc)
+// tcol + a * 8 + o (sum a, pixel o) of its own lane; with rpl rows per lane,
+// row rr's from tcol + rr * 8 * nacc.
+__device__ __forceinline__ unsigned acc_tcol(unsigned tbase, int warp, int nacc, int rpl = 1)
 {
-    return tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)((warp >> 2) * 8 * nacc);
+    return tbase + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)((warp >> 2) * rpl * 8 * nacc);
 }
 
 template <int NAP>
@@ -300,6 +307,56 @@ __device__ __forceinline__ void acc_update(unsigned tcol, const float2 (&p)[NAP]
     }
 }
 
+// acc_update in two halves, so that the tensor-memory loads' latency overlaps
+// other work: acc_issue starts loading the thread's 8 x NACC sums of one row
+// (column layout of acc_update); after tmem_wait_ld(), acc_apply adds one
+// bin's fields p[q][o] to them, in acc_update's operation order, and stores
+// them back.
+template <int NAP>
+__device__ __forceinline__ void acc_issue(unsigned tcol, float (&v)[8 * Acc<NAP>::N])
+{
+    if constexpr (NAP == 1) {
+        tmem_ld8(tcol, v);
+    } else {
+        tmem_ld16(tcol, v);
+        if constexpr (NAP == 2) {
+            tmem_ld8(tcol + 16, v + 16);
+        } else {
+            tmem_ld16(tcol + 16, v + 16);
+            tmem_ld16(tcol + 32, v + 32);
+        }
+    }
+}
+template <int NAP>
+__device__ __forceinline__ void acc_apply(unsigned tcol, float (&v)[8 * Acc<NAP>::N], const float2 (&p)[NAP][8])
+{
+#pragma unroll
+    for (int c = 0; c < Acc<NAP>::N; ++c) tmem_pin8(v + 8 * c);
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        v[o] = add_norm(v[o], p[0][o]);
+        if constexpr (NAP >= 2) v[8 + o] = add_norm(v[8 + o], p[1][o]);
+        if constexpr (NAP == 2) v[16 + o] = add_dot(v[16 + o], p[0][o], p[1][o]);
+        if constexpr (NAP == 3) {
+            v[16 + o] = add_norm(v[16 + o], p[2][o]);
+            v[24 + o] = add_dot(v[24 + o], p[0][o], p[1][o]);
+            v[32 + o] = add_dot(v[32 + o], p[1][o], p[2][o]);
+            v[40 + o] = add_dot(v[40 + o], p[2][o], p[0][o]);
+        }
+    }
+    if constexpr (NAP == 1) {
+        tmem_st8(tcol, v);
+    } else {
+        tmem_st16(tcol, v);
+        if constexpr (NAP == 2) {
+            tmem_st8(tcol + 16, v + 16);
+        } else {
+            tmem_st16(tcol + 16, v + 16);
+            tmem_st16(tcol + 32, v + 32);
+        }
+    }
+}
+
 // The sums of the thread's 8 pixels, acc[o][a], back in registers.
 template <int NAP>
 __device__ __forceinline__ void acc_read(unsigned tcol, float (&acc)[8][Acc<NAP>::N])
@@ -317,7 +374,7 @@ __device__ __forceinline__ void acc_read(unsigned tcol, float (&acc)[8][Acc<NAP>
 }
 
 // Shared-memory regions of the fused kernel (layout of prop_smem_bytes).
-template <int NAP, int NX>
+template <int NAP, int NX, int RPL = 1>
 struct PropSmem {
     uint64_t *full;   // [NSTAGE] data of a stage has landed
     uint64_t *empty;  // [NSTAGE] all warps are done with a stage
@@ -343,7 +400,7 @@ struct PropSmem {
     {
         static_assert(2 * NSTAGE * sizeof(uint64_t) <= 120, "barriers overlap the tensor-memory slot");
         if (threadIdx.x < 32) tmem_alloc(tslot, tcols);
-        for (int m = threadIdx.x; m < NX / 2; m += PROP_THREADS) {
+        for (int m = threadIdx.x; m < NX / 2; m += (int)blockDim.x) {
             float s, c;
             sincospif(2.0f * (float)m / (float)(NX / 2), &s, &c);
             sW[m] = make_float2(c, s);
@@ -351,7 +408,7 @@ struct PropSmem {
         if (threadIdx.x == 0) {
             for (int st = 0; st < NSTAGE; ++st) {
                 mbar_init(&full[st], 1);
-                mbar_init(&empty[st], PROP_WARPS);
+                mbar_init(&empty[st], prop_warps(RPL));
             }
             mbar_fence_init();
         }
@@ -373,22 +430,26 @@ struct PropSmem {
 // The bin loop of one row tile: Eq. 2 phasors, the inverse lateral DFT and
 // the per-pixel sums over bins [b_begin, b_begin + nb) of one frame. Qf is the
 // frame's [n_bins][NAP][8][2][NX/16] paired spectra (lateral_kernel's layout,
-// 2 NAP NX complex values per bin); row jj (clamped into the frame) at depth
-// zj. `seq` counts the bins this CTA staged before this call: the staging
-// ring's stage and phase continue from it. The sums accumulate in the
-// thread's tensor-memory columns from tcol. With FIELDS, lanes of valid rows
+// 2 NAP NX complex values per bin). The lane's RPL rows rr (clamped into the
+// frame) are jj[rr] at depths zj[rr]. `seq` counts the bins this CTA staged
+// before this call: the staging ring's stage and phase continue from it. Row
+// rr's sums accumulate in the thread's tensor-memory columns from
+// tcol + rr * 8 * NACC. With FIELDS (one row per lane), lanes of valid rows
 // also write bin b's fields to fields_row + b * bin_stride. Returns false if a
 // bounded wait expired; the copies still in flight have landed by then.
-template <int NAP, int NX, bool FIELDS>
-__device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const float2 *__restrict__ Qf,
+template <int NAP, int NX, bool FIELDS, int RPL = 1>
+__device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX, RPL> &sm, const float2 *__restrict__ Qf,
                                           const uint4 *__restrict__ phase, const int *__restrict__ bin_evan,
-                                          int b_begin, int nb, int jj, float zj, unsigned seq, unsigned tcol,
-                                          float2 *__restrict__ fields_row, bool row_ok, size_t bin_stride)
+                                          int b_begin, int nb, const int (&jj)[RPL], const float (&zj)[RPL],
+                                          unsigned seq, unsigned tcol, float2 *__restrict__ fields_row, bool row_ok,
+                                          size_t bin_stride)
 {
-    using S = Shape<NX>;
+    using S = Shape<NX, RPL>;
+    static_assert(!FIELDS || RPL == 1, "fields are written by the one-row form");
     constexpr int H = S::H, L2 = S::L2, LPR = S::LPR, RPW = S::RPW, KPL = S::KPL;
     constexpr int RS = S::RS;
     constexpr int NOUT = KPL * L2;  // 8 pixels per lane
+    constexpr int NACC = Acc<NAP>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
     float2 *myT = sm.sT + (size_t)warp * (NAP * RPW * 2 * RS);
@@ -397,7 +458,9 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
     // Radix-2 DIF split: lanes of half g take
     // x_g[n'] = exp(2 pi i g n'/nx) (P[n'] + (-1)^g P[n'+H]); the twiddle and
     // the sign are in the paired spectra, so both halves use the same phasors.
-    const unsigned jw = (unsigned)jj;
+    unsigned jw[RPL];
+#pragma unroll
+    for (int rr = 0; rr < RPL; ++rr) jw[rr] = (unsigned)jj[rr];
 
     // Staging pipeline: thread 0 keeps NSTAGE-1 bins in flight with TMA bulk
     // copies (spectra + phase words), each completing on the stage's `full`
@@ -443,87 +506,118 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX> &sm, const flo
         // bins u = g H + L2 n1 + n2 (ph0) and takes the other half's from its
         // partner lane, lane ^ L2 (ph1). The row's phase word is
         // anchor + j*step_hi + hi32(j*step_lo); dropping the carry out of the
-        // low word costs at most 2^-32 turn.
-        float2 ph0[8], ph1[8];
+        // low word costs at most 2^-32 turn. One phase-word load serves the
+        // lane's RPL rows.
+        float2 ph0[RPL][8], ph1[RPL][8];
         if (evan) {
 #pragma unroll
             for (int n1 = 0; n1 < 8; ++n1) {
                 const uint4 d = cD[g * H + L2 * n1 + n2];
-                const float2 c = phase_cis(d.x + jw * d.y + __umulhi(jw, d.z));
-                const float a = exp2f(__uint_as_float(d.w) * zj);
-                ph0[n1] = make_float2(c.x * a, c.y * a);
+#pragma unroll
+                for (int rr = 0; rr < RPL; ++rr) {
+                    const float2 c = phase_cis(d.x + jw[rr] * d.y + __umulhi(jw[rr], d.z));
+                    const float a = exp2f(__uint_as_float(d.w) * zj[rr]);
+                    ph0[rr][n1] = make_float2(c.x * a, c.y * a);
+                }
             }
         } else {
 #pragma unroll
             for (int n1 = 0; n1 < 8; ++n1) {
                 const uint4 d = cD[g * H + L2 * n1 + n2];
-                ph0[n1] = phase_cis(d.x + jw * d.y + __umulhi(jw, d.z));
+#pragma unroll
+                for (int rr = 0; rr < RPL; ++rr) ph0[rr][n1] = phase_cis(d.x + jw[rr] * d.y + __umulhi(jw[rr], d.z));
             }
         }
 #pragma unroll
-        for (int n1 = 0; n1 < 8; ++n1)
-            ph1[n1] = make_float2(__shfl_xor_sync(0xffffffffu, ph0[n1].x, L2),
-                                  __shfl_xor_sync(0xffffffffu, ph0[n1].y, L2));
+        for (int rr = 0; rr < RPL; ++rr)
+#pragma unroll
+            for (int n1 = 0; n1 < 8; ++n1)
+                ph1[rr][n1] = make_float2(__shfl_xor_sync(0xffffffffu, ph0[rr][n1].x, L2),
+                                          __shfl_xor_sync(0xffffffffu, ph0[rr][n1].y, L2));
 
         // first factor: 8-point DFT over n1, twiddle, into the transpose region.
         // The lane's twiddles are loaded once for all apertures (the compiler
-        // reloads them per aperture otherwise; measured 2% faster).
+        // reloads them per aperture otherwise; measured 2% faster). One spectra
+        // load serves the lane's RPL rows.
 #pragma unroll
         for (int q = 0; q < NAP; ++q) {
-            float2 x[8];
+            float2 x[RPL][8];
 #pragma unroll
             for (int n1 = 0; n1 < 8; ++n1) {
                 // a ph0 + c ph1 as two chains of one multiply and three FMAs: 8 FMA-pipe
                 // instructions where two complex products and a packed add take 9
                 const float4 qq = cQ[((q * 8 + n1) * 2 + g) * L2 + n2];
-                const float2 a = make_float2(qq.x, qq.y), c = make_float2(qq.z, qq.w), p = ph0[n1], r = ph1[n1];
-                x[n1] = make_float2(fmaf(a.x, p.x, fmaf(-a.y, p.y, fmaf(c.x, r.x, -c.y * r.y))),
-                                    fmaf(a.x, p.y, fmaf(a.y, p.x, fmaf(c.x, r.y, c.y * r.x))));
-            }
-            IDft<8>::run(x);
-            float2 *reg = myT + ((q * RPW + r) * 2 + g) * RS;
+                const float2 a = make_float2(qq.x, qq.y), c = make_float2(qq.z, qq.w);
 #pragma unroll
-            for (int k1 = 0; k1 < 8; ++k1)
-                reg[S::tpos(k1, n2)] = k1 ? cmul(x[k1], twk[k1]) : x[k1];
+                for (int rr = 0; rr < RPL; ++rr) {
+                    const float2 p0 = ph0[rr][n1], p1 = ph1[rr][n1];
+                    x[rr][n1] = make_float2(fmaf(a.x, p0.x, fmaf(-a.y, p0.y, fmaf(c.x, p1.x, -c.y * p1.y))),
+                                            fmaf(a.x, p0.y, fmaf(a.y, p0.x, fmaf(c.x, p1.y, c.y * p1.x))));
+                }
+            }
+#pragma unroll
+            for (int rr = 0; rr < RPL; ++rr) {
+                IDft<8>::run(x[rr]);
+                float2 *reg = myT + ((q * RPW + r * RPL + rr) * 2 + g) * RS;
+#pragma unroll
+                for (int k1 = 0; k1 < 8; ++k1)
+                    reg[S::tpos(k1, n2)] = k1 ? cmul(x[rr][k1], twk[k1]) : x[rr][k1];
+            }
         }
         __syncwarp();
 
         // second factor: L2-point DFTs over n2; lane owns pixels i = 2(k1 + 8 k2) + g
-        float2 p[NAP][NOUT];
 #pragma unroll
-        for (int q = 0; q < NAP; ++q) {
-            const float2 *reg = myT + ((q * RPW + r) * 2 + g) * RS;
-#pragma unroll
-            for (int s = 0; s < KPL; ++s) {
-                const int k1 = n2 * KPL + s;
-                float2 v[L2];
-                if constexpr (S::V4) {
-                    const float4 *reg4 = reinterpret_cast<const float4 *>(reg + k1 * S::TS);
-#pragma unroll
-                    for (int t = 0; t < L2; t += 2) {
-                        const float4 w4 = reg4[t / 2];
-                        v[t] = make_float2(w4.x, w4.y);
-                        v[t + 1] = make_float2(w4.z, w4.w);
-                    }
-                } else {
-#pragma unroll
-                    for (int t = 0; t < L2; ++t) v[t] = reg[S::tpos(k1, t)];
-                }
-                IDft<L2>::run(v);
-#pragma unroll
-                for (int k2 = 0; k2 < L2; ++k2) p[q][s * L2 + k2] = v[k2];
+        for (int rr = 0; rr < RPL; ++rr) {
+            const unsigned tcol_r = tcol + (unsigned)(rr * 8 * NACC);
+            // Two rows per lane leave the registers to start loading the row's
+            // sums before its second factor, which then hides their latency.
+            float v[8 * NACC];
+            if constexpr (RPL > 1) {
+                if (rr == 0) tmem_wait_st();   // the previous bin's stores have landed
+                acc_issue<NAP>(tcol_r, v);
             }
-        }
-
-        // per-pixel sums over the bins
-        acc_update<NAP>(tcol, p);
-        if constexpr (FIELDS) {
-            if (row_ok) {  // fields of bin b
-                float2 *dst = fields_row + (size_t)b * bin_stride;
+            float2 p[NAP][NOUT];
 #pragma unroll
-                for (int o = 0; o < NOUT; ++o) {
-                    const int k1 = n2 * KPL + o / L2, k2 = o % L2;
-                    dst[2 * (k1 + 8 * k2) + g] = p[0][o];
+            for (int q = 0; q < NAP; ++q) {
+                const float2 *reg = myT + ((q * RPW + r * RPL + rr) * 2 + g) * RS;
+#pragma unroll
+                for (int s = 0; s < KPL; ++s) {
+                    const int k1 = n2 * KPL + s;
+                    float2 v[L2];
+                    if constexpr (S::V4) {
+                        const float4 *reg4 = reinterpret_cast<const float4 *>(reg + k1 * S::TS);
+#pragma unroll
+                        for (int t = 0; t < L2; t += 2) {
+                            const float4 w4 = reg4[t / 2];
+                            v[t] = make_float2(w4.x, w4.y);
+                            v[t + 1] = make_float2(w4.z, w4.w);
+                        }
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < L2; ++t) v[t] = reg[S::tpos(k1, t)];
+                    }
+                    IDft<L2>::run(v);
+#pragma unroll
+                    for (int k2 = 0; k2 < L2; ++k2) p[q][s * L2 + k2] = v[k2];
+                }
+            }
+
+            // per-pixel sums over the bins
+            if constexpr (RPL > 1) {
+                tmem_wait_ld();
+                acc_apply<NAP>(tcol_r, v, p);
+            } else {
+                acc_update<NAP>(tcol_r, p);
+            }
+            if constexpr (FIELDS) {
+                if (row_ok) {  // fields of bin b
+                    float2 *dst = fields_row + (size_t)b * bin_stride;
+#pragma unroll
+                    for (int o = 0; o < NOUT; ++o) {
+                        const int k1 = n2 * KPL + o / L2, k2 = o % L2;
+                        dst[2 * (k1 + 8 * k2) + g] = p[0][o];
+                    }
                 }
             }
         }
@@ -574,10 +668,11 @@ prop_corr_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase,
     const unsigned tbase = sm.init(tmem_cols<NAP>());
     const unsigned tcol = acc_tcol(tbase, warp, NACC);
     acc_zero<NAP>(tcol);
+    const int jja[1] = {jj};
+    const float zja[1] = {z0f + (float)jj * dzf};
     const bool ok = prop_bins<NAP, NX, FIELDS>(
-        sm, Q + (size_t)f * n_bins * 2 * NAP * NX, phase, bin_evan, b_begin, b_end - b_begin, jj,
-        z0f + (float)jj * dzf, 0u, tcol, FIELDS ? fields + ((size_t)f * n_bins * nz + j) * NX : nullptr, row_ok,
-        (size_t)nz * NX);
+        sm, Q + (size_t)f * n_bins * 2 * NAP * NX, phase, bin_evan, b_begin, b_end - b_begin, jja, zja, 0u, tcol,
+        FIELDS ? fields + ((size_t)f * n_bins * nz + j) * NX : nullptr, row_ok, (size_t)nz * NX);
     if (!ok && lane == 0) atomicOr(out.status, 1);
     const bool aborted = __syncthreads_or(!ok) != 0;
     float acc[NOUT][NACC];
@@ -660,23 +755,24 @@ __host__ __device__ __forceinline__ long long seg_slot(int c, long long tt, long
 // be) writes its sums to slot seg_slot of part[slot][NACC][RPC][NX], and
 // epi_reduce_seg_kernel adds a split tile's slots in CTA order. The staging
 // ring carries over from segment to segment.
-template <int NAP, int NX>
-__global__ void __launch_bounds__(PROP_THREADS, PROP_CTAS)
+template <int NAP, int NX, int RPL>
+__global__ void __launch_bounds__(32 * prop_warps(RPL), PROP_CTAS)
 prop_seg_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase, const int *__restrict__ bin_evan,
                 int n_bins, int nz, int tiles, float z0f, float dzf, long long W, float *__restrict__ part,
                 EpiOut out)
 {
-    using S = Shape<NX>;
+    using S = Shape<NX, RPL>;
     constexpr int L2 = S::L2, LPR = S::LPR, RPW = S::RPW, RPC = S::RPC, KPL = S::KPL;
     constexpr int NACC = Acc<NAP>::N;
     constexpr int NOUT = KPL * L2;
+    constexpr int NT = 32 * prop_warps(RPL);
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const PropSmem<NAP, NX> sm(smem_raw);
-    __shared__ float wmax[PROP_THREADS / 32];
+    const PropSmem<NAP, NX, RPL> sm(smem_raw);
+    __shared__ float wmax[NT / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
     const unsigned tbase = sm.init(tmem_cols<NAP>());
-    const unsigned tcol = acc_tcol(tbase, warp, NACC);
+    const unsigned tcol = acc_tcol(tbase, warp, NACC, RPL);
     const int G = gridDim.x, c = blockIdx.x;
     long long w = (long long)c * W / G;
     const long long w1 = (long long)(c + 1) * W / G;
@@ -686,41 +782,52 @@ prop_seg_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase, c
         const int b0 = (int)(w - tt * n_bins);
         const int nb = (int)min((long long)(n_bins - b0), w1 - w);
         const int f = (int)(tt / tiles), tile = (int)(tt - (long long)f * tiles);
-        const int rowl = warp * RPW + r;
-        const int j = tile * RPC + rowl;
-        const bool row_ok = j < nz;
-        const int jj = row_ok ? j : nz - 1;
-        acc_zero<NAP>(tcol);
-        const bool ok = prop_bins<NAP, NX, false>(sm, Q + (size_t)f * n_bins * 2 * NAP * NX, phase, bin_evan, b0, nb,
-                                                  jj, z0f + (float)jj * dzf, seq, tcol, nullptr, row_ok, 0);
+        int jr[RPL], jj[RPL];
+        float zj[RPL];
+        bool rok[RPL];
+#pragma unroll
+        for (int rr = 0; rr < RPL; ++rr) {
+            jr[rr] = tile * RPC + warp * RPW + r * RPL + rr;
+            rok[rr] = jr[rr] < nz;
+            jj[rr] = rok[rr] ? jr[rr] : nz - 1;
+            zj[rr] = z0f + (float)jj[rr] * dzf;
+            acc_zero<NAP>(tcol + (unsigned)(rr * 8 * NACC));
+        }
+        const bool ok = prop_bins<NAP, NX, false, RPL>(sm, Q + (size_t)f * n_bins * 2 * NAP * NX, phase, bin_evan,
+                                                       b0, nb, jj, zj, seq, tcol, nullptr, false, 0);
         seq += (unsigned)nb;
         if (!ok && lane == 0) atomicOr(out.status, 1);
         if (__syncthreads_or(!ok)) break;
-        float acc[NOUT][NACC];
-        acc_read<NAP>(tcol, acc);
-        if (nb == n_bins) {
-            // the whole tile: per-pixel epilogue from the registers
-            float rmax = 0.0f;
-            if (row_ok) {
+        float rmax = 0.0f;
+#pragma unroll
+        for (int rr = 0; rr < RPL; ++rr) {
+            float acc[NOUT][NACC];
+            acc_read<NAP>(tcol + (unsigned)(rr * 8 * NACC), acc);   // warp-collective
+            if (nb == n_bins) {
+                // the whole tile: per-pixel epilogue from the registers
+                if (rok[rr]) {
+#pragma unroll
+                    for (int o = 0; o < NOUT; ++o) {
+                        const int k1 = n2 * KPL + o / L2, k2 = o % L2;
+                        const int i = 2 * (k1 + 8 * k2) + g;
+                        rmax = fmaxf(rmax, pixel_epilogue<NAP>(acc[o], out, f, (size_t)jr[rr] * NX + i));
+                    }
+                }
+            } else if (rok[rr]) {
+                constexpr size_t plane = (size_t)RPC * NX;
+                float *dst = part + (size_t)seg_slot(c, tt, W, G, n_bins) * NACC * plane +
+                             (size_t)(jr[rr] - tile * RPC) * NX;
 #pragma unroll
                 for (int o = 0; o < NOUT; ++o) {
                     const int k1 = n2 * KPL + o / L2, k2 = o % L2;
                     const int i = 2 * (k1 + 8 * k2) + g;
-                    rmax = fmaxf(rmax, pixel_epilogue<NAP>(acc[o], out, f, (size_t)j * NX + i));
+#pragma unroll
+                    for (int a = 0; a < NACC; ++a) dst[a * plane + i] = acc[o][a];
                 }
             }
-            if constexpr (NAP > 1) block_max_to(rmax, out.fmax + f, wmax, PROP_THREADS);
-        } else if (row_ok) {
-            constexpr size_t plane = (size_t)RPC * NX;
-            float *dst = part + (size_t)seg_slot(c, tt, W, G, n_bins) * NACC * plane + (size_t)rowl * NX;
-#pragma unroll
-            for (int o = 0; o < NOUT; ++o) {
-                const int k1 = n2 * KPL + o / L2, k2 = o % L2;
-                const int i = 2 * (k1 + 8 * k2) + g;
-#pragma unroll
-                for (int a = 0; a < NACC; ++a) dst[a * plane + i] = acc[o][a];
-            }
         }
+        if constexpr (NAP > 1)
+            if (nb == n_bins) block_max_to(rmax, out.fmax + f, wmax, NT);
         w += nb;
     }
     sm.release(tbase, tmem_cols<NAP>());
@@ -885,8 +992,10 @@ prop_batch_kernel(const BatchFrame *__restrict__ frames, const int2 *__restrict_
         const bool row_ok = j < fr.nz;
         const int jj = row_ok ? j : fr.nz - 1;
         acc_zero<NAP>(tcol);
-        const bool ok = prop_bins<NAP, NX, false>(sm, fr.Q, fr.phase, fr.bin_evan, 0, fr.n_bins, jj,
-                                                  fr.z0f + (float)jj * fr.dzf, seq, tcol, nullptr, row_ok, 0);
+        const int jja[1] = {jj};
+        const float zja[1] = {fr.z0f + (float)jj * fr.dzf};
+        const bool ok = prop_bins<NAP, NX, false>(sm, fr.Q, fr.phase, fr.bin_evan, 0, fr.n_bins, jja, zja, seq, tcol,
+                                                  nullptr, row_ok, 0);
         seq += (unsigned)fr.n_bins;
         if (!ok && lane == 0) atomicOr(out.status, 1);
         if (__syncthreads_or(!ok)) break;
@@ -949,16 +1058,23 @@ cudaError_t launch_prop_t(const pam_plan_s &p, int n_frames, int n_split, float 
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <int NAP, int NX>
-cudaError_t launch_seg_t(const pam_plan_s &p, int n_frames, const EpiOut &out, cudaStream_t st)
+template <int NAP, int NX, int RPL>
+cudaError_t launch_seg_rt(const pam_plan_s &p, int n_frames, const EpiOut &out, cudaStream_t st)
 {
-    using S = Shape<NX>;
+    using S = Shape<NX, RPL>;
     const int tiles = (p.nz + S::RPC - 1) / S::RPC;
     const long long W = (long long)n_frames * tiles * p.n_bins;
     const int G = prop_seg_ctas(p, n_frames);
-    prop_seg_kernel<NAP, NX><<<G, PROP_THREADS, prop_smem_bytes<NAP, NX>(), st>>>(
+    prop_seg_kernel<NAP, NX, RPL><<<G, 32 * prop_warps(RPL), prop_smem_bytes<NAP, NX, RPL>(), st>>>(
         p.w.Q, p.t.phase, p.t.bin_evan, p.n_bins, p.nz, tiles, (float)p.d.z0_m, (float)p.d.dz_m, W, p.w.part, out);
     return cudaGetLastError();
+}
+
+template <int NAP, int NX>
+cudaError_t launch_seg_t(const pam_plan_s &p, int n_frames, const EpiOut &out, cudaStream_t st)
+{
+    return p.lane_rows == 2 ? launch_seg_rt<NAP, NX, 2>(p, n_frames, out, st)
+                            : launch_seg_rt<NAP, NX, 1>(p, n_frames, out, st);
 }
 
 template <int NX, bool CLUSTER>
@@ -1020,9 +1136,12 @@ cudaError_t prepare_nx()
     if (e == cudaSuccess) e = prepare_nc<NX, false>();
     if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<2, NX>, prop_smem_bytes<2, NX>());
     if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<3, NX>, prop_smem_bytes<3, NX>());
-    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<1, NX>, prop_smem_bytes<1, NX>());
-    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<2, NX>, prop_smem_bytes<2, NX>());
-    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<3, NX>, prop_smem_bytes<3, NX>());
+    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<1, NX, 1>, prop_smem_bytes<1, NX, 1>());
+    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<2, NX, 1>, prop_smem_bytes<2, NX, 1>());
+    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<3, NX, 1>, prop_smem_bytes<3, NX, 1>());
+    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<1, NX, 2>, prop_smem_bytes<1, NX, 2>());
+    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<2, NX, 2>, prop_smem_bytes<2, NX, 2>());
+    if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<3, NX, 2>, prop_smem_bytes<3, NX, 2>());
     return e;
 }
 

@@ -66,6 +66,7 @@ _SIGS = {
     "pam_plan_set_grid": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_plan_set_fft_radix": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_plan_set_gemm_tile": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pam_plan_set_lane_rows": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_as_backprop": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
     "pam_as_tax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pam_as_dax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
@@ -367,6 +368,10 @@ class Plan:
     def set_fft_radix(self, radix: int = 8):
         """Largest radix of the time FFT's stages (4 or 8)."""
         _check(load().pam_plan_set_fft_radix(self._h, int(radix)))
+
+    def set_lane_rows(self, rows: int = 1):
+        """Depth rows per lane of the fused kernel (1 or 2; bit-identical results)."""
+        _check(load().pam_plan_set_lane_rows(self._h, int(rows)))
 
     def set_gemm_tile(self, m: int = 128):
         """M tile of the tensor-core form's MMAs: 128 (one CTA per row) or 256 (CTA pairs on two rows)."""

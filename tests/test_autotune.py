@@ -125,3 +125,30 @@ def test_tune_gemm_tile_applies_the_fastest(tmp_path, monkeypatch):
     t = autotune.Autotuner(str(tmp_path / "db.json"))
     assert autotune.tune_gemm_tile(t, plan, RF(), "fp16split") == 128 and plan.m == 128
     assert t.lookup("gemm_tile_fp16split:ne128:nt4096:nz512:F64") == 128
+
+
+def test_tune_lane_rows_applies_to_every_plan(tmp_path, monkeypatch):
+    class FakePlan:
+        n_elem, n_samples, nz = 128, 4096, 512
+
+        def __init__(self):
+            self.rows = None
+
+        def set_lane_rows(self, r):
+            self.rows = r
+
+        def as_tax(self, rf, outs=None):
+            pass
+
+    class RF:
+        shape = (1, 128, 4096)
+
+        def dim(self):
+            return 3
+
+    plans = [FakePlan(), FakePlan()]
+    monkeypatch.setattr(autotune, "_event_timer", lambda call, warmup=1, iters=3: {1: 1.0, 2: 0.9}[plans[0].rows])
+    t = autotune.Autotuner(str(tmp_path / "db.json"))
+    assert autotune.tune_lane_rows(t, plans, RF()) == 2
+    assert [p.rows for p in plans] == [2, 2]
+    assert t.lookup("lane_rows:ne128:nt4096:nz512:F1") == 2
