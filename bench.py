@@ -298,9 +298,16 @@ def run_forms(args, w, pool, stream, dev):
               "rho_n": torch.empty(args.batch, w.nz, w.nx, device=dev)}
         nb = max(1, P // args.batch)
         tile = lane_rows = None
-        if form != "fp32":   # the GEMM's M tile (one CTA per row, or CTA pairs), autotuned
-            tile = autotune.tune_gemm_tile(tuner, fp, pool[0:args.batch], form)
-        else:                # depth rows per lane of the fused kernel, autotuned
+        if form != "fp32":   # the GEMM's M tile (one CTA per row, or CTA pairs)
+            if args.gemm_tile:
+                tile = args.gemm_tile
+                fp.set_gemm_tile(tile)
+            else:
+                tile = autotune.tune_gemm_tile(tuner, fp, pool[0:args.batch], form)
+        elif args.lane_rows:  # depth rows per lane of the fused kernel
+            lane_rows = args.lane_rows
+            fp.set_lane_rows(lane_rows)
+        else:
             lane_rows = autotune.tune_lane_rows(tuner, [fp], pool[0:args.batch])
 
         def bstep(i):
@@ -563,8 +570,18 @@ def run_ours(args):
     # SM the other streams' small kernels run beside it. Picked by the autotuner
     # on short runs of this loop (cached), before the timed region.
     from paper_2412_02413_gb300 import autotune
-    radix_choice = autotune.tune_time_fft_radix(autotune.Autotuner(), plans, pool[0:F])
-    lane_rows_choice = autotune.tune_lane_rows(autotune.Autotuner(), plans, pool[0:F])
+    if args.fft_radix:
+        radix_choice = args.fft_radix
+        for p_ in plans:
+            p_.set_fft_radix(args.fft_radix)
+    else:
+        radix_choice = autotune.tune_time_fft_radix(autotune.Autotuner(), plans, pool[0:F])
+    if args.lane_rows:
+        lane_rows_choice = args.lane_rows
+        for p_ in plans:
+            p_.set_lane_rows(args.lane_rows)
+    else:
+        lane_rows_choice = autotune.tune_lane_rows(autotune.Autotuner(), plans, pool[0:F])
     grid_choice = None
     if NS > 1 and args.grid < 0:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -642,6 +659,11 @@ def run_ours(args):
                  for _ in range(NE)]
     outs_np = [(a.numpy(), b.numpy()) for a, b in outs_host]
     extra = [pam.Plan.from_workload(w, max_frames=F) for _ in range(NE - NS)]
+    for p_ in extra:   # the tuned choices of the timed plans
+        p_.set_fft_radix(int(radix_choice))
+        p_.set_lane_rows(int(lane_rows_choice))
+        if grid_choice:
+            p_.set_grid(int(grid_choice))
     plans2 = plans + extra
     streams2 = streams + [torch.cuda.Stream(device=dev) for _ in range(NE - NS)]
     done = [torch.cuda.Event() for _ in range(NE)]
@@ -756,6 +778,12 @@ def main():
     ap.add_argument("--streams", type=int, default=3, help="plans / streams the steps alternate over")
     ap.add_argument("--grid", type=int, default=-1,
                     help="CTAs of the fused kernel in the multi-stream loop (-1: autotuned, 0: one per SM)")
+    ap.add_argument("--fft-radix", type=int, default=0, choices=[0, 4, 8],
+                    help="largest radix of the time FFT (0: autotuned)")
+    ap.add_argument("--lane-rows", type=int, default=0, choices=[0, 1, 2],
+                    help="depth rows per lane of the fused kernel (0: autotuned)")
+    ap.add_argument("--gemm-tile", type=int, default=0, choices=[0, 128, 256],
+                    help="M tile of the tensor-core forms (0: autotuned)")
     ap.add_argument("--pool", type=int, default=POOL_FRAMES)
     ap.add_argument("--cpu-runs", type=int, default=10, help="runs of each cpu_baseline measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
