@@ -80,7 +80,7 @@ def prop_source_hash():
 def committed_traffic():
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     or None when the kernel source changed since it was captured."""
-    p = os.path.join(ROOT, "profiles", "prop_corr_traffic.json")
+    p = os.path.join(ROOT, "profiles", "prop_seg_traffic_astax_128el_128x512.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
