@@ -297,13 +297,18 @@ def run_forms(args, w, pool, stream, dev):
         fo = {"image": torch.empty(args.batch, w.nz, w.nx, device=dev),
               "rho_n": torch.empty(args.batch, w.nz, w.nx, device=dev)}
         nb = max(1, P // args.batch)
-        tile = lane_rows = None
-        if form != "fp32":   # the GEMM's M tile (one CTA per row, or CTA pairs)
+        tile = gframes = lane_rows = None
+        if form != "fp32":   # the GEMM's M tile (one CTA per row, or CTA pairs) and frames per CTA
             if args.gemm_tile:
                 tile = args.gemm_tile
                 fp.set_gemm_tile(tile)
             else:
                 tile = autotune.tune_gemm_tile(tuner, fp, pool[0:args.batch], form)
+            if args.gemm_frames:
+                gframes = args.gemm_frames
+                fp.set_gemm_frames(gframes)
+            else:
+                gframes = autotune.tune_gemm_frames(tuner, fp, pool[0:args.batch], form)
         elif args.lane_rows:  # depth rows per lane of the fused kernel
             lane_rows = args.lane_rows
             fp.set_lane_rows(lane_rows)
@@ -330,7 +335,8 @@ def run_forms(args, w, pool, stream, dev):
         bstep(0)
         torch.cuda.synchronize()
         img = fo["image"].double()
-        entry = {"frames_per_call": args.batch, "gemm_tile_m": tile, "lane_rows": lane_rows,
+        entry = {"frames_per_call": args.batch, "gemm_tile_m": tile, "gemm_frames_per_cta": gframes,
+                 "lane_rows": lane_rows,
                  "value": args.batch * args.batch_steps / (fms / 1000.0),
                  "unit": "frames/s", "ms_per_frame": fms / (args.batch * args.batch_steps),
                  "main_kernel_us_per_frame": 1000.0 * kms / max(kn, 1) / args.batch}
@@ -784,6 +790,8 @@ def main():
                     help="depth rows per lane of the fused kernel (0: autotuned)")
     ap.add_argument("--gemm-tile", type=int, default=0, choices=[0, 128, 256],
                     help="M tile of the tensor-core forms (0: autotuned)")
+    ap.add_argument("--gemm-frames", type=int, default=0, choices=[0, 16, 32],
+                    help="frames per CTA of the tensor-core forms (0: autotuned)")
     ap.add_argument("--pool", type=int, default=POOL_FRAMES)
     ap.add_argument("--cpu-runs", type=int, default=10, help="runs of each cpu_baseline measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -196,6 +196,14 @@ pam_status pam_plan_set_lane_rows(pam_plan_t p, int rows);
  * values. */
 pam_status pam_plan_set_gemm_tile(pam_plan_t p, int m);
 
+/* Frames per CTA of the tensor-core form (PAM_FORM_GEMM_*): 32 (the default;
+ * the MMA's N = 64 columns hold Re and Im of 32 frames) or 16 (N = 32). A
+ * call's frames are processed in groups of this size; with 16, a call of 16
+ * frames or fewer does no MMA work for absent frames, and each MMA reads half
+ * the spectra operand for the same circulant operand. Results are identical.
+ * PAM_ERR_INVALID_ARG for other values. */
+pam_status pam_plan_set_gemm_frames(pam_plan_t p, int frames);
+
 /* AS back-propagation energy map, Eq. 3, for one apodization.
  *   rf          device float32 [n_frames][n_elem][n_samples]
  *   apod_index  -1 = full aperture (all ones); 0..n_apod-1 = plan aperture q

@@ -11,7 +11,8 @@ Knobs with no closed-form best value on a given GPU:
   division);
 * the persistent grid of a batch (``Batch.configure(persistent_ctas=...)``);
 * the M tile of the tensor-core form's MMAs, 128 (one CTA per row) or 256
-  (CTA pairs, ``Plan.set_gemm_tile``).
+  (CTA pairs, ``Plan.set_gemm_tile``), and its frames per CTA, 32 or 16 (the
+  MMA's N tile, ``Plan.set_gemm_frames``).
 The tuner times each candidate through the library's own calls, keeps the
 fastest, and caches it under a key made of the problem's shape: (kind,
 n_elem, nt bucket, nz bucket, frames). nt and nz are bucketed to the next
@@ -250,4 +251,20 @@ def tune_gemm_tile(tuner: Autotuner, plan, rf, form: str, force: bool = False):
 
     best = tuner.tune(key, (128, 256), run, force=force)
     plan.set_gemm_tile(int(best))
+    return best
+
+
+def tune_gemm_frames(tuner: Autotuner, plan, rf, form: str, force: bool = False):
+    """Best frames per CTA (32 or 16) of the tensor-core form for
+    ``plan.as_tax(rf)``; applied to the plan. The two give identical results."""
+    F = rf.shape[0] if rf.dim() == 3 else 1
+    key = make_key(f"gemm_frames_{form}", plan.n_elem, plan.n_samples, plan.nz, F)
+    outs = {}
+
+    def run(c):
+        plan.set_gemm_frames(int(c))
+        return _event_timer(lambda: plan.as_tax(rf, outs=outs), warmup=2, iters=5)
+
+    best = tuner.tune(key, (32, 16), run, force=force)
+    plan.set_gemm_frames(int(best))
     return best

@@ -688,6 +688,14 @@ pam_status pam_plan_set_gemm_tile(pam_plan_t p, int m)
     return PAM_OK;
 }
 
+pam_status pam_plan_set_gemm_frames(pam_plan_t p, int frames)
+{
+    if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");
+    if (frames != 16 && frames != 32) return fail(PAM_ERR_INVALID_ARG, "frames per CTA must be 16 or 32");
+    p->gemm_frames = frames;
+    return PAM_OK;
+}
+
 pam_status pam_plan_set_split(pam_plan_t p, int n_split)
 {
     if (!p) return fail(PAM_ERR_INVALID_ARG, "plan is NULL");

@@ -7,9 +7,9 @@
 //   c_j[d] = (1/nx) sum_u exp(i kz_u z_j) exp(+2 pi i u d / nx),
 // i.e. the inverse lateral DFT of the row's propagator phasors. The plan
 // tabulates c_j once per (bin, row) from the exact FP64 phase words, in
-// 16-bit form. A call then evaluates the sum over elements for 32 frames at a
-// time as one tcgen05 GEMM per (bin, row) with M = 128 pixels,
-// N = 2 x 32 (Re, Im of each frame) and K = 16 per element block of 8:
+// 16-bit form. A call then evaluates the sum over elements for FG = 32 (or 16)
+// frames at a time as one tcgen05 GEMM per (bin, row) with M = 128 pixels,
+// N = 2 x FG (Re, Im of each frame) and K = 16 per element block of 8:
 //   A[i][k] = Re or Im c_j[(i - e_k) mod nx]   (8 x 8 Toeplitz blocks in shared memory)
 //   B[k][n] = +-Re or Im of a S / sigma          (packed per call)
 // so that the real GEMM yields Re and Im of the complex sum. Each aperture is
@@ -33,9 +33,15 @@ namespace {
 using namespace ptx;
 
 constexpr int NXP = 128;                    // lateral length of this form
-constexpr int FG = kFramesPerGroup;         // frames per CTA
-constexpr int NG = 2 * FG;                  // GEMM N
-constexpr int CS_B = NG / 8 * 128;          // bytes between K chunks of B
+// Frames per CTA (FG, 32 or 16; kFramesPerGroup sizes the workspace for the
+// larger) and what follows from it: the GEMM's N = 2 FG columns (Re and Im of
+// each frame) and the bytes between K chunks of the B tile.
+template <int FG> struct Grp {
+    static_assert(FG == 16 || FG == 32, "frames per CTA");
+    static constexpr int NG = 2 * FG;
+    static constexpr int CS_B = NG / 8 * 128;
+    static constexpr int FW = FG / 2;        // frames per fold warp
+};
 
 __host__ __device__ __forceinline__ int K_of(int4 kq) { return kq.w; }
 
@@ -127,19 +133,20 @@ __device__ __forceinline__ int frame_exp(unsigned bits)
 // PAIR: the tile is stored as its two halves of N / 2 columns (the Re
 // columns, then the Im columns), each in the same canonical layout, so that
 // each CTA of a pair copies its half with one bulk copy.
-template <bool FP16, bool SPLIT, bool PAIR>
+template <bool FP16, bool SPLIT, bool PAIR, int FG>
 __global__ void __launch_bounds__(256)
 prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, const float *__restrict__ kwgt,
                   int K, int n_bins, int ne, int F, const unsigned *__restrict__ smax, uint8_t *__restrict__ Bhi,
                   uint8_t *__restrict__ Blo)
 {
+    constexpr int NG = Grp<FG>::NG, CS_B = Grp<FG>::CS_B;
     const int b = blockIdx.x, g = blockIdx.y;
     const size_t tile = (size_t)K * NG * 2;
     uint8_t *dh = Bhi + ((size_t)g * n_bins + b) * tile;
     uint8_t *dl = SPLIT ? Blo + ((size_t)g * n_bins + b) * tile : nullptr;
     for (int idx = threadIdx.x; idx < K * NG; idx += blockDim.x) {
         const int k = idx / NG, n = idx % NG;
-        const int f = g * FG + n % FG, kind = n / FG;   // columns: Re of the 32 frames, then Im
+        const int f = g * FG + n % FG, kind = n / FG;   // columns: Re of the FG frames, then Im
         float v = 0.f;
         const short kt = ktab[k];
         if (f < F && kt >= 0) {
@@ -175,7 +182,7 @@ prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, 
 // One K step of 16 is one element block: 8 columns pairing with Re c, then 8
 // pairing with Im c (LBO = BLK_BYTES).
 //
-// One CTA per (depth row j, group of 32 frames); warp-specialised, with no
+// One CTA per (depth row j, group of FG frames); warp-specialised, with no
 // CTA-wide barrier inside the bin loop:
 //   warp 0: bulk copies of each bin's B tile and c words into a ring of NST
 //     stages;
@@ -185,7 +192,7 @@ prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, 
 //     tensor core finishes in about 48 cycles each;
 //   warps 4-11: build the Toeplitz blocks of bin b+1, then fold the
 //     accumulators of bin b into per-pixel sums. Warp w reads tensor-memory
-//     lane quarter w % 4 (pixels 32 (w%4) .. +31) for frames 16 ((w-4)/4) .. +15.
+//     lane quarter w % 4 (pixels 32 (w%4) .. +31) for frames FG/2 ((w-4)/4) .. +FG/2-1.
 // The issuing warps have the lowest warp numbers: while the build/fold warps
 // issue FMAs back to back, the schedulers favour them, and MMA issue is on
 // the critical path.
@@ -197,7 +204,6 @@ prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, 
 // status word, each role drains the copies or MMAs it issued, and the CTA exits.
 constexpr int BLK_BYTES = 32 * 128;       // 32 core matrices of one part (Re or Im)
 constexpr int A_BYTES = 2 * BLK_BYTES;    // Re and Im
-constexpr int FW = FG / 2;                // frames per compute warp
 constexpr int MAX_NST = 4;
 constexpr size_t GEMM_SMEM_LIMIT = 232448;  // opt-in shared memory per CTA
 constexpr size_t GEMM_SMEM_EXTRA = 24 * 8 + 16;
@@ -208,19 +214,19 @@ static_assert(2 * 128 * REG_FOLD + 128 * REG_CTRL <= 384 * REG_LAUNCH, "register
 
 // Shared memory of one pipeline stage: NPART x (A blocks, B tile, c words);
 // a CTA of a pair holds half of the B tile.
-__host__ __device__ constexpr size_t gemm_stage_bytes(int K, int npart, bool pair = false)
+__host__ __device__ constexpr size_t gemm_stage_bytes(int K, int npart, bool pair, int fg)
 {
-    return (size_t)npart * (A_BYTES + (size_t)K * (pair ? NG / 2 : NG) * 2 + NXP * 4);
+    return (size_t)npart * (A_BYTES + (size_t)K * (pair ? fg : 2 * fg) * 2 + NXP * 4);
 }
-int gemm_stages(int K, bool split, bool pair = false)
+int gemm_stages(int K, bool split, bool pair, int fg)
 {
-    const size_t st = gemm_stage_bytes(K, split ? 2 : 1, pair);
+    const size_t st = gemm_stage_bytes(K, split ? 2 : 1, pair, fg);
     const size_t n = (GEMM_SMEM_LIMIT - GEMM_SMEM_EXTRA) / st;
     return (int)(n < MAX_NST ? n : MAX_NST);
 }
-size_t gemm_smem(int K, bool split, bool pair = false)
+size_t gemm_smem(int K, bool split, bool pair, int fg)
 {
-    return gemm_stages(K, split, pair) * gemm_stage_bytes(K, split ? 2 : 1, pair) + GEMM_SMEM_EXTRA;
+    return gemm_stages(K, split, pair, fg) * gemm_stage_bytes(K, split ? 2 : 1, pair, fg) + GEMM_SMEM_EXTRA;
 }
 
 // steps: element block of K step st in bits 4 (st % 16) of steps[st / 16].
@@ -235,7 +241,7 @@ size_t gemm_smem(int K, bool split, bool pair = false)
 // memory. Both CTAs' build and fold warps arrive on rank 0's go barriers; the
 // MMA commits arrive on the stage and accumulator barriers of both CTAs. Each
 // SM thus stages and reads half of B.
-template <int NAP, bool FP16, bool SPLIT, bool BANDS = false, bool PAIR = false>
+template <int NAP, bool FP16, bool SPLIT, bool BANDS = false, bool PAIR = false, int FG = 32>
 __global__ void __launch_bounds__(gemm_threads<NAP>(), 1)
 prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ clo, const uint8_t *__restrict__ Bhi,
                  const uint8_t *__restrict__ Blo, ulonglong2 steps, int4 kq, int n_bins, int nz, int F, int NST,
@@ -245,6 +251,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
     static_assert(!(BANDS && PAIR), "the band form runs unpaired");
     constexpr int NACC = BANDS ? 1 : (NAP == 2 ? 3 : 6);
     constexpr int NPART = SPLIT ? 2 : 1;
+    constexpr int NG = Grp<FG>::NG, FW = Grp<FG>::FW;
     constexpr int ACC_COLS = NAP * NG;
     constexpr int NGC = PAIR ? NG / 2 : NG;      // B columns in this CTA's shared memory
     constexpr int CS_BC = NGC / 8 * 128;         // bytes between K chunks of this CTA's B
@@ -252,7 +259,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
     static_assert(2 * ACC_COLS <= 512, "two accumulator sets must fit in tensor memory");
     extern __shared__ __align__(1024) uint8_t sm[];
     const size_t bytesB = (size_t)K_of(kq) * NGC * 2;   // this CTA's part of one B tile
-    const size_t stage = gemm_stage_bytes(K_of(kq), NPART, PAIR);
+    const size_t stage = gemm_stage_bytes(K_of(kq), NPART, PAIR, FG);
     auto sA = [&](int s) { return sm + s * stage; };
     auto sB = [&](int s) { return sm + s * stage + NPART * A_BYTES; };
     auto sC = [&](int s) { return reinterpret_cast<uint32_t *>(sm + s * stage + NPART * (A_BYTES + bytesB)); };
@@ -308,8 +315,9 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
     // copy / MMA warpgroup (warps 0-3) drops to REG_CTRL, the two build/fold warpgroups rise
     // to REG_FOLD (2 x 128 x REG_FOLD + 128 x REG_CTRL <= 64512). The host checks
     // that the kernel was built with 168 registers per thread before launching.
-    // The band form keeps one sum per pixel and frame and needs no split.
-    if constexpr (!BANDS) {
+    // The band form keeps one sum per pixel and frame, and 16 frames per CTA
+    // half the fold's sums: neither needs the split.
+    if constexpr (!BANDS && FG == 32) {
         if (warp < 4)
             asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(REG_CTRL));
         else
@@ -465,11 +473,11 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
             const int t = b & 1;
             if (!wait(&afull[t], (unsigned)(b >> 1) & 1u)) return false;
             tc_fence_after();
-            // columns of aperture q: Re of frames 0..31, then Im of frames 0..31
+            // columns of aperture q: Re of frames 0..FG-1, then Im of frames 0..FG-1
             const unsigned base = tmem + ((unsigned)(32 * quarter) << 16) + (unsigned)(t * ACC_COLS + fh * FW);
             // four frames at a time, so that the loaded values take 24 registers
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
+            for (int h = 0; h < FW / 4; ++h) {
                 float re[NAP][4], im[NAP][4];
 #pragma unroll
                 for (int q = 0; q < NAP; ++q) {
@@ -477,7 +485,7 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
                     tmem_ld4(base + (unsigned)(q * NG + FG + 4 * h), im[q]);
                 }
                 tmem_wait_ld();
-                if (h == 3) {
+                if (h == FW / 4 - 1) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) go_arrive(t);   // set t is free for bin b + 2
@@ -590,18 +598,18 @@ ulonglong2 gemm_steps(const pam_plan_s &p)
     return steps;
 }
 
-template <int NAP, bool FP16, bool SPLIT, bool PAIR>
+template <int NAP, bool FP16, bool SPLIT, bool PAIR, int FG>
 cudaError_t launch_gemm_t(const pam_plan_s &p, int n_frames, cudaStream_t st)
 {
     const int groups = (n_frames + FG - 1) / FG;
     const int4 kq = make_int4(p.kq[0], p.kq[1], p.kq[2], p.kq[3]);
-    const int nst = gemm_stages(p.K, SPLIT, PAIR);
+    const int nst = gemm_stages(p.K, SPLIT, PAIR, FG);
     if (nst < 2 || p.K / 16 > 32) return cudaErrorInvalidConfiguration;
     const ulonglong2 steps = gemm_steps(p);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(PAIR ? (p.nz + 1) & ~1 : p.nz, groups);   // pairs of rows: an even grid
     cfg.blockDim = dim3(gemm_threads<NAP>());
-    cfg.dynamicSmemBytes = gemm_smem(p.K, SPLIT, PAIR);
+    cfg.dynamicSmemBytes = gemm_smem(p.K, SPLIT, PAIR, FG);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     if (PAIR) {
@@ -612,7 +620,7 @@ cudaError_t launch_gemm_t(const pam_plan_s &p, int n_frames, cudaStream_t st)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    cudaError_t e = cudaLaunchKernelEx(&cfg, prec_gemm_kernel<NAP, FP16, SPLIT, false, PAIR>, p.t.c_hi, p.t.c_lo,
+    cudaError_t e = cudaLaunchKernelEx(&cfg, prec_gemm_kernel<NAP, FP16, SPLIT, false, PAIR, FG>, p.t.c_hi, p.t.c_lo,
                                        reinterpret_cast<const uint8_t *>(p.w.Bhi),
                                        reinterpret_cast<const uint8_t *>(p.w.Blo), steps, kq, p.n_bins, p.nz, n_frames,
                                        nst, p.w.smax, p.w.part, p.w.status, 0);
@@ -629,18 +637,32 @@ cudaError_t launch_bands_form(const pam_plan_s &p, const float2 *S, int n_frames
     if (e != cudaSuccess) return e;
     prec_smax_kernel<<<dim3(p.n_bins, n_frames), 128, 0, st>>>(S, p.n_bins, p.ne, p.w.smax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    constexpr int FG = 32;
     const int groups = (n_frames + FG - 1) / FG;
-    prec_bprep_kernel<FP16, false, false><<<dim3(p.n_bins, groups), 256, 0, st>>>(
+    prec_bprep_kernel<FP16, false, false, FG><<<dim3(p.n_bins, groups), 256, 0, st>>>(
         S, p.t.ktab, p.t.kwgt, p.K, p.n_bins, p.ne, n_frames, p.w.smax, reinterpret_cast<uint8_t *>(p.w.Bhi),
         nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (gemm_stages(p.K, false) < 2 || p.K / 16 > 32) return cudaErrorInvalidConfiguration;
+    if (gemm_stages(p.K, false, false, FG) < 2 || p.K / 16 > 32) return cudaErrorInvalidConfiguration;
     const int4 kq = make_int4(p.kq[0], p.kq[1], p.kq[2], p.kq[3]);
     const ulonglong2 steps = gemm_steps(p);
-    prec_gemm_kernel<3, FP16, false, true><<<dim3(p.nz, groups), gemm_threads<3>(), gemm_smem(p.K, false), st>>>(
+    prec_gemm_kernel<3, FP16, false, true><<<dim3(p.nz, groups), gemm_threads<3>(), gemm_smem(p.K, false, false, FG), st>>>(
         p.t.c_hi, nullptr, reinterpret_cast<const uint8_t *>(p.w.Bhi), nullptr, steps, kq, p.n_bins, p.nz, n_frames,
-        gemm_stages(p.K, false), p.w.smax, bands, p.w.status, n_bands);
+        gemm_stages(p.K, false, false, FG), p.w.smax, bands, p.w.status, n_bands);
     return cudaGetLastError();
+}
+
+template <bool FP16, bool SPLIT, bool PAIR, int FG>
+cudaError_t launch_form_t(const pam_plan_s &p, int n_frames, cudaStream_t st)
+{
+    const int groups = (n_frames + FG - 1) / FG;
+    prec_bprep_kernel<FP16, SPLIT, PAIR, FG><<<dim3(p.n_bins, groups), 256, 0, st>>>(
+        p.w.S, p.t.ktab, p.t.kwgt, p.K, p.n_bins, p.ne, n_frames, p.w.smax, reinterpret_cast<uint8_t *>(p.w.Bhi),
+        reinterpret_cast<uint8_t *>(p.w.Blo));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return p.n_apod == 2 ? launch_gemm_t<2, FP16, SPLIT, PAIR, FG>(p, n_frames, st)
+                         : launch_gemm_t<3, FP16, SPLIT, PAIR, FG>(p, n_frames, st);
 }
 
 template <bool FP16, bool SPLIT>
@@ -650,31 +672,25 @@ cudaError_t launch_form(const pam_plan_s &p, int n_frames, cudaStream_t st)
     if (e != cudaSuccess) return e;
     prec_smax_kernel<<<dim3(p.n_bins, n_frames), 128, 0, st>>>(p.w.S, p.n_bins, p.ne, p.w.smax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int groups = (n_frames + FG - 1) / FG;
-    const bool pair = p.gemm_m == 256;
-    auto bprep = pair ? prec_bprep_kernel<FP16, SPLIT, true> : prec_bprep_kernel<FP16, SPLIT, false>;
-    bprep<<<dim3(p.n_bins, groups), 256, 0, st>>>(p.w.S, p.t.ktab, p.t.kwgt, p.K, p.n_bins, p.ne, n_frames, p.w.smax,
-                                                 reinterpret_cast<uint8_t *>(p.w.Bhi),
-                                                 reinterpret_cast<uint8_t *>(p.w.Blo));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const bool pair = p.gemm_m == 256, f16 = p.gemm_frames == 16;
     if (pair)
-        return p.n_apod == 2 ? launch_gemm_t<2, FP16, SPLIT, true>(p, n_frames, st)
-                             : launch_gemm_t<3, FP16, SPLIT, true>(p, n_frames, st);
-    return p.n_apod == 2 ? launch_gemm_t<2, FP16, SPLIT, false>(p, n_frames, st)
-                         : launch_gemm_t<3, FP16, SPLIT, false>(p, n_frames, st);
+        return f16 ? launch_form_t<FP16, SPLIT, true, 16>(p, n_frames, st)
+                   : launch_form_t<FP16, SPLIT, true, 32>(p, n_frames, st);
+    return f16 ? launch_form_t<FP16, SPLIT, false, 16>(p, n_frames, st)
+               : launch_form_t<FP16, SPLIT, false, 32>(p, n_frames, st);
 }
 
-template <int NAP, bool FP16, bool SPLIT, bool BANDS = false, bool PAIR = false>
+template <int NAP, bool FP16, bool SPLIT, bool BANDS = false, bool PAIR = false, int FG = 32>
 cudaError_t set_gemm_smem_one()
 {
     static_assert(MAX_NST >= 2, "the copy ring needs two stages");
-    cudaError_t e = cudaFuncSetAttribute(prec_gemm_kernel<NAP, FP16, SPLIT, BANDS, PAIR>,
+    cudaError_t e = cudaFuncSetAttribute(prec_gemm_kernel<NAP, FP16, SPLIT, BANDS, PAIR, FG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM_LIMIT);
-    if (e != cudaSuccess || BANDS) return e;
+    if (e != cudaSuccess || BANDS || FG != 32) return e;
     // The register split (setmaxnreg) is sized for a launch of exactly REG_LAUNCH
     // registers per thread; with fewer, the increase could never be granted.
     cudaFuncAttributes a;
-    if ((e = cudaFuncGetAttributes(&a, prec_gemm_kernel<NAP, FP16, SPLIT, BANDS, PAIR>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&a, prec_gemm_kernel<NAP, FP16, SPLIT, BANDS, PAIR, FG>)) != cudaSuccess) return e;
     return a.numRegs == REG_LAUNCH ? cudaSuccess : cudaErrorInvalidConfiguration;
 }
 
@@ -683,7 +699,9 @@ cudaError_t set_gemm_smem()
 {
     cudaError_t e = set_gemm_smem_one<NAP, FP16, SPLIT, BANDS, false>();
     if (e != cudaSuccess || BANDS) return e;
-    return set_gemm_smem_one<NAP, FP16, SPLIT, false, true>();
+    if ((e = set_gemm_smem_one<NAP, FP16, SPLIT, false, true>()) != cudaSuccess) return e;
+    if ((e = set_gemm_smem_one<NAP, FP16, SPLIT, false, false, 16>()) != cudaSuccess) return e;
+    return set_gemm_smem_one<NAP, FP16, SPLIT, false, true, 16>();
 }
 
 }  // namespace

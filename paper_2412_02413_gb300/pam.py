@@ -67,6 +67,7 @@ _SIGS = {
     "pam_plan_set_fft_radix": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_plan_set_gemm_tile": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_plan_set_lane_rows": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "pam_plan_set_gemm_frames": (ctypes.c_int, [_VP, ctypes.c_int]),
     "pam_as_backprop": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
     "pam_as_tax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
     "pam_as_dax": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP, _VP, _VP, _VP, _VP]),
@@ -368,6 +369,10 @@ class Plan:
     def set_fft_radix(self, radix: int = 8):
         """Largest radix of the time FFT's stages (4 or 8)."""
         _check(load().pam_plan_set_fft_radix(self._h, int(radix)))
+
+    def set_gemm_frames(self, frames: int = 32):
+        """Frames per CTA of the tensor-core form (32 or 16; identical results)."""
+        _check(load().pam_plan_set_gemm_frames(self._h, int(frames)))
 
     def set_lane_rows(self, rows: int = 1):
         """Depth rows per lane of the fused kernel (1 or 2; bit-identical results)."""

@@ -152,3 +152,27 @@ def test_tune_lane_rows_applies_to_every_plan(tmp_path, monkeypatch):
     assert autotune.tune_lane_rows(t, plans, RF()) == 2
     assert [p.rows for p in plans] == [2, 2]
     assert t.lookup("lane_rows:ne128:nt4096:nz512:F1") == 2
+
+
+def test_tune_gemm_frames_applies_the_fastest(tmp_path, monkeypatch):
+    class FakePlan:
+        n_elem, n_samples, nz = 128, 4096, 512
+        fr = None
+
+        def set_gemm_frames(self, f):
+            self.fr = f
+
+        def as_tax(self, rf, outs=None):
+            pass
+
+    class RF:
+        shape = (8, 128, 4096)
+
+        def dim(self):
+            return 3
+
+    plan = FakePlan()
+    monkeypatch.setattr(autotune, "_event_timer", lambda call, warmup=1, iters=3: {32: 1.0, 16: 0.6}[plan.fr])
+    t = autotune.Autotuner(str(tmp_path / "db.json"))
+    assert autotune.tune_gemm_frames(t, plan, RF(), "bf16") == 16 and plan.fr == 16
+    assert t.lookup("gemm_frames_bf16:ne128:nt4096:nz512:F8") == 16

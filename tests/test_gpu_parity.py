@@ -596,21 +596,27 @@ def test_gemm_form_rejects_unsupported():
 @pytest.mark.parametrize("form", ["bf16", "fp16split"])
 def test_gemm_tile_pairs_match_single_rows(form):
     """The 2-CTA tile (M = 256, cta_group::2: one MMA covers two depth rows)
-    sums the same products in the same order as one CTA per row, so the maps
-    are bit-identical; 23 rows leave the last pair with one row, and 20 frames
-    make a ragged second frame group."""
+    and 16 frames per CTA (N = 32) sum the same products in the same order as
+    one CTA per row with 32 frames, so the maps are bit-identical; 23 rows
+    leave the last pair with one row, and 20 frames make a ragged last frame
+    group (of 16 and of 32)."""
     w = _tiny(128, 512, 23, bins=12, fs=40e6, f_lo=1e6, f_hi=8e6, pattern_m=16)
     frames = torch.from_numpy(synth.random_rf(128, 512, seed=35, n_frames=20)).cuda()
     plan = _plan(w, max_frames=20, form=form)
     kw = dict(rho_n=True, rho_pairs=True, image_as=True)
     plan.set_gemm_tile(128)
+    plan.set_gemm_frames(32)
     one = {k: v.clone() for k, v in plan.as_tax(frames, **kw).items()}
-    plan.set_gemm_tile(256)
-    two = plan.as_tax(frames, **kw)
-    torch.cuda.synchronize()
-    for k in one:
-        assert torch.equal(one[k], two[k]), k
+    for m, fg in ((256, 32), (128, 16), (256, 16)):
+        plan.set_gemm_tile(m)
+        plan.set_gemm_frames(fg)
+        two = plan.as_tax(frames, **kw)
+        torch.cuda.synchronize()
+        for k in one:
+            assert torch.equal(one[k], two[k]), (m, fg, k)
     orc = oracle.as_tax(_geom(w), frames[19].cpu().numpy(), oracle.pattern(128, 3, 16))
     assert rel_l2(two["image_as"][19].cpu().numpy(), orc["image_as"]) <= FORM_TOL[form][0]
     with pytest.raises(_pam().PamError):
         plan.set_gemm_tile(64)
+    with pytest.raises(_pam().PamError):
+        plan.set_gemm_frames(8)
