@@ -738,8 +738,8 @@ def run_ours(args):
                     "blocking_value": e2e_blocking},
             "gpu_launches": int(launches),
             "avg_launch_us_alone": alone_launch_s * 1e6,
-            "roofline": {"bound": "alu", "kernel": "prop_seg_kernel<3,128> (fused propagate + inverse lateral FFT "
-                                                   "+ cross-spectra)",
+            "roofline": {"bound": "alu", "kernel": f"prop_seg_kernel<3,128,{int(lane_rows_choice)}> (fused propagate + "
+                                                   "inverse lateral FFT + cross-spectra; rows per lane)",
                          "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
                          "traffic": traffic,
                          "peak_basis": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "

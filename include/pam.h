@@ -181,9 +181,13 @@ pam_status pam_plan_set_fft_radix(pam_plan_t p, int radix);
 
 /* Depth rows per lane of the plain path's fused kernel when it takes the
  * whole (frame, row tile, bin) sequence in one wave (the default split): 1
- * (16 warps per CTA) or 2 (8 warps, each lane computing two rows of the same
- * pixels, so that each load of the staged spectra and phase words serves
- * both). The arithmetic of a row is the same either way, so the results are
+ * (16 warps per CTA) or 2 (the default; each lane computing two rows of the same pixels,
+ * so that each load of the staged spectra and phase words serves both; 12
+ * warps for nx >= 64, which hold 1.5x the work in flight and cover 1.5x the
+ * rows per CTA, and 8 warps below). The arithmetic of a row is the same
+ * either way. For nx >= 64 the larger row tiles divide the bins among the
+ * CTAs differently, so the sums are grouped differently and the maps agree to
+ * rounding; with one CTA (pam_plan_set_grid(p, 1)) or nx < 64 they are
  * bit-identical. PAM_ERR_INVALID_ARG for other values. */
 pam_status pam_plan_set_lane_rows(pam_plan_t p, int rows);
 

@@ -151,8 +151,8 @@ def tune_time_fft_radix(tuner: Autotuner, plans, rf, force: bool = False):
 
 def tune_lane_rows(tuner: Autotuner, plans, rf, force: bool = False):
     """Best depth rows per lane (1 or 2) of the fused kernel for
-    ``plans[0].as_tax(rf)``; applied to every plan of ``plans``. The two give
-    bit-identical results."""
+    ``plans[0].as_tax(rf)``; applied to every plan of ``plans``. The two agree
+    to rounding (the sums over bins are grouped by row tile)."""
     plan = plans[0]
     F = rf.shape[0] if rf.dim() == 3 else 1
     key = make_key("lane_rows", plan.n_elem, plan.n_samples, plan.nz, F)

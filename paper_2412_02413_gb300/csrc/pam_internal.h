@@ -120,7 +120,7 @@ struct pam_plan_s {
     int split_override = 0;            // pam_plan_set_split (0 = automatic)
     int grid_override = 0;             // pam_plan_set_grid (0 = every SM)
     int fft_radix = 8;                 // pam_plan_set_fft_radix: largest radix of the time FFT's stages (4 or 8)
-    int lane_rows = 1;                 // pam_plan_set_lane_rows: depth rows per lane of the fused kernel (1 or 2)
+    int lane_rows = 2;                 // pam_plan_set_lane_rows: depth rows per lane of the fused kernel (1 or 2)
     int gemm_m = 128;                  // pam_plan_set_gemm_tile: M of the tensor-core form's MMA (128 or 256)
     int gemm_frames = 32;              // pam_plan_set_gemm_frames: frames per CTA of the tensor-core form (32 or 16)
     bool seg_ok = false;               // Workspace::part holds prop_seg_part_floats (even division of small batches)

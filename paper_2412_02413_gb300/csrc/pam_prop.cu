@@ -34,10 +34,17 @@ namespace {
 constexpr int PROP_WARPS = 16;
 constexpr int PROP_THREADS = 32 * PROP_WARPS;
 // Depth rows per lane (RPL) of a fused kernel: 1 with PROP_WARPS warps of up
-// to 128 registers, or 2 with half as many warps of up to 255, where a lane
-// takes two rows of the same pixels and every spectra and phase-word load
-// from shared memory serves both. A CTA covers the same rows either way.
-constexpr int prop_warps(int rpl) { return PROP_WARPS / rpl; }
+// to 128 registers, or 2 with 12 warps of up to 168, where a lane takes two
+// rows of the same pixels and every spectra and phase-word load from shared
+// memory serves both. Two rows need 163 registers per thread, so 12 warps of
+// them hold 1.5x the work in flight of 16 warps of one row in the same
+// register file, and a CTA covers 1.5x the rows. Below nx = 64 the transposes
+// of 12 such warps do not fit in shared memory, and 8 warps cover the rows of
+// 16 warps of one row.
+constexpr int prop_warps(int rpl, int nx) { return rpl == 1 ? PROP_WARPS : (nx >= 64 ? 12 : 8); }
+// Bins in flight per CTA: 4, or 3 where 12 warps' transposes leave room for
+// no more.
+constexpr int prop_nstage(int rpl, int nx) { return prop_warps(rpl, nx) == 12 ? 3 : 4; }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
@@ -111,7 +118,6 @@ __device__ __forceinline__ float2 phase_cis(unsigned w)
 
 using namespace ptx;
 
-constexpr int NSTAGE = 4;       // bins in flight per CTA
 // One CTA per SM (16 warps, up to 128 registers each): with two, the warp
 // scheduler favours the older CTA, which then finishes its share early and
 // leaves the other running at half occupancy.
@@ -122,7 +128,7 @@ template <int NX, int RPL = 1> struct Shape {
     static constexpr int L2 = H / 8;               // lanes per half row
     static constexpr int LPR = 2 * L2;             // lanes per row
     static constexpr int RPW = 32 / LPR * RPL;     // rows per warp
-    static constexpr int RPC = prop_warps(RPL) * RPW;   // rows per CTA (independent of RPL)
+    static constexpr int RPC = prop_warps(RPL, NX) * RPW;   // rows per CTA
     static constexpr int KPL = 8 / L2;             // second-stage DFTs per lane
     // Transpose regions per (aperture, row, half): 8 rows k1 x L2 columns, each
     // row padded by one float2 so that the stores of one k1 and the loads of
@@ -138,11 +144,11 @@ template <int NAP> struct Acc { static constexpr int N = NAP == 1 ? 1 : (NAP == 
 
 // Tensor-memory columns of one CTA: the PROP_WARPS / 4 warps of each lane
 // quadrant (w, w + 4, ...) hold 8 pixels x NACC sums per lane each, at columns
-// [a][o] (a power of 2 of at least 32 columns is allocated). With two rows
-// per lane, half as many warps hold twice the columns: the same total.
-template <int NAP> constexpr unsigned tmem_cols()
+// [a][o] (a power of 2 of at least 32 columns is allocated); with two rows
+// per lane, twice the columns per warp.
+template <int NAP, int RPL = 1, int NX = 128> constexpr unsigned tmem_cols()
 {
-    constexpr unsigned need = (unsigned)(PROP_WARPS / 4) * 8u * (unsigned)Acc<NAP>::N;
+    constexpr unsigned need = (unsigned)(prop_warps(RPL, NX) / 4) * (unsigned)RPL * 8u * (unsigned)Acc<NAP>::N;
     return need <= 32u ? 32u : need <= 64u ? 64u : need <= 128u ? 128u : need <= 256u ? 256u : 512u;
 }
 
@@ -150,11 +156,12 @@ template <int NAP, int NX, int RPL = 1>
 constexpr size_t prop_smem_bytes()
 {
     using S = Shape<NX, RPL>;
+    constexpr int NSTAGE = prop_nstage(RPL, NX);
     return (size_t)128                                    // full / empty mbarriers
            + (size_t)NSTAGE * 2 * NAP * NX * sizeof(float2)   // paired spectra, one per stage
            + (size_t)NSTAGE * NX * sizeof(uint4)          // phase words + evanescent coefficients
            + (size_t)(NX / 2) * sizeof(float2)            // exp(+2 pi i m / (nx/2))
-           + (size_t)prop_warps(RPL) * NAP * S::RPW * 2 * S::RS * sizeof(float2);  // transposes
+           + (size_t)prop_warps(RPL, NX) * NAP * S::RPW * 2 * S::RS * sizeof(float2);  // transposes
 }
 
 // Eq. 4 (with the Appendix A completion) for one pixel and one pair:
@@ -307,56 +314,6 @@ __device__ __forceinline__ void acc_update(unsigned tcol, const float2 (&p)[NAP]
     }
 }
 
-// acc_update in two halves, so that the tensor-memory loads' latency overlaps
-// other work: acc_issue starts loading the thread's 8 x NACC sums of one row
-// (column layout of acc_update); after tmem_wait_ld(), acc_apply adds one
-// bin's fields p[q][o] to them, in acc_update's operation order, and stores
-// them back.
-template <int NAP>
-__device__ __forceinline__ void acc_issue(unsigned tcol, float (&v)[8 * Acc<NAP>::N])
-{
-    if constexpr (NAP == 1) {
-        tmem_ld8(tcol, v);
-    } else {
-        tmem_ld16(tcol, v);
-        if constexpr (NAP == 2) {
-            tmem_ld8(tcol + 16, v + 16);
-        } else {
-            tmem_ld16(tcol + 16, v + 16);
-            tmem_ld16(tcol + 32, v + 32);
-        }
-    }
-}
-template <int NAP>
-__device__ __forceinline__ void acc_apply(unsigned tcol, float (&v)[8 * Acc<NAP>::N], const float2 (&p)[NAP][8])
-{
-#pragma unroll
-    for (int c = 0; c < Acc<NAP>::N; ++c) tmem_pin8(v + 8 * c);
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-        v[o] = add_norm(v[o], p[0][o]);
-        if constexpr (NAP >= 2) v[8 + o] = add_norm(v[8 + o], p[1][o]);
-        if constexpr (NAP == 2) v[16 + o] = add_dot(v[16 + o], p[0][o], p[1][o]);
-        if constexpr (NAP == 3) {
-            v[16 + o] = add_norm(v[16 + o], p[2][o]);
-            v[24 + o] = add_dot(v[24 + o], p[0][o], p[1][o]);
-            v[32 + o] = add_dot(v[32 + o], p[1][o], p[2][o]);
-            v[40 + o] = add_dot(v[40 + o], p[2][o], p[0][o]);
-        }
-    }
-    if constexpr (NAP == 1) {
-        tmem_st8(tcol, v);
-    } else {
-        tmem_st16(tcol, v);
-        if constexpr (NAP == 2) {
-            tmem_st8(tcol + 16, v + 16);
-        } else {
-            tmem_st16(tcol + 16, v + 16);
-            tmem_st16(tcol + 32, v + 32);
-        }
-    }
-}
-
 // The sums of the thread's 8 pixels, acc[o][a], back in registers.
 template <int NAP>
 __device__ __forceinline__ void acc_read(unsigned tcol, float (&acc)[8][Acc<NAP>::N])
@@ -376,6 +333,7 @@ __device__ __forceinline__ void acc_read(unsigned tcol, float (&acc)[8][Acc<NAP>
 // Shared-memory regions of the fused kernel (layout of prop_smem_bytes).
 template <int NAP, int NX, int RPL = 1>
 struct PropSmem {
+    static constexpr int NSTAGE = prop_nstage(RPL, NX);
     uint64_t *full;   // [NSTAGE] data of a stage has landed
     uint64_t *empty;  // [NSTAGE] all warps are done with a stage
     unsigned *tslot;  // tensor-memory base address of the CTA's sums
@@ -408,7 +366,7 @@ struct PropSmem {
         if (threadIdx.x == 0) {
             for (int st = 0; st < NSTAGE; ++st) {
                 mbar_init(&full[st], 1);
-                mbar_init(&empty[st], prop_warps(RPL));
+                mbar_init(&empty[st], prop_warps(RPL, NX));
             }
             mbar_fence_init();
         }
@@ -450,6 +408,7 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX, RPL> &sm, cons
     constexpr int RS = S::RS;
     constexpr int NOUT = KPL * L2;  // 8 pixels per lane
     constexpr int NACC = Acc<NAP>::N;
+    constexpr int NSTAGE = PropSmem<NAP, NX, RPL>::NSTAGE;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
     float2 *myT = sm.sT + (size_t)warp * (NAP * RPW * 2 * RS);
@@ -570,13 +529,6 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX, RPL> &sm, cons
 #pragma unroll
         for (int rr = 0; rr < RPL; ++rr) {
             const unsigned tcol_r = tcol + (unsigned)(rr * 8 * NACC);
-            // Two rows per lane leave the registers to start loading the row's
-            // sums before its second factor, which then hides their latency.
-            float v[8 * NACC];
-            if constexpr (RPL > 1) {
-                if (rr == 0) tmem_wait_st();   // the previous bin's stores have landed
-                acc_issue<NAP>(tcol_r, v);
-            }
             float2 p[NAP][NOUT];
 #pragma unroll
             for (int q = 0; q < NAP; ++q) {
@@ -604,12 +556,7 @@ __device__ __forceinline__ bool prop_bins(const PropSmem<NAP, NX, RPL> &sm, cons
             }
 
             // per-pixel sums over the bins
-            if constexpr (RPL > 1) {
-                tmem_wait_ld();
-                acc_apply<NAP>(tcol_r, v, p);
-            } else {
-                acc_update<NAP>(tcol_r, p);
-            }
+            acc_update<NAP>(tcol_r, p);
             if constexpr (FIELDS) {
                 if (row_ok) {  // fields of bin b
                     float2 *dst = fields_row + (size_t)b * bin_stride;
@@ -756,7 +703,7 @@ __host__ __device__ __forceinline__ long long seg_slot(int c, long long tt, long
 // epi_reduce_seg_kernel adds a split tile's slots in CTA order. The staging
 // ring carries over from segment to segment.
 template <int NAP, int NX, int RPL>
-__global__ void __launch_bounds__(32 * prop_warps(RPL), PROP_CTAS)
+__global__ void __launch_bounds__(32 * prop_warps(RPL, NX), PROP_CTAS)
 prop_seg_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase, const int *__restrict__ bin_evan,
                 int n_bins, int nz, int tiles, float z0f, float dzf, long long W, float *__restrict__ part,
                 EpiOut out)
@@ -765,13 +712,13 @@ prop_seg_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase, c
     constexpr int L2 = S::L2, LPR = S::LPR, RPW = S::RPW, RPC = S::RPC, KPL = S::KPL;
     constexpr int NACC = Acc<NAP>::N;
     constexpr int NOUT = KPL * L2;
-    constexpr int NT = 32 * prop_warps(RPL);
+    constexpr int NT = 32 * prop_warps(RPL, NX);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const PropSmem<NAP, NX, RPL> sm(smem_raw);
     __shared__ float wmax[NT / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
-    const unsigned tbase = sm.init(tmem_cols<NAP>());
+    const unsigned tbase = sm.init(tmem_cols<NAP, RPL, NX>());
     const unsigned tcol = acc_tcol(tbase, warp, NACC, RPL);
     const int G = gridDim.x, c = blockIdx.x;
     long long w = (long long)c * W / G;
@@ -830,7 +777,7 @@ prop_seg_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase, c
             if (nb == n_bins) block_max_to(rmax, out.fmax + f, wmax, NT);
         w += nb;
     }
-    sm.release(tbase, tmem_cols<NAP>());
+    sm.release(tbase, tmem_cols<NAP, RPL, NX>());
 }
 
 // --------------------------------------------------------- epilogue ----
@@ -1062,10 +1009,11 @@ template <int NAP, int NX, int RPL>
 cudaError_t launch_seg_rt(const pam_plan_s &p, int n_frames, const EpiOut &out, cudaStream_t st)
 {
     using S = Shape<NX, RPL>;
+    static_assert(prop_smem_bytes<NAP, NX, RPL>() + 1024 <= 232448, "shared memory of the fused kernel");
     const int tiles = (p.nz + S::RPC - 1) / S::RPC;
     const long long W = (long long)n_frames * tiles * p.n_bins;
     const int G = prop_seg_ctas(p, n_frames);
-    prop_seg_kernel<NAP, NX, RPL><<<G, 32 * prop_warps(RPL), prop_smem_bytes<NAP, NX, RPL>(), st>>>(
+    prop_seg_kernel<NAP, NX, RPL><<<G, 32 * prop_warps(RPL, NX), prop_smem_bytes<NAP, NX, RPL>(), st>>>(
         p.w.Q, p.t.phase, p.t.bin_evan, p.n_bins, p.nz, tiles, (float)p.d.z0_m, (float)p.d.dz_m, W, p.w.part, out);
     return cudaGetLastError();
 }
@@ -1192,6 +1140,12 @@ cudaError_t launch_expire_wait(int *status, cudaStream_t st)
 
 int prop_rows_per_cta(int nx) { return PROP_WARPS * (32 / (nx / 8)); }
 
+// Rows per CTA of prop_seg_kernel for the plan's rows per lane.
+static int seg_rows(const pam_plan_s &p)
+{
+    return p.lane_rows == 2 ? prop_warps(2, p.nx) * 2 * (32 / (p.nx / 8)) : prop_rows_per_cta(p.nx);
+}
+
 int prop_ctas_per_sm() { return PROP_CTAS; }
 
 bool prop_uses_cluster(int n_split) { return n_split <= kMaxClusterSplit; }
@@ -1204,7 +1158,7 @@ bool prop_seg_mode(const pam_plan_s &p, int n_split, bool fields)
 
 int prop_seg_ctas(const pam_plan_s &p, int n_frames)
 {
-    const int rows = prop_rows_per_cta(p.nx);
+    const int rows = seg_rows(p);
     const long long W = (long long)n_frames * ((p.nz + rows - 1) / rows) * p.n_bins;
     long long G = (long long)PROP_CTAS * p.num_sms;
     if (p.grid_override > 0 && p.grid_override < G) G = p.grid_override;
@@ -1213,7 +1167,9 @@ int prop_seg_ctas(const pam_plan_s &p, int n_frames)
 
 size_t prop_seg_part_floats(const pam_plan_s &p)
 {
-    const int rows = prop_rows_per_cta(p.nx);
+    // the larger row tile of the two rows-per-lane settings, which can change after the plan is made
+    const int r1 = prop_rows_per_cta(p.nx), r2 = prop_warps(2, p.nx) * 2 * (32 / (p.nx / 8));
+    const int rows = r1 > r2 ? r1 : r2;
     return (size_t)2 * PROP_CTAS * p.num_sms * n_acc(p.n_apod) * rows * p.nx;
 }
 
@@ -1260,7 +1216,7 @@ cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_s
     dim3 grid((npix4 + EPI_THREADS - 1) / EPI_THREADS, n_frames);
     auto v4 = [](float *q) { return reinterpret_cast<float4 *>(q); };
     if (!from_partials && prop_seg_mode(p, n_split, fields)) {
-        const int rows = prop_rows_per_cta(p.nx);
+        const int rows = seg_rows(p);
         const int tiles = (p.nz + rows - 1) / rows;
         const long long W = (long long)n_frames * tiles * p.n_bins;
         const int G = prop_seg_ctas(p, n_frames);

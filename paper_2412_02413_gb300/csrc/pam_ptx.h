@@ -199,13 +199,6 @@ __device__ __forceinline__ void umma_commit_pair_elect(uint64_t *bar, unsigned s
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
-// Values loaded by tcgen05.ld are valid only after tmem_wait_ld(). Called
-// right after it, this empty statement claims to rewrite 8 of them, so that
-// no use of them can be scheduled ahead of the wait.
-__device__ __forceinline__ void tmem_pin8(float *v)
-{
-    asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]));
-}
 
 // Tensor-memory allocation by one whole warp: `ncols` (a power of 2, >= 32)
 // columns of all 128 lanes; the base address is written to shared memory at

@@ -374,8 +374,8 @@ class Plan:
         """Frames per CTA of the tensor-core form (32 or 16; identical results)."""
         _check(load().pam_plan_set_gemm_frames(self._h, int(frames)))
 
-    def set_lane_rows(self, rows: int = 1):
-        """Depth rows per lane of the fused kernel (1 or 2; bit-identical results)."""
+    def set_lane_rows(self, rows: int = 2):
+        """Depth rows per lane of the fused kernel (1 or 2; the maps agree to rounding)."""
         _check(load().pam_plan_set_lane_rows(self._h, int(rows)))
 
     def set_gemm_tile(self, m: int = 128):

@@ -174,33 +174,37 @@ def test_fused_grid_matches_oracle_and_is_deterministic(w2_frame, grid, lane_row
 @pytest.mark.parametrize("ne,nt,nz,nbins", [
     (16, 128, 300, None),   # nx 16: 256-row tiles, ragged
     (32, 256, 77, 20),      # nx 32
-    (64, 256, 70, 33),      # nx 64: 64-row tiles, ragged
-    (128, 512, 45, 17),     # nx 128: 32-row tiles, ragged
+    (64, 256, 70, 33),      # nx 64: 64-row tiles, 96 with two rows per lane
+    (128, 512, 45, 17),     # nx 128: 32-row tiles, 48 with two rows per lane
 ])
-def test_two_rows_per_lane_bit_identical(ne, nt, nz, nbins):
-    """Two depth rows per lane (8 warps) run each row's arithmetic exactly as
-    one row per lane (16 warps): AS, AS-DAX and AS-TAX maps are bit-identical,
-    over ragged row tiles, several frames and a split of the bins across CTAs,
-    and match the oracle."""
+def test_two_rows_per_lane_matches_one_row(ne, nt, nz, nbins):
+    """Two depth rows per lane run each row's arithmetic exactly as one row per
+    lane. With one CTA (every tile in one pass over the bins) the AS, AS-DAX
+    and AS-TAX maps are bit-identical; over the full grid, where the larger
+    row tiles of nx >= 64 group the bins' partial sums differently (bit-identical
+    below nx = 64), both match the oracle, over ragged tiles, several frames
+    and a split of the bins across CTAs."""
     w = _tiny(ne, nt, nz, bins=nbins, fs=40e6, pattern_m=max(2, ne // 8))
     frames = synth.random_rf(ne, nt, seed=60 + ne, n_frames=3)
     rf = torch.from_numpy(frames).cuda()
     for n_apod, call in ((3, "as_tax"), (2, "as_dax")):
         plan = _plan(w, n_apod=n_apod, max_frames=3)
-        for grid in (0, 5):
+        for grid in (1, 0, 5):
             plan.set_grid(grid)
             plan.set_lane_rows(1)
             one = {k: v.clone() for k, v in getattr(plan, call)(rf, rho_pairs=True, image_as=True).items()}
             plan.set_lane_rows(2)
             two = getattr(plan, call)(rf, rho_pairs=True, image_as=True)
             torch.cuda.synchronize()
-            for k in one:
-                assert torch.equal(one[k], two[k]), (n_apod, grid, k)
-        A = oracle.pattern(ne, n_apod, w.pattern_m)
-        orc = (oracle.as_tax if n_apod == 3 else oracle.as_xcorr)(_geom(w), frames[2], A)
-        compare_xcorr({k: v[2:3] for k, v in two.items()}, orc, check_peak=False)
+            if grid == 1 or ne < 64:
+                for k in one:
+                    assert torch.equal(one[k], two[k]), (n_apod, grid, k)
+            A = oracle.pattern(ne, n_apod, w.pattern_m)
+            orc = (oracle.as_tax if n_apod == 3 else oracle.as_xcorr)(_geom(w), frames[2], A)
+            compare_xcorr({k: v[2:3] for k, v in two.items()}, orc, check_peak=False)
         plan.close()
     plan = _plan(w, n_apod=1, max_frames=3)
+    plan.set_grid(1)
     plan.set_lane_rows(1)
     e1 = plan.as_backprop(rf).clone()
     plan.set_lane_rows(2)
