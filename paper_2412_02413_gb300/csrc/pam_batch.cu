@@ -244,6 +244,7 @@ struct pam_batch_s {
     pam_plan_s *base = nullptr;     // geometry, apodization, workspace for F frames of n_bins bins
     int F = 0, n_bins = 0, ne = 0, nx = 0, napq = 0, max_nt = 0, max_npix = 0, cpl = 4;
     int grid = 0, grid_override = 0, n_items = 0;
+    int rpl = 1;                     // depth rows per lane of the fused kernel (2 for nx >= 64)
     std::vector<int> nt, nz, nbf, bins_h;   // per frame: samples, rows, bin count; bins [F][n_bins]
     std::vector<size_t> rf_off, px_off;
     size_t rf_total = 0, px_total = 0;
@@ -335,7 +336,8 @@ pam_status enqueue(pam_batch_s *b, const float *rf, float *image, float *rho_n, 
     out.fmax = p.w.fmax;
     out.status = p.w.status;
     const int grid = b->grid_override > 0 ? std::min(b->grid_override, b->n_items) : b->grid;
-    e = pam::launch_prop_batch(b->nx, b->napq, grid, b->frames, b->items, b->n_items, b->counter, out, st);
+    e = pam::launch_prop_batch(b->nx, b->napq, grid, b->frames, b->items, b->n_items, b->counter, out, st, nullptr,
+                               b->rpl);
     if (e != cudaSuccess) return pam::cuda_fail(e, "propagate/correlate launch");
     e = pam::launch_normalize_batch(b->F, b->max_npix, b->frames, out, st);
     if (e != cudaSuccess) return pam::cuda_fail(e, "normalise launch");
@@ -422,7 +424,10 @@ pam_status pam_batch_create(const pam_plan_desc *common, const pam_frame_desc *f
         tw_off[f] = tw_total;
         tw_total += (size_t)b->nt[f];
     }
-    const int rpc = pam::prop_rows_per_cta(b->nx);
+    // Two rows per lane on 12 warps where they fit (nx >= 64): 1.5x the work in
+    // flight per SM, and row tiles of 1.5x the rows.
+    b->rpl = b->nx >= 64 ? 2 : 1;
+    const int rpc = pam::prop_rows_per_cta(b->nx, b->rpl);
     std::vector<int2> items;
     for (int f = 0; f < n_frames; ++f)
         for (int t = 0; t * rpc < b->nz[f]; ++t) items.push_back(make_int2(f, t));

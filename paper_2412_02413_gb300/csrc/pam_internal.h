@@ -17,9 +17,10 @@ constexpr int kFramesPerGroup = 32;
 constexpr int kMaxGemmK = 384;     // GEMM depth of the tensor-core form: 16 per (aperture, 8-element block)
 
 // Rows of the depth grid handled by one CTA of the fused propagate-and-correlate
-// kernel for a lateral length nx (8 warps; 2*nx/16 lanes per row).
+// kernel for a lateral length nx (2*nx/16 lanes per row) and rpl depth rows per
+// lane (1: 16 warps; 2: 12 warps for nx >= 64, 8 below).
 int prop_ctas_per_sm();   // resident CTAs per SM of the fused kernels (their register limit)
-int prop_rows_per_cta(int nx);
+int prop_rows_per_cta(int nx, int rpl = 1);
 
 // Bin splits up to this size reduce inside a thread-block cluster (portable limit).
 constexpr int kMaxClusterSplit = 8;
@@ -162,8 +163,10 @@ size_t prop_seg_part_floats(const pam_plan_s &p);
 // Batch (pam_batch.cu): the persistent propagate-and-correlate kernel over
 // (frame, row tile) items and the per-frame normalisation.
 // n_items_dev (optional): a device int that caps n_items when the kernel starts.
+// rpl: depth rows per lane; the items' row tiles are prop_rows_per_cta(nx, rpl) rows.
 cudaError_t launch_prop_batch(int nx, int napq, int grid, const BatchFrame *frames, const int2 *items, int n_items,
-                              int *counter, const EpiOut &out, cudaStream_t st, const int *n_items_dev = nullptr);
+                              int *counter, const EpiOut &out, cudaStream_t st, const int *n_items_dev = nullptr,
+                              int rpl = 1);
 // Full-aperture energy split by bins: the fused kernel (one aperture, whatever
 // Q holds) over n_bands contiguous chunks of Omega, chunk b = bins
 // [floor(n_bins b / n_bands), floor(n_bins (b+1) / n_bands)), each chunk's

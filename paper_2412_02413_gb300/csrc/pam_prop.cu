@@ -908,24 +908,25 @@ epi_normalize_kernel(const float4 *__restrict__ rho_tmp, const float4 *__restric
 // pairs taken from a global counter; an item runs every bin of its frame, so
 // its per-pixel epilogue follows directly from the registers. The staging
 // ring's position carries over from item to item.
-template <int NAP, int NX>
-__global__ void __launch_bounds__(PROP_THREADS, PROP_CTAS)
+template <int NAP, int NX, int RPL>
+__global__ void __launch_bounds__(32 * prop_warps(RPL, NX), PROP_CTAS)
 prop_batch_kernel(const BatchFrame *__restrict__ frames, const int2 *__restrict__ items, int n_items,
                   const int *__restrict__ n_items_dev, int *__restrict__ counter, EpiOut out)
 {
     if (n_items_dev) n_items = min(n_items, *n_items_dev);
-    using S = Shape<NX>;
+    using S = Shape<NX, RPL>;
     constexpr int L2 = S::L2, LPR = S::LPR, RPW = S::RPW, RPC = S::RPC, KPL = S::KPL;
     constexpr int NACC = Acc<NAP>::N;
     constexpr int NOUT = KPL * L2;
+    constexpr int NT = 32 * prop_warps(RPL, NX);
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const PropSmem<NAP, NX> sm(smem_raw);
+    const PropSmem<NAP, NX, RPL> sm(smem_raw);
     __shared__ int s_item;
-    __shared__ float wmax[PROP_THREADS / 32];
+    __shared__ float wmax[NT / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r = lane / LPR, g = (lane % LPR) / L2, n2 = lane % L2;
-    const unsigned tbase = sm.init(tmem_cols<NAP>());
-    const unsigned tcol = acc_tcol(tbase, warp, NACC);
+    const unsigned tbase = sm.init(tmem_cols<NAP, RPL, NX>());
+    const unsigned tcol = acc_tcol(tbase, warp, NACC, RPL);
     unsigned seq = 0;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -935,31 +936,39 @@ prop_batch_kernel(const BatchFrame *__restrict__ frames, const int2 *__restrict_
         if (it >= n_items) break;
         const int2 w = items[it];
         const BatchFrame fr = frames[w.x];
-        const int j = w.y * RPC + warp * RPW + r;
-        const bool row_ok = j < fr.nz;
-        const int jj = row_ok ? j : fr.nz - 1;
-        acc_zero<NAP>(tcol);
-        const int jja[1] = {jj};
-        const float zja[1] = {fr.z0f + (float)jj * fr.dzf};
-        const bool ok = prop_bins<NAP, NX, false>(sm, fr.Q, fr.phase, fr.bin_evan, 0, fr.n_bins, jja, zja, seq, tcol,
-                                                  nullptr, row_ok, 0);
+        int jr[RPL], jj[RPL];
+        float zj[RPL];
+        bool rok[RPL];
+#pragma unroll
+        for (int rr = 0; rr < RPL; ++rr) {
+            jr[rr] = w.y * RPC + warp * RPW + r * RPL + rr;
+            rok[rr] = jr[rr] < fr.nz;
+            jj[rr] = rok[rr] ? jr[rr] : fr.nz - 1;
+            zj[rr] = fr.z0f + (float)jj[rr] * fr.dzf;
+            acc_zero<NAP>(tcol + (unsigned)(rr * 8 * NACC));
+        }
+        const bool ok = prop_bins<NAP, NX, false, RPL>(sm, fr.Q, fr.phase, fr.bin_evan, 0, fr.n_bins, jj, zj, seq,
+                                                       tcol, nullptr, false, 0);
         seq += (unsigned)fr.n_bins;
         if (!ok && lane == 0) atomicOr(out.status, 1);
         if (__syncthreads_or(!ok)) break;
-        float acc[NOUT][NACC];
-        acc_read<NAP>(tcol, acc);
         float rmax = 0.0f;
-        if (row_ok) {
 #pragma unroll
-            for (int o = 0; o < NOUT; ++o) {
-                const int k1 = n2 * KPL + o / L2, k2 = o % L2;
-                const int i = 2 * (k1 + 8 * k2) + g;
-                rmax = fmaxf(rmax, pixel_epilogue<NAP>(acc[o], out, 0, fr.out_off + (size_t)j * NX + i));
+        for (int rr = 0; rr < RPL; ++rr) {
+            float acc[NOUT][NACC];
+            acc_read<NAP>(tcol + (unsigned)(rr * 8 * NACC), acc);   // warp-collective
+            if (rok[rr]) {
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    const int k1 = n2 * KPL + o / L2, k2 = o % L2;
+                    const int i = 2 * (k1 + 8 * k2) + g;
+                    rmax = fmaxf(rmax, pixel_epilogue<NAP>(acc[o], out, 0, fr.out_off + (size_t)jr[rr] * NX + i));
+                }
             }
         }
-        block_max_to(rmax, out.fmax + w.x, wmax, PROP_THREADS);
+        block_max_to(rmax, out.fmax + w.x, wmax, NT);
     }
-    sm.release(tbase, tmem_cols<NAP>());
+    sm.release(tbase, tmem_cols<NAP, RPL, NX>());
 }
 
 // Per-frame rho_n and image for a batch packed by per-frame pixel offsets.
@@ -1082,8 +1091,10 @@ cudaError_t prepare_nx()
 {
     cudaError_t e = prepare_nc<NX, true>();
     if (e == cudaSuccess) e = prepare_nc<NX, false>();
-    if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<2, NX>, prop_smem_bytes<2, NX>());
-    if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<3, NX>, prop_smem_bytes<3, NX>());
+    if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<2, NX, 1>, prop_smem_bytes<2, NX, 1>());
+    if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<3, NX, 1>, prop_smem_bytes<3, NX, 1>());
+    if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<2, NX, 2>, prop_smem_bytes<2, NX, 2>());
+    if (e == cudaSuccess) e = set_smem_of(prop_batch_kernel<3, NX, 2>, prop_smem_bytes<3, NX, 2>());
     if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<1, NX, 1>, prop_smem_bytes<1, NX, 1>());
     if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<2, NX, 1>, prop_smem_bytes<2, NX, 1>());
     if (e == cudaSuccess) e = set_smem_of(prop_seg_kernel<3, NX, 1>, prop_smem_bytes<3, NX, 1>());
@@ -1093,17 +1104,25 @@ cudaError_t prepare_nx()
     return e;
 }
 
+template <int NAP, int NX, int RPL>
+cudaError_t launch_batch_t(int grid, const BatchFrame *frames, const int2 *items, int n_items, const int *n_items_dev,
+                           int *counter, const EpiOut &out, cudaStream_t st)
+{
+    static_assert(prop_smem_bytes<NAP, NX, RPL>() + 1024 <= 232448, "shared memory of the fused kernel");
+    prop_batch_kernel<NAP, NX, RPL><<<grid, 32 * prop_warps(RPL, NX), prop_smem_bytes<NAP, NX, RPL>(), st>>>(
+        frames, items, n_items, n_items_dev, counter, out);
+    return cudaGetLastError();
+}
+
 template <int NX>
 cudaError_t launch_batch_nx(int napq, int grid, const BatchFrame *frames, const int2 *items, int n_items,
-                            const int *n_items_dev, int *counter, const EpiOut &out, cudaStream_t st)
+                            const int *n_items_dev, int *counter, const EpiOut &out, cudaStream_t st, int rpl)
 {
-    if (napq == 2)
-        prop_batch_kernel<2, NX><<<grid, PROP_THREADS, prop_smem_bytes<2, NX>(), st>>>(frames, items, n_items,
-                                                                                      n_items_dev, counter, out);
-    else
-        prop_batch_kernel<3, NX><<<grid, PROP_THREADS, prop_smem_bytes<3, NX>(), st>>>(frames, items, n_items,
-                                                                                      n_items_dev, counter, out);
-    return cudaGetLastError();
+    if (rpl == 2)
+        return napq == 2 ? launch_batch_t<2, NX, 2>(grid, frames, items, n_items, n_items_dev, counter, out, st)
+                         : launch_batch_t<3, NX, 2>(grid, frames, items, n_items, n_items_dev, counter, out, st);
+    return napq == 2 ? launch_batch_t<2, NX, 1>(grid, frames, items, n_items, n_items_dev, counter, out, st)
+                     : launch_batch_t<3, NX, 1>(grid, frames, items, n_items, n_items_dev, counter, out, st);
 }
 
 template <int NX>
@@ -1138,13 +1157,10 @@ cudaError_t launch_expire_wait(int *status, cudaStream_t st)
     return cudaGetLastError();
 }
 
-int prop_rows_per_cta(int nx) { return PROP_WARPS * (32 / (nx / 8)); }
+int prop_rows_per_cta(int nx, int rpl) { return prop_warps(rpl, nx) * rpl * (32 / (nx / 8)); }
 
 // Rows per CTA of prop_seg_kernel for the plan's rows per lane.
-static int seg_rows(const pam_plan_s &p)
-{
-    return p.lane_rows == 2 ? prop_warps(2, p.nx) * 2 * (32 / (p.nx / 8)) : prop_rows_per_cta(p.nx);
-}
+static int seg_rows(const pam_plan_s &p) { return prop_rows_per_cta(p.nx, p.lane_rows); }
 
 int prop_ctas_per_sm() { return PROP_CTAS; }
 
@@ -1168,7 +1184,7 @@ int prop_seg_ctas(const pam_plan_s &p, int n_frames)
 size_t prop_seg_part_floats(const pam_plan_s &p)
 {
     // the larger row tile of the two rows-per-lane settings, which can change after the plan is made
-    const int r1 = prop_rows_per_cta(p.nx), r2 = prop_warps(2, p.nx) * 2 * (32 / (p.nx / 8));
+    const int r1 = prop_rows_per_cta(p.nx, 1), r2 = prop_rows_per_cta(p.nx, 2);
     const int rows = r1 > r2 ? r1 : r2;
     return (size_t)2 * PROP_CTAS * p.num_sms * n_acc(p.n_apod) * rows * p.nx;
 }
@@ -1249,14 +1265,15 @@ cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_s
 }
 
 cudaError_t launch_prop_batch(int nx, int napq, int grid, const BatchFrame *frames, const int2 *items, int n_items,
-                              int *counter, const EpiOut &out, cudaStream_t st, const int *n_items_dev)
+                              int *counter, const EpiOut &out, cudaStream_t st, const int *n_items_dev, int rpl)
 {
     if (napq != 2 && napq != 3) return cudaErrorInvalidValue;
+    if (rpl != 1 && rpl != 2) return cudaErrorInvalidValue;
     switch (nx) {
-    case 16: return launch_batch_nx<16>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st);
-    case 32: return launch_batch_nx<32>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st);
-    case 64: return launch_batch_nx<64>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st);
-    case 128: return launch_batch_nx<128>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st);
+    case 16: return launch_batch_nx<16>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st, rpl);
+    case 32: return launch_batch_nx<32>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st, rpl);
+    case 64: return launch_batch_nx<64>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st, rpl);
+    case 128: return launch_batch_nx<128>(napq, grid, frames, items, n_items, n_items_dev, counter, out, st, rpl);
     default: return cudaErrorInvalidValue;
     }
 }

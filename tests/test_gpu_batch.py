@@ -130,7 +130,7 @@ def test_batch_graph_replay_direct_launch_and_grid_agree():
     img4, rn4 = b.as_tax(rf)
     assert torch.equal(img1, img4) and torch.equal(rn1, rn4)
     n_items, grid, k = b.info()
-    rows = 8 * (32 // (ne // 8))        # rows per work item: 8 warps, 2 nx/16 lanes per row
+    rows = 16 * (32 // (ne // 8))       # rows per work item: 16 warps (one row per lane at nx = 32), nx/8 lanes per row
     assert grid == 1 and n_items == sum((nz + rows - 1) // rows for _, nz in frames) and k >= 16
     b.sync()
 
