@@ -10,14 +10,15 @@
 // reach global memory. The epilogue forms rho_qr, the eps clamp, rho_TAX
 // (Eq. 10), its per-frame maximum, rho_n and the image (Eq. 5 / 11).
 //
-// Work mapping of the fused kernel: 8 warps per CTA. Each depth row is owned
-// by 2*(nx/16) lanes that each hold 8 pixels of that row for all apodizations.
+// Work mapping of the fused kernel: one CTA per SM, 16 warps with one depth
+// row per lane or 12 (8 below nx = 64) with two. Each depth row is owned by
+// 2*(nx/16) lanes that each hold 8 pixels of that row for all apodizations.
 // The nx-point inverse DFT is one radix-2 decimation-in-frequency split,
-// folded into the phase words as below, followed by two (nx/2)-point halves.
-// Each half is an 8-point DFT in registers, a twiddle, a transpose through
-// padded shared memory and an (nx/16)-point DFT in registers. A CTA loops over
-// a contiguous chunk of bins. Each bin's spectra and phase words are staged in
-// shared memory with cp.async, double-buffered.
+// folded into the staged spectra as below, followed by two (nx/2)-point
+// halves. Each half is an 8-point DFT in registers, a twiddle, a transpose
+// through padded shared memory and an (nx/16)-point DFT in registers. A CTA
+// loops over a contiguous chunk of bins. Each bin's spectra and phase words
+// are staged in shared memory by bulk copies, 3 or 4 bins in flight.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -118,7 +119,7 @@ __device__ __forceinline__ float2 phase_cis(unsigned w)
 
 using namespace ptx;
 
-// One CTA per SM (16 warps, up to 128 registers each): with two, the warp
+// One CTA per SM (it takes the whole register file): with two, the warp
 // scheduler favours the older CTA, which then finishes its share early and
 // leaves the other running at half occupancy.
 constexpr int PROP_CTAS = 1;
