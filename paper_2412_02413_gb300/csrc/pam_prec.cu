@@ -100,18 +100,37 @@ prec_table_kernel(const uint4 *__restrict__ phase, const float *__restrict__ liv
 }
 
 // ----------------------------------------------------- per-call prep ----
-// max |Re S|, |Im S| of each frame (bits of a non-negative float).
-__global__ void prec_smax_kernel(const float2 *__restrict__ S, int n_bins, int ne, unsigned *__restrict__ smax)
+// max |Re S|, |Im S| of each frame (bits of a non-negative float). A frame's
+// n_vals = n_bins x ne values are contiguous; the blocks of grid row f read
+// them as float4 pairs in a grid-stride loop and fold one maximum each into
+// smax[f] (the maximum does not depend on the order).
+constexpr int SMAX_THREADS = 256;
+__global__ void __launch_bounds__(SMAX_THREADS)
+prec_smax_kernel(const float2 *__restrict__ S, int n_vals, unsigned *__restrict__ smax)
 {
-    const int b = blockIdx.x, f = blockIdx.y;
+    __shared__ float wm[SMAX_THREADS / 32];
+    const int f = blockIdx.y;
+    const float4 *src = reinterpret_cast<const float4 *>(S + (size_t)f * n_vals);
+    const int n4 = n_vals / 2;   // n_vals is even (ne is a multiple of 8)
     float m = 0.f;
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-        const float2 v = S[((size_t)f * n_bins + b) * ne + e];
-        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    for (int i = blockIdx.x * SMAX_THREADS + threadIdx.x; i < n4; i += gridDim.x * SMAX_THREADS) {
+        const float4 v = src[i];
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(&smax[f], __float_as_uint(m));
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < SMAX_THREADS / 32; ++w) m = fmaxf(m, wm[w]);
+        atomicMax(&smax[f], __float_as_uint(m));
+    }
+}
+// Blocks per frame of prec_smax_kernel: about 1024 float4 each, at most 32.
+int smax_blocks(int n_vals)
+{
+    const int n = (n_vals / 2 + 4 * SMAX_THREADS - 1) / (4 * SMAX_THREADS);
+    return n < 1 ? 1 : (n > 32 ? 32 : n);
 }
 
 // Power-of-2 scale 2^E >= max of the frame, so that S / 2^E is exact and
@@ -144,28 +163,45 @@ prec_bprep_kernel(const float2 *__restrict__ S, const short *__restrict__ ktab, 
     const size_t tile = (size_t)K * NG * 2;
     uint8_t *dh = Bhi + ((size_t)g * n_bins + b) * tile;
     uint8_t *dl = SPLIT ? Blo + ((size_t)g * n_bins + b) * tile : nullptr;
-    for (int idx = threadIdx.x; idx < K * NG; idx += blockDim.x) {
-        const int k = idx / NG, n = idx % NG;
+    // Thread (kc, n) writes the 8 entries k = 8 kc .. 8 kc + 7 of column n: one
+    // 16-byte row of a core matrix (consecutive n, consecutive rows).
+    for (int idx = threadIdx.x; idx < (K / 8) * NG; idx += blockDim.x) {
+        const int kc = idx / NG, n = idx % NG;
         const int f = g * FG + n % FG, kind = n / FG;   // columns: Re of the FG frames, then Im
-        float v = 0.f;
-        const short kt = ktab[k];
-        if (f < F && kt >= 0) {
-            const int e = kt & 0x3FFF, imag = (kt >> 14) & 1;
-            const float sc = kwgt[k] * ldexpf(1.0f, -frame_exp(smax[f]));
-            const float2 s = S[((size_t)f * n_bins + b) * ne + e];
-            const float sr = s.x * sc, si = s.y * sc;
-            v = imag == 0 ? (kind == 0 ? sr : si) : (kind == 0 ? -si : sr);
+        const bool live = f < F;
+        const float p2 = live ? ldexpf(1.0f, -frame_exp(smax[f])) : 0.f;
+        const float2 *Sf = S + ((size_t)(live ? f : 0) * n_bins + b) * ne;
+        unsigned h[4], l[4];
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            unsigned short hh[2], ll[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int k = 8 * kc + t + u;
+                float v = 0.f;
+                const short kt = ktab[k];
+                if (live && kt >= 0) {
+                    const int e = kt & 0x3FFF, imag = (kt >> 14) & 1;
+                    const float sc = kwgt[k] * p2;
+                    const float2 s = Sf[e];
+                    const float sr = s.x * sc, si = s.y * sc;
+                    v = imag == 0 ? (kind == 0 ? sr : si) : (kind == 0 ? -si : sr);
+                }
+                hh[u] = to16<FP16>(v);
+                ll[u] = SPLIT ? to16<FP16>(v - from16<FP16>(hh[u])) : (unsigned short)0;
+            }
+            h[t / 2] = (unsigned)hh[0] | ((unsigned)hh[1] << 16);
+            l[t / 2] = (unsigned)ll[0] | ((unsigned)ll[1] << 16);
         }
-        const unsigned short h = to16<FP16>(v);
         size_t off;
         if constexpr (PAIR) {
             const int half = n / FG, nn = n % FG;
-            off = (size_t)half * K * FG * 2 + (size_t)(k / 8) * (CS_B / 2) + (nn / 8) * 128 + (nn % 8) * 16 + (k % 8) * 2;
+            off = (size_t)half * K * FG * 2 + (size_t)kc * (CS_B / 2) + (nn / 8) * 128 + (nn % 8) * 16;
         } else {
-            off = (size_t)(k / 8) * CS_B + (n / 8) * 128 + (n % 8) * 16 + (k % 8) * 2;
+            off = (size_t)kc * CS_B + (n / 8) * 128 + (n % 8) * 16;
         }
-        *reinterpret_cast<unsigned short *>(dh + off) = h;
-        if (SPLIT) *reinterpret_cast<unsigned short *>(dl + off) = to16<FP16>(v - from16<FP16>(h));
+        *reinterpret_cast<uint4 *>(dh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        if (SPLIT) *reinterpret_cast<uint4 *>(dl + off) = make_uint4(l[0], l[1], l[2], l[3]);
     }
 }
 
@@ -635,7 +671,8 @@ cudaError_t launch_bands_form(const pam_plan_s &p, const float2 *S, int n_frames
 {
     cudaError_t e = cudaMemsetAsync(p.w.smax, 0, sizeof(unsigned) * n_frames, st);
     if (e != cudaSuccess) return e;
-    prec_smax_kernel<<<dim3(p.n_bins, n_frames), 128, 0, st>>>(S, p.n_bins, p.ne, p.w.smax);
+    prec_smax_kernel<<<dim3(smax_blocks(p.n_bins * p.ne), n_frames), SMAX_THREADS, 0, st>>>(S, p.n_bins * p.ne,
+                                                                                           p.w.smax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     constexpr int FG = 32;
     const int groups = (n_frames + FG - 1) / FG;
@@ -670,7 +707,8 @@ cudaError_t launch_form(const pam_plan_s &p, int n_frames, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(p.w.smax, 0, sizeof(unsigned) * n_frames, st);
     if (e != cudaSuccess) return e;
-    prec_smax_kernel<<<dim3(p.n_bins, n_frames), 128, 0, st>>>(p.w.S, p.n_bins, p.ne, p.w.smax);
+    prec_smax_kernel<<<dim3(smax_blocks(p.n_bins * p.ne), n_frames), SMAX_THREADS, 0, st>>>(p.w.S, p.n_bins * p.ne,
+                                                                                           p.w.smax);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const bool pair = p.gemm_m == 256, f16 = p.gemm_frames == 16;
     if (pair)

@@ -783,43 +783,44 @@ prop_seg_kernel(const float2 *__restrict__ Q, const uint4 *__restrict__ phase, c
 
 // --------------------------------------------------------- epilogue ----
 
+constexpr int EPI_THREADS = 128;
+
 // Sums the per-split partials in split order (deterministic) and finishes
-// the per-pixel epilogue. One warp per accumulator sums 32 groups of four
-// pixels (every partial load of a thread is independent, so they overlap);
-// warp 0 then combines the accumulators of its pixels.
+// the per-pixel epilogue. Each thread takes four pixels: one float4 of every
+// accumulator plane of every split, all loads of a split issued before its
+// sums.
 template <int NAP>
-__global__ void __launch_bounds__(32 * Acc<NAP>::N)
+__global__ void __launch_bounds__(EPI_THREADS)
 epi_reduce_kernel(const float4 *__restrict__ part, int n_split, int npix4, EpiOut out)
 {
     constexpr int NACC = Acc<NAP>::N;
-    __shared__ float4 sA[NACC][32];
-    __shared__ float wmax[NACC];
+    __shared__ float wmax[EPI_THREADS / 32];
     const int f = blockIdx.y;
-    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int x4 = blockIdx.x * 32 + lane;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (x4 < npix4) {
-        const float4 *src = part + ((size_t)f * n_split * NACC + c) * npix4 + x4;
-        const size_t stride = (size_t)NACC * npix4;
-#pragma unroll 4
-        for (int s = 0; s < n_split; ++s) {
-            const float4 v = src[s * stride];
-            a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
-        }
-    }
-    sA[c][lane] = a;
-    __syncthreads();
+    const int x4 = blockIdx.x * EPI_THREADS + threadIdx.x;
     float rmax = 0.0f;
-    if (c == 0 && x4 < npix4) {
+    if (x4 < npix4) {
+        float4 a[NACC];
+#pragma unroll
+        for (int c = 0; c < NACC; ++c) a[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 *src = part + (size_t)f * n_split * NACC * npix4 + x4;
+        for (int s = 0; s < n_split; ++s) {
+            float4 v[NACC];
+#pragma unroll
+            for (int c = 0; c < NACC; ++c) v[c] = src[((size_t)s * NACC + c) * npix4];
+#pragma unroll
+            for (int c = 0; c < NACC; ++c) {
+                a[c].x += v[c].x; a[c].y += v[c].y; a[c].z += v[c].z; a[c].w += v[c].w;
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float acc[NACC];
 #pragma unroll
-            for (int k = 0; k < NACC; ++k) acc[k] = reinterpret_cast<const float *>(&sA[k][lane])[i];
+            for (int k = 0; k < NACC; ++k) acc[k] = reinterpret_cast<const float *>(&a[k])[i];
             rmax = fmaxf(rmax, pixel_epilogue<NAP>(acc, out, f, (size_t)x4 * 4 + i));
         }
     }
-    if constexpr (NAP > 1) block_max_to(rmax, out.fmax + f, wmax, 32 * NACC);
+    if constexpr (NAP > 1) block_max_to(rmax, out.fmax + f, wmax, EPI_THREADS);
 }
 
 // The split tiles of prop_seg_kernel: for each pixel of a tile that two or
@@ -883,8 +884,6 @@ epi_reduce_seg_kernel(const float4 *__restrict__ part, int npix4, int nx, int rp
     }
     if constexpr (NAP > 1) block_max_to(rmax, out.fmax + f, wmax, 32 * NACC);
 }
-
-constexpr int EPI_THREADS = 128;
 
 // rho_n = rho / max (Sec. II-A: the maximum becomes exactly 1) and the image
 // I = rho_n^2 E (Eq. 5 / Eq. 11). Four pixels per thread.
@@ -1249,13 +1248,12 @@ cudaError_t launch_epilogue(const pam_plan_s &p, int n_frames, int napq, int n_s
         if (e != cudaSuccess) return e;
     } else if (from_partials || !prop_uses_cluster(n_split)) {
         const float4 *part = reinterpret_cast<const float4 *>(p.w.part);
-        dim3 rgrid((npix4 + 31) / 32, n_frames);
         if (napq == 1)
-            epi_reduce_kernel<1><<<rgrid, 32 * Acc<1>::N, 0, st>>>(part, n_split, npix4, out);
+            epi_reduce_kernel<1><<<grid, EPI_THREADS, 0, st>>>(part, n_split, npix4, out);
         else if (napq == 2)
-            epi_reduce_kernel<2><<<rgrid, 32 * Acc<2>::N, 0, st>>>(part, n_split, npix4, out);
+            epi_reduce_kernel<2><<<grid, EPI_THREADS, 0, st>>>(part, n_split, npix4, out);
         else
-            epi_reduce_kernel<3><<<rgrid, 32 * Acc<3>::N, 0, st>>>(part, n_split, npix4, out);
+            epi_reduce_kernel<3><<<grid, EPI_THREADS, 0, st>>>(part, n_split, npix4, out);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
