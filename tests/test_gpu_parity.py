@@ -588,6 +588,33 @@ def test_gemm_form_overlapping_apertures(form):
     assert ncc <= ncc_tol, ncc
 
 
+def test_gemm_tile_and_frames_options_on_dax():
+    """The two-aperture kernels under every (M tile, frames per CTA) pair:
+    AS-DAX with overlapping, unaligned apertures, 18 frames (a ragged group of
+    16 and of 32) and 13 rows (a pair with one row), bit-identical to the
+    default and within the split form's tolerance of the oracle."""
+    w = _tiny(128, 512, 13, bins=10, fs=40e6, f_lo=1e6, f_hi=8e6, pattern_m=16)
+    e = np.arange(128)
+    A = np.zeros((2, 128), np.float32)
+    A[0, :70] = 0.5 + 0.5 * np.cos(np.pi * e[:70] / 71.0)
+    A[1, 37:] = 0.75 + 0.25 * np.sin(e[37:] / 9.0)
+    frames = synth.random_rf(128, 512, seed=37, n_frames=18)
+    rf = torch.from_numpy(frames).cuda()
+    plan = _plan(w, n_apod=2, apod=A, max_frames=18, form="fp16split")
+    kw = dict(rho_n=True, rho_pairs=True, image_as=True)
+    ref = {k: v.clone() for k, v in plan.as_dax(rf, **kw).items()}
+    for m, fg in ((256, 32), (128, 16), (256, 16)):
+        plan.set_gemm_tile(m)
+        plan.set_gemm_frames(fg)
+        out = plan.as_dax(rf, **kw)
+        torch.cuda.synchronize()
+        for k in ref:
+            assert torch.equal(ref[k], out[k]), (m, fg, k)
+    orc = oracle.as_xcorr(_geom(w), frames[17], A)
+    assert rel_l2(out["image"][17].cpu().numpy(), orc["image"]) <= FORM_TOL["fp16split"][0]
+    assert float(np.max(np.abs(out["rho_pairs"][17].cpu().numpy() - orc["rho_pairs"]))) <= FORM_TOL["fp16split"][1]
+
+
 def test_gemm_form_rejects_unsupported():
     pam = _pam()
     with pytest.raises(pam.PamError):
