@@ -478,21 +478,40 @@ prec_gemm_kernel(const uint32_t *__restrict__ chi, const uint32_t *__restrict__ 
 #pragma unroll
             for (int a = 0; a < NACC; ++a) acc[f][a] = make_float2(0.f, 0.f);
 
-        // Thread (part, n, r) writes row r of block n: the 8 entries
-        // c[(8 (n mod 16) + r - t) mod 128], t = 0..7, as one 16-byte row of
-        // Re parts and one of Im parts.
+        // Row r of block n holds the 8 entries c[(8 (n mod 16) + r - t) mod 128],
+        // t = 0..7, as one 16-byte row of Re parts and one of Im parts; blocks n
+        // and n + 16 are the same. With the split, thread (part, d, r) computes
+        // row r of T_d of its part once and stores it in both blocks (half the
+        // loads per thread of building the two parts in turn: 4% faster); with
+        // one part, thread (n, r) builds row r of block n (computing once and
+        // storing twice was 1.4% slower there).
         auto build = [&](int b) -> bool {
             const int s = b % NST;
             if (!wait(&full[s], (unsigned)(b / NST) & 1u)) return false;
-#pragma unroll
-            for (int pidx = 0; pidx < NPART; ++pidx) {
-                const int n = ctid >> 3, r = ctid & 7;
+            if constexpr (SPLIT) {
+                const int pidx = ctid >> 7, d = (ctid >> 3) & 15, r = ctid & 7;
                 const uint32_t *cw = sC(s) + pidx * NXP;
+                const int m0 = 8 * d + r;
+                unsigned w[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) w[t] = cw[(m0 - t) & (NXP - 1)];
+                uint8_t *A = sA(s) + pidx * A_BYTES + d * 128 + r * 16;
+                const uint4 re = make_uint4(__byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
+                                            __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
+                const uint4 im = make_uint4(__byte_perm(w[0], w[1], 0x7632), __byte_perm(w[2], w[3], 0x7632),
+                                            __byte_perm(w[4], w[5], 0x7632), __byte_perm(w[6], w[7], 0x7632));
+                *reinterpret_cast<uint4 *>(A) = re;
+                *reinterpret_cast<uint4 *>(A + 16 * 128) = re;
+                *reinterpret_cast<uint4 *>(A + BLK_BYTES) = im;
+                *reinterpret_cast<uint4 *>(A + BLK_BYTES + 16 * 128) = im;
+            } else {
+                const int n = ctid >> 3, r = ctid & 7;
+                const uint32_t *cw = sC(s);
                 const int m0 = 8 * (n & 15) + r;
                 unsigned w[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) w[t] = cw[(m0 - t) & (NXP - 1)];
-                uint8_t *A = sA(s) + pidx * A_BYTES + n * 128 + r * 16;
+                uint8_t *A = sA(s) + n * 128 + r * 16;
                 *reinterpret_cast<uint4 *>(A) =
                     make_uint4(__byte_perm(w[0], w[1], 0x5410), __byte_perm(w[2], w[3], 0x5410),
                                __byte_perm(w[4], w[5], 0x5410), __byte_perm(w[6], w[7], 0x5410));
